@@ -1,0 +1,361 @@
+"""Benchmark: ChFSI H.X applies/s on the 32-atom erf cluster (lmax 30, 48 radial functions,
+d = 46128, 96 x 60 x 120 grid, 80 states, Chebyshev degree 16) on one GB300.
+
+A step is one ChFSI iteration (Sec. 3.2.1): the degree-16 Chebyshev filter (16 H.X block
+products in the chosen precision, three-term recurrence fused into the H.X epilogue),
+Cholesky-QR (two passes, FP64) and Rayleigh-Ritz (one FP64 H.X, Gram, Jacobi eigensolve,
+rotations, residual norms). value = state-columns multiplied by H per second
+= (degree + 1) * n_s / step time, summed over ranks (each rank runs its own block:
+weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "ChFSI H·X applies/s and SCF time to 1e-6 Ha: mixed/batched vs FP64, 1 GB300"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 ALU peaks of one GB300: FP64 nominal 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes
+# x 2 flop x 2.07 GHz (maximum SM clock).
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ algorithmic work
+def algorithmic_flops(w, n_s):
+    """Per-state flop counts of one H.X (FFT count for phi, parity-folded Legendre)."""
+    L, N, nr, nt, nph = w.L, w.nmax, w.n_r, w.n_theta, w.n_phi
+    f_rad = 2.0 * nr * N * L * L                      # one direction
+    f_leg = 2.0 * nt * L * L * nr / 2.0               # one direction, folded
+    f_phi = 2.5 * nph * math.log2(nph) * nr * nt      # one direction (real FFT estimate)
+    f_v = float(nr * nt * nph)
+    return {"radial_synth": f_rad * n_s, "angular": (2 * f_leg + 2 * f_phi + f_v) * n_s,
+            "radial_anal": f_rad * n_s}
+
+
+def dense_flops(d, n):
+    # CholQR twice (Gram + rotation) + RR (Gram + two rotations)
+    return 2 * (2.0 * d * n * n + 2.0 * d * n * n) + (2.0 * d * n * n + 4.0 * d * n * n)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows),
+                "power_w_max": max((float(r[3]) for r in self.rows
+                                    if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    import paper_1404_3773_gb300 as cs
+    from paper_1404_3773_gb300 import CS_FP32, CS_FP64
+
+    prec = CS_FP64 if args.precision == "fp64" else CS_FP32
+    w = W.erf_cluster_32()
+    n_s, degree = w.n_s, w.degree
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, local)
+    v = w.potential_at(cs.grid_points(ctx))
+    cs.cs_set_potential(ctx, torch.tensor(v, dtype=torch.float64, device=dev))
+    d = ctx.d
+    # each rank filters its own block of states (independent seeds)
+    X0h = W.gaussian_block(w.x_seed + 1000 * rank, d, n_s)
+    X0 = torch.tensor(np.ascontiguousarray(X0h.T), device=dev)
+    work = ctx.workspace(n_s, prec)
+    theta = torch.empty(n_s, dtype=torch.float64, device=dev)
+    resid = torch.empty_like(theta)
+    # bounds (untimed set-up): Lanczos upper bound, first-pass interval, then one
+    # iteration to reach the steady-state interval used by every timed step
+    v0 = torch.tensor(W.gaussian(4242 + rank, d), device=dev)
+    b, tmin = cs.cs_lanczos_bound(ctx, v0, 10, work)
+    cs.cs_cholqr(ctx, X0, work)
+    a0, a = tmin, tmin + (b - tmin) / 10.0
+    Xs = X0.clone()
+    cs.cs_chfsi_step(ctx, Xs, degree, a, b, a0, theta, resid, prec, work)
+    th = theta.cpu().numpy()
+    a, a0 = float(th[-1]), float(th[0])
+    X0.copy_(Xs)
+    X = torch.empty_like(X0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def step():
+        cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, prec, work)
+
+    for _ in range(args.warmup):
+        X.copy_(X0)
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = cs.cs_launch_count(ctx)
+    cs.cs_profile_begin(ctx)
+    total_ms = 0.0
+    launches_timed = 0
+    for _ in range(args.steps):
+        X.copy_(X0)
+        flush.fill_(1.0)  # L2 flush between timed iterations (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        before = cs.cs_launch_count(ctx)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        launches_timed += cs.cs_launch_count(ctx) - before
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    prof_ms, prof_n = cs.cs_profile_end(ctx)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    if rank == 0:
+        time.sleep(0.3)
+        clocks.stop()
+    ms_per_step = total_ms / args.steps
+    applies_per_step = (degree + 1) * n_s
+    value = world * applies_per_step / (ms_per_step / 1e3)
+
+    # ---- end to end through the public API: host (pinned) X in, Ritz vectors + values out
+    Xh = torch.empty_like(X0, device="cpu").pin_memory()
+    Xh.copy_(X0.cpu())
+    Xout = torch.empty_like(Xh).pin_memory()
+    thh = torch.empty(n_s, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        X.copy_(Xh, non_blocking=True)
+        step()
+        Xout.copy_(X, non_blocking=True)
+        thh.copy_(theta, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = X0.numel() * 8
+    d2h = X0.numel() * 8 + n_s * 8
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel class (device time measured live above)
+    names = ["radial_synth", "angular", "radial_anal", "dense_fp64"]
+    dom = int(np.argmax(prof_ms))
+    per_launch_ms = prof_ms[dom] / max(1, prof_n[dom])
+    af = algorithmic_flops(w, n_s)
+    peak_dense = FP64_PEAK_TFLOPS
+    if names[dom] == "dense_fp64":
+        flops_per_launch = dense_flops(d, n_s) / max(1, prof_n[dom] / args.steps)
+        peak = peak_dense
+        kdtype = "f64"
+    else:
+        flops_per_launch = af[names[dom]]
+        # launches of the class run in the filter precision, one per step in FP64 (RR)
+        kdtype = "f64" if prec == CS_FP64 else "f32"
+        peak = FP64_PEAK_TFLOPS if prec == CS_FP64 else FP32_PEAK_TFLOPS
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": names[dom], "kernel_dtype": kdtype,
+                "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300)" if peak == FP64_PEAK_TFLOPS
+                else "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flops_per_launch": flops_per_launch,
+                "avg_launch_ms": round(per_launch_ms, 5),
+                "share": {names[i]: round(prof_ms[i] / max(1e-9, sum(prof_ms)), 4)
+                          for i in range(4)},
+                "launches": {names[i]: int(prof_n[i]) for i in range(4)}}
+
+    cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == CS_FP64 else "f32+f64",
+        "data": "synthetic (seeded erf pseudo-atom cluster and Gaussian state block)",
+        "config": {"workload": "erf32_l30_n48: 32 erf atoms in r<=8, R=14, lmax=30, 48 radial "
+                               "fns/l, d=46128, grid 96x60x120, 80 states, degree 16",
+                   "step": "one ChFSI iteration: filter (16 H.X) + CholQR x2 + Rayleigh-Ritz "
+                           "(1 FP64 H.X)",
+                   "filter_precision": args.precision, "orthonormalisation": "fp64",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world} (independent state blocks)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(world * applies_per_step / (e2e_ms / 1e3), 2),
+                "unit": "applies/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches_timed),
+        "clocks": clocks.summary(),
+        "ritz": {"theta_min": float(theta.min().item()), "resid_max_lowest64":
+                 float(resid[:64].max().item())},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(w, budget_s=15.0, cols=8):
+    """The FP64 oracle as it stands, on the host cores: H.X on `cols` states of the same
+    workload, repeated for about `budget_s` seconds. Returns applies/s (state columns per
+    second)."""
+    from oracle.basis import basis_for
+    from oracle.hamiltonian import Hamiltonian
+    b = basis_for(w)
+    H = Hamiltonian(b, w.potential_at(b.points()))
+    X = w.x_block(cols)
+    H.apply(X)  # warm
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        H.apply(X)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(n * cols / el, 4), "unit": "applies/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n} oracle H.X calls on {cols} of the 80 states of the same workload "
+                      f"(FP64, numpy; {el:.1f} s)"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    w = W.erf_cluster_32()
+    from oracle.basis import basis_for
+    from oracle.hamiltonian import Hamiltonian
+    b = basis_for(w)
+    H = Hamiltonian(b, w.potential_at(b.points()))
+    cols = 4
+    X = w.x_block(cols)
+    for _ in range(args.warmup):
+        H.apply(X)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H.apply(X)
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    value = args.steps * cols / el
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4),
+            "unit": "applies/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded erf pseudo-atom cluster and Gaussian state block)",
+            "config": {"workload": "erf32_l30_n48 (same as the GPU arm)",
+                       "step": f"one oracle H.X on {cols} of the 80 states (bounded sample)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "applies/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} oracle H.X calls on {cols} states"},
+            "e2e": {"value": round(value, 4), "unit": "applies/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * cs.h -- C ABI of libclusterspec: the Chebyshev-filtered subspace iteration (ChFSI) hot
+ * path of the spherical spectral Kohn-Sham method (Banerjee, Elliott, James, "A spectral
+ * scheme for Kohn-Sham density functional theory of clusters"), on one GB300 (sm_103a).
+ *
+ * Problem statement the calls follow:
+ *   basis     F_lmn = R_ln(r) Y_lm(theta, phi) on the ball |x| <= R, 0 <= l <= lmax,
+ *             -l <= m <= l, 0 <= n < nmax; d = (lmax+1)^2 nmax functions (Sec. 2.2.1,
+ *             eqs. eigfunction_1, spherical_bessel_1, spherical_harmonics_1). Real
+ *             harmonics without the Condon-Shortley phase: Y_l0 = Theta_l0(cos theta),
+ *             Y_lm = sqrt2 Theta_lm cos(m phi), Y_l,-m = sqrt2 Theta_lm sin(m phi), m > 0.
+ *   index     alpha(l, m, n) = (l^2 + l + m) nmax + n  (0-based form of the footnote to
+ *             eq. Hij_def).
+ *   grid      N_r radial nodes with weights including r^2, N_theta Gauss points in
+ *             cos(theta) in ascending order, N_phi uniform angles 2 pi q / N_phi
+ *             (Sec. 2.2.2). Grid functions are [k][j][q] arrays, q fastest.
+ *   operator  H = 1/2 diag(Lambda) + B^T diag(W V) B + P diag(h) P^T, B the synthesis
+ *             matrix, W the quadrature weights, V the effective potential on the grid,
+ *             P the projector coefficients (Sec. 2.2.4 eq. matvec_final, Sec. 2.3.2).
+ *   filter    scaled Chebyshev filter of Sec. 3.2.1 (the cited Zhou-Saad recurrence).
+ *
+ * Conventions for every call:
+ *   - Every call returns cs_status. No exception, exit or abort crosses the ABI.
+ *     Arguments are checked before any launch (CS_ERR_ARG). cs_last_error(ctx) returns
+ *     a message for the last failing call on that context.
+ *   - Ownership: the caller owns every buffer it passes (host or device) and the library
+ *     never frees one. A context owns its tables, allocated by cs_basis_init and
+ *     freed by cs_basis_free.
+ *   - Streams: cs_stream is a cudaStream_t (NULL = legacy default stream). All device
+ *     work is enqueued on it. Calls return after enqueueing, except the ones documented
+ *     as synchronising (they read FP64 scalars back).
+ *   - Blocks X are column-major d x n_s with leading dimension ld >= d, one column per
+ *     state, element type given by cs_precision (FP64: double; FP32: float).
+ *   - A context is not thread-safe. It is bound to the CUDA device given at init.
+ */
+#ifndef CLUSTERSPEC_CS_H
+#define CLUSTERSPEC_CS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_ctx cs_ctx;
+typedef void* cs_stream; /* a cudaStream_t */
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_ARG = 1,           /* invalid argument (checked before any launch)          */
+  CS_ERR_ALLOC = 2,         /* device or host allocation failed                      */
+  CS_ERR_CUDA = 3,          /* a CUDA runtime call or a launch failed                */
+  CS_ERR_STATE = 4,         /* call order violated (e.g. apply before set_potential)  */
+  CS_ERR_CHOLESKY = 5,      /* Cholesky factorisation broke down (rank-deficient block) */
+  CS_ERR_NOT_CONVERGED = 6, /* iteration limit reached before the tolerance           */
+  CS_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                     */
+  CS_ERR_NUMERIC = 8        /* NaN or Inf detected in a result                        */
+} cs_status;
+
+typedef enum { CS_RADIAL_GAUSS_LEGENDRE = 0, CS_RADIAL_GAUSS_JACOBI_R2 = 1 } cs_radial_rule;
+
+typedef struct {
+  int n_r;     /* radial nodes                                        */
+  int n_theta; /* Gauss points in cos(theta), > lmax                  */
+  int n_phi;   /* uniform phi points, even, >= 2 lmax + 2             */
+  int radial;  /* cs_radial_rule                                      */
+} cs_quadrature;
+
+typedef enum {
+  CS_FP64 = 0, /* FP64 storage and arithmetic                                 */
+  CS_FP32 = 1  /* FP32 storage and arithmetic (FP32 FMA pipe)                 */
+} cs_precision;
+
+/* ------------------------------------------------------------------ basis / context */
+
+/* Build a context: Bessel zeros z_ln (Sec. 2.2.1 eq. laplacian_eigenvalue: Lambda_ln =
+ * (z_ln/R)^2), radial table R_ln(r_k), normalised Legendre table Theta_lm(t_j), phi
+ * twiddles, kinetic diagonal; uploads them to `cuda_device`. Host-side set-up, then
+ * synchronous uploads. nmax = radial functions per l. Requirements: R > 0, 0 <= lmax,
+ * nmax >= 1, n_theta > lmax, n_phi even and >= 2 lmax + 2, n_r >= 1.
+ * On success *out owns device tables; free with cs_basis_free. */
+cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, int cuda_device,
+                        cs_ctx** out);
+
+/* Free a context and all tables it owns (synchronises its device). NULL is accepted. */
+cs_status cs_basis_free(cs_ctx* ctx);
+
+/* Sizes: d = (lmax+1)^2 nmax and the grid dimensions. Any pointer may be NULL. */
+cs_status cs_basis_dims(const cs_ctx* ctx, long long* d, int* n_r, int* n_theta, int* n_phi);
+
+/* Host copies (caller-allocated) of the grid: r[n_r], w_r[n_r] (weights include r^2),
+ * t[n_theta] (= cos theta, ascending), w_t[n_theta], phi[n_phi]. Any pointer may be NULL. */
+cs_status cs_grid(const cs_ctx* ctx, double* r, double* w_r, double* t, double* w_t,
+                  double* phi);
+
+/* Host copy of the kinetic diagonal 1/2 Lambda_alpha, length d (Sec. 2.2.4). */
+cs_status cs_kinetic(const cs_ctx* ctx, double* half_lambda);
+
+/* Host copy of the Bessel zeros z[l * nmax + n], (lmax+1) x nmax values. */
+cs_status cs_bessel_zeros(const cs_ctx* ctx, double* z);
+
+/* ------------------------------------------------------------------ operator set-up */
+
+/* Set the effective potential V_eff (Sec. 2.2.3 eq. lin_eigen), given on the grid as a
+ * DEVICE array of N_r * N_theta * N_phi doubles, layout [k][j][q]. The context stores
+ * W * V (quadrature weights folded in) in FP64 and FP32. Enqueued on `stream`; the caller
+ * may reuse v_grid once the stream has passed this call. */
+cs_status cs_set_potential(cs_ctx* ctx, const double* v_grid, cs_stream stream);
+
+/* Non-local Kleinman-Bylander part (Sec. 2.3.2): n_p rank-one projectors h_i p_i (x) p_i.
+ * p_coef: DEVICE, d x n_p column-major (ld = d), the projector coefficients in this
+ * basis (for grid values use cs_forward_transform first). h: HOST, n_p couplings.
+ * The context copies both (FP64 and FP32). n_p = 0 removes the projectors. */
+cs_status cs_set_projectors(cs_ctx* ctx, int n_p, const double* p_coef, const double* h,
+                            cs_stream stream);
+
+/* Forward basis transform (Sec. 2.2.2 eqs. Ar_lm, Arlm_to_coeff) of n grid functions:
+ * g: DEVICE [n][N_r][N_theta][N_phi] doubles; coef: DEVICE d x n column-major with
+ * leading dimension ld >= d; coef = B^T diag(W) g. work: DEVICE, at least
+ * cs_workspace_bytes(ctx, n, CS_FP64) bytes. */
+cs_status cs_forward_transform(cs_ctx* ctx, int n, const double* g, double* coef, long long ld,
+                               void* work, cs_stream stream);
+
+/* Inverse basis transform (Sec. 2.2.2 eq. G_lmr and the inverse spherical harmonic
+ * transform): f[n][N_r][N_theta][N_phi] = (B coef)^T. Arguments as above. */
+cs_status cs_inverse_transform(cs_ctx* ctx, int n, const double* coef, long long ld, double* f,
+                               void* work, cs_stream stream);
+
+/* Device workspace (bytes) needed by cs_apply_H / cs_cheb_filter / transforms on n_s
+ * columns at precision `prec`, and by cs_rayleigh_ritz / cs_chfsi (their FP64 needs are
+ * included for prec = CS_FP64; for CS_FP32 the FP32 filter buffers are added). */
+cs_status cs_workspace_bytes(const cs_ctx* ctx, int n_s, cs_precision prec, size_t* bytes);
+
+/* ------------------------------------------------------------------ hot path */
+
+/* HX = H X for a block of n_s states (Sec. 2.2.4 eq. matvec_final): per-l radial
+ * synthesis GEMMs (eq. G_lmr), per-radial-node inverse and forward spherical harmonic
+ * transforms with the pointwise W*V product, per-l radial analysis GEMMs (eq.
+ * Arlm_to_coeff), plus 1/2 Lambda X and the projector pair. X, HX: DEVICE, d x n_s,
+ * leading dimension ld, element type per prec; X and HX must not overlap.
+ * Requires cs_set_potential first (CS_ERR_STATE otherwise). */
+cs_status cs_apply_H(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
+                     cs_precision prec, void* work, cs_stream stream);
+
+/* In place: X <- p_m(H) X = T_m((H - c)/e) X / T_m((a0 - c)/e), c = (a+b)/2,
+ * e = (b-a)/2, by the scaled three-term recurrence (Sec. 3.2.1; degree m = `degree`
+ * >= 1 H.X products). Requires a < b and a0 < a. X: DEVICE d x n_s, ld, type per prec. */
+cs_status cs_cheb_filter(cs_ctx* ctx, int n_s, void* X, long long ld, int degree, double a,
+                         double b, double a0, cs_precision prec, void* work,
+                         cs_stream stream);
+
+/* Cholesky-QR with column scaling (Sec. 3.1.1, 3.2.1), applied twice: X <- X D R^{-1}
+ * with D = diag(X^T X)^(-1/2), D X^T X D = R^T R. X: DEVICE FP64 d x n_s (ld).
+ * Synchronising. CS_ERR_CHOLESKY if a pivot is not positive. */
+cs_status cs_cholqr(cs_ctx* ctx, int n_s, double* X, long long ld, void* work,
+                    cs_stream stream);
+
+/* Rayleigh-Ritz on an orthonormal FP64 block (Sec. 3.2.1): HX = H X (FP64), Hs =
+ * sym(X^T H X) = Q Theta Q^T (Jacobi eigensolver on the device), X <- X Q, and the
+ * residual norms ||H x_i - theta_i x_i||_2. theta, resid: DEVICE n_s doubles (ascending
+ * theta). If HX_out is not NULL it receives H X Q (DEVICE d x n_s, ld). Synchronising. */
+cs_status cs_rayleigh_ritz(cs_ctx* ctx, int n_s, double* X, long long ld, double* theta,
+                           double* resid, double* HX_out, void* work, cs_stream stream);
+
+/* k-step Lanczos from the DEVICE vector v0 (length d, FP64, not modified): *b = largest
+ * Ritz value + |beta_k| (upper bound of the spectrum for the filter), *theta_min =
+ * smallest Ritz value. k <= 64. Synchronising. */
+cs_status cs_lanczos_bound(cs_ctx* ctx, int k, const double* v0, double* b, double* theta_min,
+                           void* work, cs_stream stream);
+
+/* ChFSI loop (Sec. 3.2.1): Lanczos bounds from v0, then [filter (precision prec) ->
+ * Cholesky-QR (FP64) -> Rayleigh-Ritz (FP64)] until the largest residual of the n_want
+ * lowest Ritz pairs is <= tol or max_iter iterations. X: DEVICE FP64 d x n_s (ld), the
+ * initial block on entry, the Ritz vectors on exit. theta, resid: DEVICE n_s doubles.
+ * *iters receives the iteration count. First pass: a0 = smallest Lanczos Ritz value,
+ * a = a0 + (b - a0)/10; later passes: a = largest Ritz value, a0 = smallest.
+ * Synchronising. CS_ERR_NOT_CONVERGED if max_iter is reached (results still written). */
+cs_status cs_chfsi(cs_ctx* ctx, int n_s, int n_want, double* X, long long ld, int degree,
+                   double tol, int max_iter, cs_precision prec, const double* v0,
+                   double* theta, double* resid, int* iters, void* work, cs_stream stream);
+
+/* One ChFSI iteration (Sec. 3.2.1) with given filter bounds: X <- p_m(H) X (precision prec),
+ * Cholesky-QR (FP64), Rayleigh-Ritz (FP64) with residual norms. X: DEVICE FP64 d x n_s
+ * (ld), orthonormal or not on entry, Ritz vectors on exit. theta, resid: DEVICE n_s
+ * doubles. Synchronising (reads the factorisation status back). */
+cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degree, double a,
+                        double b, double a0, cs_precision prec, double* theta, double* resid,
+                        void* work, cs_stream stream);
+
+/* Measurement hooks: between cs_profile_begin and cs_profile_end the library records a
+ * CUDA event pair on the launching stream around every kernel it launches on ctx.
+ * cs_profile_end synchronises, and writes per kernel class the summed device time (ms[4])
+ * and the launch count (launches[4]); classes: 0 radial synthesis GEMMs, 1 angular
+ * transforms (per radial node), 2 radial analysis GEMMs with the fused epilogue, 3 dense
+ * FP64 linear algebra and conversions. */
+cs_status cs_profile_begin(cs_ctx* ctx);
+cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
+
+/* Last error message of the context (static storage inside ctx; "" if none). A NULL ctx
+ * returns the message of the last failed cs_basis_init on this thread. */
+const char* cs_last_error(const cs_ctx* ctx);
+
+/* Number of kernels this library has launched on `ctx` since it was created. */
+long long cs_launch_count(const cs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLUSTERSPEC_CS_H */

@@ -1,0 +1,351 @@
+"""Python binding of libclusterspec: the ChFSI hot path of the spherical spectral
+Kohn-Sham method on a GB300 (sm_103a).
+
+Argument marshalling only: every numerical step runs in the library's CUDA kernels
+(include/cs.h documents each entry point). PyTorch supplies device memory and streams.
+There is no CPU fallback: importing this package raises if the compiled library is
+missing, and every call raises RuntimeError on a non-zero cs_status.
+
+Blocks of states are torch tensors of shape (n_s, ld) (row i = state i), i.e. the
+column-major d x n_s matrices of the C ABI with leading dimension ld = tensor.stride(0);
+only the first d entries of each row are used.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch  # loads the CUDA runtime that the library links against
+
+__all__ = [
+    "CS_FP64", "CS_FP32", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
+    "CsError", "Context", "cs_basis_init", "cs_basis_free", "cs_basis_dims", "cs_grid",
+    "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
+    "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
+    "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
+    "cs_chfsi_step", "cs_profile_begin", "cs_profile_end",
+    "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libclusterspec.so")
+
+CS_FP64, CS_FP32 = 0, 1
+CS_RADIAL_GAUSS_LEGENDRE, CS_RADIAL_GAUSS_JACOBI_R2 = 0, 1
+_STATUS = {0: "CS_OK", 1: "CS_ERR_ARG", 2: "CS_ERR_ALLOC", 3: "CS_ERR_CUDA",
+           4: "CS_ERR_STATE", 5: "CS_ERR_CHOLESKY", 6: "CS_ERR_NOT_CONVERGED",
+           7: "CS_ERR_TIMEOUT", 8: "CS_ERR_NUMERIC"}
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"libclusterspec.so not found at {_LIB_PATH}; build it with "
+        "`python -m paper_1404_3773_gb300.build` (there is no CPU fallback)")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+
+class _Quad(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("radial", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+_d = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "cs_basis_init": (_i, [_d, _i, _i, ctypes.POINTER(_Quad), _i, ctypes.POINTER(_vp)]),
+    "cs_basis_free": (_i, [_vp]),
+    "cs_basis_dims": (_i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                           ctypes.POINTER(_i)]),
+    "cs_grid": (_i, [_vp, _dp, _dp, _dp, _dp, _dp]),
+    "cs_kinetic": (_i, [_vp, _dp]),
+    "cs_bessel_zeros": (_i, [_vp, _dp]),
+    "cs_set_potential": (_i, [_vp, _vp, _vp]),
+    "cs_set_projectors": (_i, [_vp, _i, _vp, _dp, _vp]),
+    "cs_forward_transform": (_i, [_vp, _i, _vp, _vp, _ll, _vp, _vp]),
+    "cs_inverse_transform": (_i, [_vp, _i, _vp, _ll, _vp, _vp, _vp]),
+    "cs_workspace_bytes": (_i, [_vp, _i, _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_apply_H": (_i, [_vp, _i, _vp, _vp, _ll, _i, _vp, _vp]),
+    "cs_cheb_filter": (_i, [_vp, _i, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp]),
+    "cs_cholqr": (_i, [_vp, _i, _vp, _ll, _vp, _vp]),
+    "cs_rayleigh_ritz": (_i, [_vp, _i, _vp, _ll, _vp, _vp, _vp, _vp, _vp]),
+    "cs_lanczos_bound": (_i, [_vp, _i, _vp, _dp, _dp, _vp, _vp]),
+    "cs_chfsi": (_i, [_vp, _i, _i, _vp, _ll, _i, _d, _i, _i, _vp, _vp, _vp,
+                      ctypes.POINTER(_i), _vp, _vp]),
+    "cs_chfsi_step": (_i, [_vp, _i, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp, _vp, _vp]),
+    "cs_profile_begin": (_i, [_vp]),
+    "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
+    "cs_last_error": (ctypes.c_char_p, [_vp]),
+    "cs_launch_count": (_ll, [_vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def exported_symbols() -> list:
+    return list(_SIGS)
+
+
+class CsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """Owns one cs_ctx (tables of a basis on a quadrature grid, bound to one device)."""
+
+    def __init__(self, handle: int, device: int):
+        self._h = ctypes.c_void_p(handle)
+        self.device = device
+        d = _ll()
+        nr, nt, nph = _i(), _i(), _i()
+        _lib.cs_basis_dims(self._h, ctypes.byref(d), ctypes.byref(nr), ctypes.byref(nt),
+                           ctypes.byref(nph))
+        self.d, self.n_r, self.n_theta, self.n_phi = d.value, nr.value, nt.value, nph.value
+        self._ws = {}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, status: int):
+        if status != 0:
+            raise CsError(status, _lib.cs_last_error(self._h).decode())
+
+    def workspace(self, n_s: int, precision: int = CS_FP64) -> torch.Tensor:
+        """A cached device workspace of cs_workspace_bytes(n_s, precision) bytes."""
+        nbytes = cs_workspace_bytes(self, n_s, precision)
+        key = (self.device,)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._ws[key] = ws
+        return ws
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.cs_basis_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------- ABI mirrors
+def cs_basis_init(R: float, lmax: int, nmax: int, n_r: int, n_theta: int, n_phi: int,
+                  radial: int = CS_RADIAL_GAUSS_LEGENDRE, cuda_device: int = 0) -> Context:
+    q = _Quad(n_r, n_theta, n_phi, radial)
+    h = _vp()
+    st = _lib.cs_basis_init(float(R), int(lmax), int(nmax), ctypes.byref(q), int(cuda_device),
+                            ctypes.byref(h))
+    if st != 0:
+        raise CsError(st, _lib.cs_last_error(None).decode())
+    return Context(h.value, cuda_device)
+
+
+def cs_basis_free(ctx: Context):
+    ctx.close()
+
+
+def cs_basis_dims(ctx: Context):
+    return ctx.d, ctx.n_r, ctx.n_theta, ctx.n_phi
+
+
+def cs_grid(ctx: Context):
+    """Host copies (numpy float64) of r, w_r, t, w_t, phi."""
+    import numpy as np
+    r, wr = np.empty(ctx.n_r), np.empty(ctx.n_r)
+    t, wt = np.empty(ctx.n_theta), np.empty(ctx.n_theta)
+    ph = np.empty(ctx.n_phi)
+    c = lambda a: a.ctypes.data_as(_dp)  # noqa: E731
+    ctx.check(_lib.cs_grid(ctx.handle, c(r), c(wr), c(t), c(wt), c(ph)))
+    return r, wr, t, wt, ph
+
+
+def cs_kinetic(ctx: Context):
+    import numpy as np
+    out = np.empty(ctx.d)
+    ctx.check(_lib.cs_kinetic(ctx.handle, out.ctypes.data_as(_dp)))
+    return out
+
+
+def cs_bessel_zeros(ctx: Context, lmax: int, nmax: int):
+    import numpy as np
+    out = np.empty((lmax + 1) * nmax)
+    ctx.check(_lib.cs_bessel_zeros(ctx.handle, out.ctypes.data_as(_dp)))
+    return out.reshape(lmax + 1, nmax)
+
+
+def cs_set_potential(ctx: Context, v_grid: torch.Tensor, stream=None):
+    assert v_grid.dtype == torch.float64 and v_grid.is_cuda and v_grid.is_contiguous()
+    assert v_grid.numel() == ctx.n_r * ctx.n_theta * ctx.n_phi
+    ctx.check(_lib.cs_set_potential(ctx.handle, _ptr(v_grid), _stream_ptr(stream)))
+
+
+def cs_set_projectors(ctx: Context, p_coef: torch.Tensor | None, h, stream=None):
+    """p_coef: (n_p, d) float64 device tensor (rows = projector coefficient vectors)."""
+    import numpy as np
+    if p_coef is None or p_coef.shape[0] == 0:
+        ctx.check(_lib.cs_set_projectors(ctx.handle, 0, None, None, _stream_ptr(stream)))
+        return
+    assert p_coef.dtype == torch.float64 and p_coef.is_contiguous() and p_coef.shape[1] == ctx.d
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    ctx.check(_lib.cs_set_projectors(ctx.handle, p_coef.shape[0], _ptr(p_coef),
+                                     hh.ctypes.data_as(_dp), _stream_ptr(stream)))
+
+
+def _check_block(ctx: Context, X: torch.Tensor, dtype):
+    assert X.is_cuda and X.dtype == dtype and X.dim() == 2 and X.stride(1) == 1
+    assert X.shape[1] >= ctx.d
+    return X.shape[0], X.stride(0)
+
+
+def cs_forward_transform(ctx: Context, g: torch.Tensor, coef: torch.Tensor, work=None,
+                         stream=None):
+    """g: (n, n_r, n_theta, n_phi) float64; coef: (n, ld) float64 (output)."""
+    n, ld = _check_block(ctx, coef, torch.float64)
+    assert g.is_contiguous() and g.dtype == torch.float64 and g.shape[0] == n
+    work = ctx.workspace(n) if work is None else work
+    ctx.check(_lib.cs_forward_transform(ctx.handle, n, _ptr(g), _ptr(coef), ld, _ptr(work),
+                                        _stream_ptr(stream)))
+
+
+def cs_inverse_transform(ctx: Context, coef: torch.Tensor, f: torch.Tensor, work=None,
+                         stream=None):
+    n, ld = _check_block(ctx, coef, torch.float64)
+    assert f.is_contiguous() and f.dtype == torch.float64 and f.shape[0] == n
+    work = ctx.workspace(n) if work is None else work
+    ctx.check(_lib.cs_inverse_transform(ctx.handle, n, _ptr(coef), ld, _ptr(f), _ptr(work),
+                                        _stream_ptr(stream)))
+
+
+def cs_workspace_bytes(ctx: Context, n_s: int, precision: int = CS_FP64) -> int:
+    out = ctypes.c_size_t()
+    ctx.check(_lib.cs_workspace_bytes(ctx.handle, int(n_s), int(precision), ctypes.byref(out)))
+    return out.value
+
+
+def _dtype(precision):
+    return torch.float64 if precision == CS_FP64 else torch.float32
+
+
+def cs_apply_H(ctx: Context, X: torch.Tensor, HX: torch.Tensor, precision: int = CS_FP64,
+               work=None, stream=None):
+    n_s, ld = _check_block(ctx, X, _dtype(precision))
+    assert HX.shape == X.shape and HX.stride() == X.stride() and HX.dtype == X.dtype
+    work = ctx.workspace(n_s, precision) if work is None else work
+    ctx.check(_lib.cs_apply_H(ctx.handle, n_s, _ptr(X), _ptr(HX), ld, int(precision),
+                              _ptr(work), _stream_ptr(stream)))
+
+
+def cs_cheb_filter(ctx: Context, X: torch.Tensor, degree: int, a: float, b: float, a0: float,
+                   precision: int = CS_FP64, work=None, stream=None):
+    n_s, ld = _check_block(ctx, X, _dtype(precision))
+    work = ctx.workspace(n_s, precision) if work is None else work
+    ctx.check(_lib.cs_cheb_filter(ctx.handle, n_s, _ptr(X), ld, int(degree), float(a),
+                                  float(b), float(a0), int(precision), _ptr(work),
+                                  _stream_ptr(stream)))
+
+
+def cs_cholqr(ctx: Context, X: torch.Tensor, work=None, stream=None):
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    work = ctx.workspace(n_s) if work is None else work
+    ctx.check(_lib.cs_cholqr(ctx.handle, n_s, _ptr(X), ld, _ptr(work), _stream_ptr(stream)))
+
+
+def cs_rayleigh_ritz(ctx: Context, X: torch.Tensor, theta: torch.Tensor, resid: torch.Tensor,
+                     HX_out: torch.Tensor | None = None, work=None, stream=None):
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    work = ctx.workspace(n_s) if work is None else work
+    ctx.check(_lib.cs_rayleigh_ritz(ctx.handle, n_s, _ptr(X), ld, _ptr(theta), _ptr(resid),
+                                    _ptr(HX_out), _ptr(work), _stream_ptr(stream)))
+
+
+def cs_lanczos_bound(ctx: Context, v0: torch.Tensor, k: int = 10, work=None, stream=None):
+    assert v0.is_cuda and v0.dtype == torch.float64 and v0.numel() >= ctx.d
+    work = ctx.workspace(1) if work is None else work
+    b, tmin = _d(), _d()
+    ctx.check(_lib.cs_lanczos_bound(ctx.handle, int(k), _ptr(v0), ctypes.byref(b),
+                                    ctypes.byref(tmin), _ptr(work), _stream_ptr(stream)))
+    return b.value, tmin.value
+
+
+def cs_chfsi(ctx: Context, X: torch.Tensor, n_want: int, degree: int, v0: torch.Tensor,
+             theta: torch.Tensor, resid: torch.Tensor, tol: float = 1e-8, max_iter: int = 50,
+             precision: int = CS_FP64, work=None, stream=None, raise_not_converged=True) -> int:
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    work = ctx.workspace(n_s, precision) if work is None else work
+    it = _i()
+    st = _lib.cs_chfsi(ctx.handle, n_s, int(n_want), _ptr(X), ld, int(degree), float(tol),
+                       int(max_iter), int(precision), _ptr(v0), _ptr(theta), _ptr(resid),
+                       ctypes.byref(it), _ptr(work), _stream_ptr(stream))
+    if st == 6 and not raise_not_converged:
+        return it.value
+    ctx.check(st)
+    return it.value
+
+
+def cs_chfsi_step(ctx: Context, X: torch.Tensor, degree: int, a: float, b: float, a0: float,
+                  theta: torch.Tensor, resid: torch.Tensor, precision: int = CS_FP64,
+                  work=None, stream=None):
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    work = ctx.workspace(n_s, precision) if work is None else work
+    ctx.check(_lib.cs_chfsi_step(ctx.handle, n_s, _ptr(X), ld, int(degree), float(a), float(b),
+                                 float(a0), int(precision), _ptr(theta), _ptr(resid),
+                                 _ptr(work), _stream_ptr(stream)))
+
+
+def cs_profile_begin(ctx: Context):
+    ctx.check(_lib.cs_profile_begin(ctx.handle))
+
+
+def cs_profile_end(ctx: Context):
+    """Returns (ms[4], launches[4]) per kernel class: radial synthesis, angular, radial
+    analysis + epilogue, dense linear algebra."""
+    ms = (ctypes.c_double * 4)()
+    n = (_ll * 4)()
+    ctx.check(_lib.cs_profile_end(ctx.handle, ms, n))
+    return list(ms), list(n)
+
+
+def cs_last_error(ctx: Context | None) -> str:
+    return _lib.cs_last_error(None if ctx is None else ctx.handle).decode()
+
+
+def cs_launch_count(ctx: Context) -> int:
+    return int(_lib.cs_launch_count(ctx.handle))
+
+
+def grid_points(ctx: Context):
+    """Cartesian coordinates (N_g, 3) of the context's quadrature grid in [k][j][q] order,
+    for evaluating a potential or projector functions on it (host, numpy)."""
+    import numpy as np
+    r, _, t, _, ph = cs_grid(ctx)
+    st = np.sqrt(1.0 - t * t)
+    x = r[:, None, None] * st[None, :, None] * np.cos(ph)[None, None, :]
+    y = r[:, None, None] * st[None, :, None] * np.sin(ph)[None, None, :]
+    z = r[:, None, None] * t[None, :, None] * np.ones_like(ph)[None, None, :]
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)

@@ -1,0 +1,73 @@
+// Internal declarations of libclusterspec (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cs.h"
+
+namespace cs {
+
+// ---------------------------------------------------------------- host tables (setup.cpp)
+struct HostTables {
+  double R = 0;
+  int lmax = 0, L = 0, N = 0;
+  long long d = 0;
+  int n_r = 0, n_theta = 0, n_phi = 0, radial = 0;
+  std::vector<double> z;        // [l][n]            Bessel zeros
+  std::vector<double> r, w_r;   // [k]               radial nodes, weights (incl. r^2)
+  std::vector<double> t, w_t;   // [j]               Gauss nodes in cos(theta), ascending
+  std::vector<double> phi;      // [q]
+  std::vector<double> rad;      // [l][k][n]         R_ln(r_k)
+  std::vector<double> theta;    // [j][m][l-m]       Theta_lm(t_j) * (m>0 ? sqrt2 : 1), packed
+  std::vector<double> half_lambda;  // [alpha]
+};
+
+// Builds every table on the host. Returns an empty string on success, else a message.
+std::string build_host_tables(double R, int lmax, int nmax, const cs_quadrature& q,
+                              HostTables& out);
+
+// packed offset of (m, l) inside one theta row: sum_{m'<m} (L - m') + (l - m)
+__host__ __device__ inline int theta_off(int L, int m) { return m * L - (m * (m - 1)) / 2; }
+__host__ __device__ inline int theta_row_len(int L) { return L * (L + 1) / 2; }
+
+// ---------------------------------------------------------------- device-side context
+template <typename T>
+struct DevTables {
+  T* rad = nullptr;        // [l][k][n]
+  T* theta = nullptr;      // [j][packed (m,l)], rows 0 .. ceil(n_theta/2)-1
+  T* trig = nullptr;       // [2][lmax+1][Q4+1]: cos(m phi_q), sin(m phi_q), q <= Q4
+  T* wv = nullptr;         // [k][j][q] W * V
+  T* wkj = nullptr;        // [k][j] w_r w_t 2 pi / n_phi
+  T* half_lambda = nullptr;// [alpha]
+  T* pcoef = nullptr;      // [p][alpha] (d x n_p column-major)
+  T* h = nullptr;          // [p]
+};
+
+}  // namespace cs
+
+struct cs_ctx {
+  cs::HostTables host;
+  int device = -1;
+  bool has_device = false;
+  bool has_potential = false;
+  int n_p = 0;
+  int Q4 = 0;              // floor(n_phi / 4): folded phi range q = 0 .. Q4
+  cs::DevTables<double> d64;
+  cs::DevTables<float> d32;
+  double* w_r_dev = nullptr; // radial weights (for forward transforms of grid data)
+  std::string err;
+  long long launches = 0;
+  // measurement hooks (cs_profile_begin / cs_profile_end)
+  bool prof = false;
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> event_pool;
+};

@@ -1,0 +1,96 @@
+// Launch interfaces of the H.X and dense linear-algebra kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace cs {
+
+enum { EP_PLAIN = 0, EP_APPLY = 1, EP_CHEB = 2 };
+enum { ANG_FULL = 0, ANG_SYNTH = 1, ANG_ANAL = 2 };
+
+// Epilogue of the radial analysis GEMM, for element (alpha, s):
+//   EP_PLAIN : out = Z
+//   EP_APPLY : out = 1/2 Lambda X + Z (+ kb)
+//   EP_CHEB  : out = cA (1/2 Lambda X + Z (+ kb) - cshift X) - cB Yprev   (Yprev may be out)
+template <typename T>
+struct Epilogue {
+  int mode = EP_PLAIN;
+  T* out = nullptr;
+  const T* X = nullptr;
+  const T* Yprev = nullptr;
+  long long ld = 0;      // leading dimension of X
+  long long ld_out = 0;  // leading dimension of out and Yprev
+  const T* half_lambda = nullptr;
+  const T* kb = nullptr;
+  long long kb_ld = 0;
+  T cA = T(0), cB = T(0), cshift = T(0);
+};
+
+template <typename T>
+struct AngArgs {
+  int L, n_r, n_theta, n_phi, Q4, S;
+  const T* theta;  // [ceil(Nt/2)][L(L+1)/2]
+  const T* trig;   // [2][L][Q4+1]
+  const T* wv;     // [k][j][q]
+  const T* wkj;    // [k][j] = w_r w_t 2 pi / Nphi (forward transforms of grid data)
+};
+
+template <typename T>
+int pick_states_per_cta(int L, int n_phi, int Q4);
+
+template <typename T>
+cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T* gin,
+                           cudaStream_t stream);
+template <typename T>
+cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,
+                                int n_r, int S, cudaStream_t stream);
+template <typename T>
+cudaError_t launch_radial_anal(const T* G, const T* rad, int L, int N, int n_r, int S,
+                               const Epilogue<T>& ep, cudaStream_t stream);
+
+// ---------------------------------------------------------------- dense FP64 pieces
+// C (na x nb, column-major, ldc) = A^T B, A: d x na (lda), B: d x nb (ldb), split over d
+// into chunks whose partial products land in `partial` (gram_partial_elems doubles) and
+// are then summed in a fixed order (deterministic).
+size_t gram_partial_elems(long long d, int na, int nb);
+cudaError_t launch_gram(const double* A, long long lda, const double* B, long long ldb,
+                        long long d, int na, int nb, double* C, int ldc, double* partial,
+                        cudaStream_t stream);
+// C (d x n, ldc) = alpha * A (d x k, lda) * Q (k x n, ldq) + beta * C. A must not overlap C.
+cudaError_t launch_gemm_nn(const double* A, long long lda, const double* Q, int ldq,
+                           long long d, int k, int n, double alpha, double beta, double* C,
+                           long long ldc, cudaStream_t stream);
+// From the Gram matrix M (n x n): U = D R^{-1}, D = diag(M)^(-1/2), D M D = R^T R.
+// work: n*n + n doubles. status[0] = 0 ok, else 1 + index of the failing pivot.
+cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
+                                 cudaStream_t stream);
+// Symmetric eigensolve of sym(A) (n x n, lda = n): theta ascending, V (n x n) columns.
+// work: n*n + 2n doubles. status[0] = sweeps used (negative if not converged).
+cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, double* work,
+                              int* status, cudaStream_t stream);
+// resid[i] = || HX[:, i] - theta[i] X[:, i] ||_2
+cudaError_t launch_residuals(const double* X, long long ldx, const double* HX, long long ldh,
+                             long long d, int n, const double* theta, double* resid,
+                             cudaStream_t stream);
+// y (d x n, ldy) = x (d x n, ldx) converted
+cudaError_t launch_convert_f64_to_f32(const double* x, long long ldx, float* y, long long ldy,
+                                      long long d, int n, cudaStream_t stream);
+cudaError_t launch_convert_f32_to_f64(const float* x, long long ldx, double* y, long long ldy,
+                                      long long d, int n, cudaStream_t stream);
+// copy of a d x n block between leading dimensions
+template <typename T>
+cudaError_t launch_copy_block(const T* x, long long ldx, T* y, long long ldy, long long d,
+                              int n, cudaStream_t stream);
+// y = x / sqrt(*nrm2)  (length d)
+cudaError_t launch_scale_inv_sqrt(const double* x, double* y, long long d, const double* nrm2,
+                                  cudaStream_t stream);
+// W V table: wv64[kj * n_phi + q] = wkj[kj] * v[kj * n_phi + q]; wv32 = (float) wv64
+cudaError_t launch_weighted_potential(const double* v, const double* wkj, int n_kj, int n_phi,
+                                      double* wv64, float* wv32, cudaStream_t stream);
+// Lanczos tridiagonal T (k x k) from alpha[k] and the squared off-diagonals beta2[k-1]
+cudaError_t launch_build_tridiag(const double* alpha, const double* beta2, int k, double* T,
+                                 cudaStream_t stream);
+
+}  // namespace cs

@@ -1,0 +1,143 @@
+"""GPU parity of H.X and the basis transforms against the FP64 oracle, through the C ABI.
+
+Bar (FP64): ||HX_gpu - HX_oracle||_F / ||HX_oracle||_F <= 1e-11 and, per column,
+max |diff| / ||HX_oracle[:, s]||_2 <= 1e-11. FP32: the same norms <= 2e-5 (reported, the
+FP32 path has no exact counterpart)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import make_ctx, need_gpu, oracle_H, register, rel_errors, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL32 = 2e-5
+
+CASES = {
+    # name: workload (sizes chosen so the oracle finishes in seconds; several tiles and a
+    # ragged tail of states per angular tile)
+    "small_ragged": W.small_cluster(lmax=6, nmax=8, n_r=20, n_theta=14, n_phi=28, n_s=13),
+    "ho_l10": W.harmonic_oscillator_ball(),
+    "odd_theta_phi_not_mult4": W.small_cluster(lmax=5, nmax=7, n_r=15, n_theta=11, n_phi=18,
+                                               n_s=3, seed=7101),
+    "lmax0_single_state": W.small_cluster(lmax=0, nmax=9, n_r=12, n_theta=1, n_phi=2, n_s=1,
+                                          seed=7201),
+    "gauss_jacobi": W.Workload("gj_small", R=7.0, lmax=7, nmax=10, n_r=24, n_theta=16, n_phi=30,
+                               radial_rule="gauss_jacobi_r2", n_s=9, degree=6,
+                               potential="erf_cluster", natoms=3, atom_seed=7301, r_place=3.0,
+                               min_sep=2.0, x_seed=7302),
+}
+for _w in CASES.values():
+    register(_w)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_apply_H_fp64_matches_oracle(case):
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, ld=ctx.d + 3)  # leading dimension > d
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_FP64)
+    torch.cuda.synchronize()
+    got = to_host(HXd, ctx.d)
+    fro, col = rel_errors(got, ref)
+    assert fro <= TOL64 and col <= TOL64, (fro, col)
+    assert torch.all(HXd[:, ctx.d:] == 0)  # padding untouched
+
+
+@pytest.mark.parametrize("case", ["small_ragged", "ho_l10"])
+def test_apply_H_fp32_error(case):
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, dtype=torch.float32)
+    HXd = torch.empty_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_FP32)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    assert fro <= TOL32 and col <= 10 * TOL32, (fro, col)
+
+
+def test_apply_H_erf32_full_size():
+    """The 32-atom cluster at full size (d = 46128, 80 states, 96 x 60 x 120 grid), in the
+    configuration the benchmark times."""
+    torch, cs = need_gpu()
+    w = W.erf_cluster_32()
+    register(w)
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_FP64)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    assert fro <= TOL64 and col <= TOL64, (fro, col)
+    X32 = Xd.float()
+    HX32 = torch.empty_like(X32)
+    cs.cs_apply_H(ctx, X32, HX32, cs.CS_FP32)
+    torch.cuda.synchronize()
+    fro32, col32 = rel_errors(to_host(HX32, ctx.d), ref)
+    assert fro32 <= TOL32, fro32
+
+
+def test_transforms_match_oracle():
+    torch, cs = need_gpu()
+    w = CASES["small_ragged"]
+    ctx = make_ctx(w)
+    Hh = oracle_H(w.name)
+    b = Hh.basis
+    X = w.x_block()
+    f_ref = b.inverse_transform(X)  # (N_r, N_t, N_p, S)
+    Xd = to_dev(X)
+    f = torch.empty((X.shape[1], ctx.n_r, ctx.n_theta, ctx.n_phi), dtype=torch.float64,
+                    device="cuda")
+    cs.cs_inverse_transform(ctx, Xd, f)
+    torch.cuda.synchronize()
+    got = np.moveaxis(f.cpu().numpy(), 0, -1)
+    assert np.max(np.abs(got - f_ref)) <= 1e-12 * np.abs(f_ref).max()
+    g = W.gaussian(55, b.n_grid * 4).reshape(4, b.n_r, b.n_theta, b.n_phi)
+    c_ref = b.forward_transform(np.moveaxis(g, 0, -1))
+    coef = torch.empty((4, ctx.d), dtype=torch.float64, device="cuda")
+    cs.cs_forward_transform(ctx, torch.tensor(g, device="cuda"), coef)
+    torch.cuda.synchronize()
+    got = coef.cpu().numpy().T
+    assert np.max(np.abs(got - c_ref)) <= 1e-12 * np.abs(c_ref).max()
+
+
+def test_zero_potential_is_kinetic_diagonal_exactly():
+    torch, cs = need_gpu()
+    w = W.small_cluster(potential="zero", n_s=5)
+    ctx = make_ctx(w)
+    X = w.x_block()
+    Xd = to_dev(X)
+    HXd = torch.empty_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_FP64)
+    torch.cuda.synchronize()
+    hl = cs.cs_kinetic(ctx)
+    assert np.array_equal(to_host(HXd, ctx.d), hl[:, None] * X)
+
+
+def test_apply_before_potential_is_state_error():
+    torch, cs = need_gpu()
+    w = CASES["small_ragged"]
+    ctx = make_ctx(w, with_potential=False)
+    Xd = to_dev(w.x_block())
+    with pytest.raises(cs.CsError, match="CS_ERR_STATE"):
+        cs.cs_apply_H(ctx, Xd, torch.empty_like(Xd))
+
+
+def test_launch_count_advances():
+    torch, cs = need_gpu()
+    w = CASES["small_ragged"]
+    ctx = make_ctx(w)
+    Xd = to_dev(w.x_block())
+    n0 = cs.cs_launch_count(ctx)
+    cs.cs_apply_H(ctx, Xd, torch.empty_like(Xd))
+    assert cs.cs_launch_count(ctx) - n0 == 3

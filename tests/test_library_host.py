@@ -1,0 +1,85 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that include/cs.h
+declares, builds its host tables (compared here with the oracle's, which share no code
+with them), and rejects bad arguments and device calls on a host-only context."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    cs = pytest.importorskip("paper_1404_3773_gb300")
+    return cs
+
+
+def _declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "cs.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", hdr)))
+
+
+def test_header_symbols_exported():
+    cs = _lib()
+    lib = ctypes.CDLL(cs.library_path())
+    names = _declared_symbols()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding mirrors every declared entry point under the same name
+    for n in names:
+        assert hasattr(cs, n), n
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_host_tables_match_oracle(rule):
+    cs = _lib()
+    from oracle.basis import Basis
+    ctx = cs.cs_basis_init(14.0, 30, 48, 96, 60, 120, rule, -1)
+    b = Basis(14.0, 30, 48, 96, 60, 120, ["gauss_legendre", "gauss_jacobi_r2"][rule])
+    r, wr, t, wt, ph = cs.cs_grid(ctx)
+    assert np.max(np.abs(r - b.r)) < 1e-13
+    assert np.max(np.abs(wr - b.w_r) / b.w_r) < 1e-12
+    assert np.max(np.abs(t - b.t)) < 1e-15 and np.max(np.abs(wt - b.w_t)) < 1e-14
+    assert np.max(np.abs(ph - b.phi)) < 1e-15
+    z = cs.cs_bessel_zeros(ctx, 30, 48)
+    assert np.max(np.abs(z - b.z) / b.z) < 1e-14
+    hl = cs.cs_kinetic(ctx)
+    assert np.max(np.abs(hl - b.half_lambda) / b.half_lambda) < 1e-13
+    assert ctx.d == b.d == 46128
+
+
+def test_bad_arguments_rejected():
+    cs = _lib()
+    with pytest.raises(cs.CsError, match="CS_ERR_ARG"):
+        cs.cs_basis_init(8.0, 10, 16, 32, 22, 41, 0, -1)  # odd n_phi
+    with pytest.raises(cs.CsError, match="CS_ERR_ARG"):
+        cs.cs_basis_init(8.0, 10, 16, 32, 10, 42, 0, -1)  # n_theta <= lmax
+    with pytest.raises(cs.CsError, match="CS_ERR_ARG"):
+        cs.cs_basis_init(-1.0, 10, 16, 32, 22, 42, 0, -1)
+
+
+def test_device_calls_on_host_context_report_state_error():
+    cs = _lib()
+    ctx = cs.cs_basis_init(8.0, 4, 6, 12, 10, 20, 0, -1)
+    lib = ctypes.CDLL(cs.library_path())
+    lib.cs_set_potential.argtypes = [ctypes.c_void_p] * 3
+    assert lib.cs_set_potential(ctx.handle, None, None) == 4  # CS_ERR_STATE
+    assert "no device" in cs.cs_last_error(ctx)
+    lib.cs_apply_H.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.cs_apply_H(ctx.handle, 4, None, None, ctx.d, 0, None, None) == 4
+
+
+def test_workspace_bytes_grows_with_block():
+    cs = _lib()
+    ctx = cs.cs_basis_init(8.0, 10, 16, 32, 22, 42, 0, -1)
+    a = cs.cs_workspace_bytes(ctx, 8)
+    b = cs.cs_workspace_bytes(ctx, 16)
+    c = cs.cs_workspace_bytes(ctx, 16, cs.CS_FP32)
+    assert 0 < a < b < c
+    # it covers at least the radial-node intermediate, two blocks and the Lanczos basis
+    assert b >= 32 * 121 * 16 * 8 + 4 * ctx.d * 16 * 8
