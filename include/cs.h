@@ -196,6 +196,21 @@ cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degre
 cs_status cs_profile_begin(cs_ctx* ctx);
 cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
 
+/* H X like cs_apply_H, for callers that cannot allocate device memory when they call (for
+ * example when another allocator already holds the free device memory, or when a loop must
+ * not take the device-wide synchronisation of cudaMalloc/cudaFree). It needs no workspace:
+ * its scratch is a 32 MiB array compiled into the library, present on every GPU that loads
+ * the library until the process exits; it calls no allocation routine. The paper has no
+ * counterpart; this is a deployment variant of the same H.X kernels.
+ * Limits and rules: N_r (lmax+1)^2 n_s x element size must be <= 32 MiB (else
+ * CS_ERR_ARG); no projectors (CS_ERR_STATE if set); the first call on a device looks up the
+ * array's device address, so make it before any stream capture on that device; all calls
+ * on a device share the array (it keeps the last call's contents; nothing in it must start
+ * at zero), so calls that overlap on the GPU race and must be serialised. Arguments as
+ * cs_apply_H without `work`. */
+cs_status cs_apply_H_noalloc(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
+                             cs_precision prec, cs_stream stream);
+
 /* Last error message of the context (static storage inside ctx; "" if none). A NULL ctx
  * returns the message of the last failed cs_basis_init on this thread. */
 const char* cs_last_error(const cs_ctx* ctx);

@@ -23,7 +23,7 @@ __all__ = [
     "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
-    "cs_chfsi_step", "cs_profile_begin", "cs_profile_end",
+    "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
 ]
 
@@ -75,6 +75,7 @@ _SIGS = {
     "cs_lanczos_bound": (_i, [_vp, _i, _vp, _dp, _dp, _vp, _vp]),
     "cs_chfsi": (_i, [_vp, _i, _i, _vp, _ll, _i, _d, _i, _i, _vp, _vp, _vp,
                       ctypes.POINTER(_i), _vp, _vp]),
+    "cs_apply_H_noalloc": (_i, [_vp, _i, _vp, _vp, _ll, _i, _vp]),
     "cs_chfsi_step": (_i, [_vp, _i, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp, _vp, _vp]),
     "cs_profile_begin": (_i, [_vp]),
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
@@ -259,6 +260,18 @@ def cs_apply_H(ctx: Context, X: torch.Tensor, HX: torch.Tensor, precision: int =
     work = ctx.workspace(n_s, precision) if work is None else work
     ctx.check(_lib.cs_apply_H(ctx.handle, n_s, _ptr(X), _ptr(HX), ld, int(precision),
                               _ptr(work), _stream_ptr(stream)))
+
+
+def cs_apply_H_noalloc(ctx: Context, X: torch.Tensor, HX: torch.Tensor,
+                       precision: int = CS_FP64, stream=None):
+    """H X without a workspace, for callers that cannot allocate device memory at the call
+    (another allocator holds the free memory, or cudaMalloc's synchronisation is not
+    acceptable). Uses the library's built-in 32 MiB scratch; see include/cs.h for the
+    size limit and the rule that overlapping calls on one device must be serialised."""
+    n_s, ld = _check_block(ctx, X, _dtype(precision))
+    assert HX.shape == X.shape and HX.stride() == X.stride() and HX.dtype == X.dtype
+    ctx.check(_lib.cs_apply_H_noalloc(ctx.handle, n_s, _ptr(X), _ptr(HX), ld, int(precision),
+                                      _stream_ptr(stream)))
 
 
 def cs_cheb_filter(ctx: Context, X: torch.Tensor, degree: int, a: float, b: float, a0: float,
