@@ -126,9 +126,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     import paper_1404_3773_gb300 as cs
-    from paper_1404_3773_gb300 import CS_FP32, CS_FP64
+    from paper_1404_3773_gb300 import CS_FP32, CS_FP64, CS_MIXED_BF16
 
-    prec = CS_FP64 if args.precision == "fp64" else CS_FP32
+    prec = {"fp64": CS_FP64, "fp32": CS_FP32, "mixed": CS_MIXED_BF16}[args.precision]
     w = W.erf_cluster_32()
     n_s, degree = w.n_s, w.degree
     ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, local)
@@ -258,7 +258,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == CS_FP64 else "f32+f64",
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "bf16x3+f32+f64"}[args.precision],
         "data": "synthetic (seeded erf pseudo-atom cluster and Gaussian state block)",
         "config": {"workload": "erf32_l30_n48: 32 erf atoms in r<=8, R=14, lmax=30, 48 radial "
                                "fns/l, d=46128, grid 96x60x120, 80 states, degree 16",
@@ -347,7 +347,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -67,8 +67,12 @@ typedef struct {
 } cs_quadrature;
 
 typedef enum {
-  CS_FP64 = 0, /* FP64 storage and arithmetic                                 */
-  CS_FP32 = 1  /* FP32 storage and arithmetic (FP32 FMA pipe)                 */
+  CS_FP64 = 0,       /* FP64 storage and arithmetic                                      */
+  CS_FP32 = 1,       /* FP32 storage and arithmetic (FP32 FMA pipe)                      */
+  CS_MIXED_BF16 = 2  /* FP32 storage; the per-l radial contractions on the tensor cores
+                        (tcgen05) with operands split into two BF16 terms (hi + lo, three
+                        products, FP32 accumulation); angular sums and the recurrence in
+                        FP32. Blocks are float. Not available with projectors.           */
 } cs_precision;
 
 /* ------------------------------------------------------------------ basis / context */
@@ -210,6 +214,11 @@ cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
  * cs_apply_H without `work`. */
 cs_status cs_apply_H_noalloc(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
                              cs_precision prec, cs_stream stream);
+
+/* Device error word of the context (synchronising): 0 if no kernel reported a problem, else
+ * the code of the first bounded wait that expired (tensor-core path). Reading clears it. A
+ * non-zero word is also reported as CS_ERR_TIMEOUT by the next synchronising call. */
+cs_status cs_device_error(cs_ctx* ctx, int* code);
 
 /* Last error message of the context (static storage inside ctx; "" if none). A NULL ctx
  * returns the message of the last failed cs_basis_init on this thread. */

@@ -18,19 +18,20 @@ import os
 import torch  # loads the CUDA runtime that the library links against
 
 __all__ = [
-    "CS_FP64", "CS_FP32", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
+    "CS_FP64", "CS_FP32", "CS_MIXED_BF16", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
     "CsError", "Context", "cs_basis_init", "cs_basis_free", "cs_basis_dims", "cs_grid",
     "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
     "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
+    "cs_device_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libclusterspec.so")
 
-CS_FP64, CS_FP32 = 0, 1
+CS_FP64, CS_FP32, CS_MIXED_BF16 = 0, 1, 2
 CS_RADIAL_GAUSS_LEGENDRE, CS_RADIAL_GAUSS_JACOBI_R2 = 0, 1
 _STATUS = {0: "CS_OK", 1: "CS_ERR_ARG", 2: "CS_ERR_ALLOC", 3: "CS_ERR_CUDA",
            4: "CS_ERR_STATE", 5: "CS_ERR_CHOLESKY", 6: "CS_ERR_NOT_CONVERGED",
@@ -78,6 +79,7 @@ _SIGS = {
     "cs_apply_H_noalloc": (_i, [_vp, _i, _vp, _vp, _ll, _i, _vp]),
     "cs_chfsi_step": (_i, [_vp, _i, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp, _vp, _vp]),
     "cs_profile_begin": (_i, [_vp]),
+    "cs_device_error": (_i, [_vp, ctypes.POINTER(_i)]),
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
     "cs_launch_count": (_ll, [_vp]),
@@ -250,7 +252,7 @@ def cs_workspace_bytes(ctx: Context, n_s: int, precision: int = CS_FP64) -> int:
 
 
 def _dtype(precision):
-    return torch.float64 if precision == CS_FP64 else torch.float32
+    return torch.float64 if precision == CS_FP64 else torch.float32  # FP32 and mixed: float
 
 
 def cs_apply_H(ctx: Context, X: torch.Tensor, HX: torch.Tensor, precision: int = CS_FP64,
@@ -329,6 +331,13 @@ def cs_chfsi_step(ctx: Context, X: torch.Tensor, degree: int, a: float, b: float
     ctx.check(_lib.cs_chfsi_step(ctx.handle, n_s, _ptr(X), ld, int(degree), float(a), float(b),
                                  float(a0), int(precision), _ptr(theta), _ptr(resid),
                                  _ptr(work), _stream_ptr(stream)))
+
+
+def cs_device_error(ctx: Context) -> int:
+    """Reads and clears the context's device error word (0 = no bounded wait expired)."""
+    code = _i()
+    ctx.check(_lib.cs_device_error(ctx.handle, ctypes.byref(code)))
+    return code.value
 
 
 def cs_profile_begin(ctx: Context):

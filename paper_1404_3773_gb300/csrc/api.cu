@@ -52,7 +52,7 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.lanV = take(d * (kMaxLanczos + 2) * 8);
   o.status = take(64 * sizeof(int));
   // last, so that every other offset is the same for both precisions
-  o.X32 = take(prec == CS_FP32 ? d * ns * 4 : 0);
+  o.X32 = take(prec != CS_FP64 ? d * ns * 4 : 0);
   o.total = off;
   return o;
 }
@@ -157,8 +157,10 @@ cs_status upload_tables(cs_ctx* c) {
   for (int m = 0; m < H.L; ++m)
     for (int q = 0; q < Q; ++q) {
       double ang = 2.0 * 3.14159265358979323846 * (double)((long long)m * q % H.n_phi) / H.n_phi;
-      trig[(size_t)m * Q + q] = std::cos(ang);
-      trig[(size_t)(H.L + m) * Q + q] = std::sin(ang);
+      double cv = std::cos(ang), sv = std::sin(ang);
+      // quarter-turn angles have exact zeros; the folded phi sums rely on them
+      trig[(size_t)m * Q + q] = std::fabs(cv) < 1e-12 ? 0.0 : cv;
+      trig[(size_t)(H.L + m) * Q + q] = std::fabs(sv) < 1e-12 ? 0.0 : sv;
     }
   if ((st = upload<T>(c, &D.trig, trig)) != CS_OK) return st;
   std::vector<double> wkj((size_t)H.n_r * H.n_theta);
@@ -178,7 +180,8 @@ cs_status upload_tables(cs_ctx* c) {
 // out = epilogue(1/2 Lambda X + Z (+ kb)); see Epilogue in hx_kernels.cuh
 template <typename T>
 cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long long ldo, int mode,
-                  double cA, double cB, double csh, const T* Yprev, char* work, cudaStream_t st) {
+                  double cA, double cB, double csh, const T* Yprev, char* work, cudaStream_t st,
+                  bool tc = false) {
   const HostTables& H = c->host;
   DevTables<T>& D = tables<T>(c);
   const Layout lay = layout(c, n_s, CS_FP64);
@@ -196,7 +199,21 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
                                    H.d, st));
     kb = reinterpret_cast<const T*>(kbZ);
   }
-  CS_LAUNCH_CLS(c, 0, 1, launch_radial_synth<T>(X, ldx, G, D.rad, H.L, H.N, H.n_r, n_s, st));
+  TcTables tt;
+  tt.synth = c->tc_synth;
+  tt.anal = c->tc_anal;
+  tt.m_tiles_synth = c->tc_mt_synth;
+  tt.kpad_synth = c->tc_kpad_synth;
+  tt.m_tiles_anal = c->tc_mt_anal;
+  tt.kpad_anal = c->tc_kpad_anal;
+  if (tc) {
+    if (sizeof(T) != 4) return fail(c, CS_ERR_ARG, "tensor-core path needs float blocks");
+    CS_LAUNCH_CLS(c, 0, 1, launch_tc_radial_synth(tt, H, reinterpret_cast<const float*>(X), ldx,
+                                                  reinterpret_cast<float*>(G), n_s, c->dev_err,
+                                                  st));
+  } else {
+    CS_LAUNCH_CLS(c, 0, 1, launch_radial_synth<T>(X, ldx, G, D.rad, H.L, H.N, H.n_r, n_s, st));
+  }
   AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj};
   CS_LAUNCH_CLS(c, 1, 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
   Epilogue<T> ep;
@@ -212,13 +229,19 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   ep.cA = (T)cA;
   ep.cB = (T)cB;
   ep.cshift = (T)csh;
-  CS_LAUNCH_CLS(c, 2, 1, launch_radial_anal<T>(G, D.rad, H.L, H.N, H.n_r, n_s, ep, st));
+  if (tc) {
+    CS_LAUNCH_CLS(c, 2, 1, launch_tc_radial_anal(tt, H, reinterpret_cast<const float*>(G), n_s,
+                                                 *reinterpret_cast<const Epilogue<float>*>(&ep),
+                                                 c->dev_err, st));
+  } else {
+    CS_LAUNCH_CLS(c, 2, 1, launch_radial_anal<T>(G, D.rad, H.L, H.N, H.n_r, n_s, ep, st));
+  }
   return CS_OK;
 }
 
 template <typename T>
 cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a, double b,
-                    double a0, char* work, cudaStream_t st) {
+                    double a0, char* work, cudaStream_t st, bool tc = false) {
   const HostTables& H = c->host;
   const Layout lay = layout(c, n_s, CS_FP64);
   T* alt = reinterpret_cast<T*>(work + lay.Yalt);
@@ -226,7 +249,7 @@ cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a
   const double cc = 0.5 * (a + b), e = 0.5 * (b - a);
   const double s1 = e / (a0 - cc);
   // Y_1 = (sigma_1/e)(H - c) Y_0 into alt
-  cs_status r = hx_core<T>(c, n_s, X, ld, alt, lda, EP_CHEB, s1 / e, 0.0, cc, nullptr, work, st);
+  cs_status r = hx_core<T>(c, n_s, X, ld, alt, lda, EP_CHEB, s1 / e, 0.0, cc, nullptr, work, st, tc);
   if (r != CS_OK) return r;
   T* prev = X;
   long long ldp = ld;
@@ -236,7 +259,8 @@ cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a
   for (int i = 1; i < degree; ++i) {
     double sn = 1.0 / (2.0 / s1 - sig);
     // Y_{i+1} = (2 sn/e)(H - c) Y_i - sig sn Y_{i-1}, written over Y_{i-1}
-    r = hx_core<T>(c, n_s, cur, ldc, prev, ldp, EP_CHEB, 2.0 * sn / e, sig * sn, cc, prev, work, st);
+    r = hx_core<T>(c, n_s, cur, ldc, prev, ldp, EP_CHEB, 2.0 * sn / e, sig * sn, cc, prev, work, st,
+                   tc);
     if (r != CS_OK) return r;
     std::swap(prev, cur);
     std::swap(ldp, ldc);
@@ -292,6 +316,19 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   return CS_OK;
 }
 
+// reads and clears the device error word (synchronising)
+cs_status check_dev_err(cs_ctx* c, cudaStream_t st) {
+  if (!c->dev_err) return CS_OK;
+  int code = 0;
+  CS_CHECK_CUDA(c, cudaMemcpyAsync(&code, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CS_CHECK_CUDA(c, cudaStreamSynchronize(st));
+  if (code != 0) {
+    CS_CHECK_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), st));
+    return fail(c, CS_ERR_TIMEOUT, "a bounded device wait expired (code " + std::to_string(code) + ")");
+  }
+  return CS_OK;
+}
+
 // filter (precision prec) -> Cholesky-QR (FP64) -> Rayleigh-Ritz (FP64); synchronising
 cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degree, double a,
                           double b, double a0, cs_precision prec, double* theta, double* resid,
@@ -305,7 +342,7 @@ cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degre
   } else {
     float* X32 = reinterpret_cast<float*>(wk + lay.X32);
     CS_LAUNCH(c, 1, launch_convert_f64_to_f32(X, ld, X32, H.d, H.d, n_s, st));
-    s = cheb_core<float>(c, n_s, X32, H.d, degree, a, b, a0, wk, st);
+    s = cheb_core<float>(c, n_s, X32, H.d, degree, a, b, a0, wk, st, prec == CS_MIXED_BF16);
     if (s == CS_OK) CS_LAUNCH(c, 1, launch_convert_f32_to_f64(X32, H.d, X, ld, H.d, n_s, st));
   }
   if (s != CS_OK) return s;
@@ -313,6 +350,7 @@ cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degre
   if ((s = rr_core(c, n_s, X, ld, theta, resid, nullptr, wk, st, status + 4)) != CS_OK) return s;
   int hs[5];
   if ((s = read_status(c, status, 5, hs, st)) != CS_OK) return s;
+  if ((s = check_dev_err(c, st)) != CS_OK) return s;
   if (hs[0] != 0 || hs[1] != 0) return fail(c, CS_ERR_CHOLESKY, "Cholesky breakdown in ChFSI");
   if (hs[4] < 0) return fail(c, CS_ERR_NOT_CONVERGED, "Jacobi eigensolver did not converge");
   return CS_OK;
@@ -365,6 +403,27 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
     cs_status st = upload_tables<double>(c);
     if (st == CS_OK) st = upload_tables<float>(c);
     if (st == CS_OK) {
+      for (int mode = 0; mode < 2 && st == CS_OK; ++mode) {
+        std::vector<uint16_t> tab;
+        int mt = 0, kp = 0;
+        build_tc_tables(c->host, mode, tab, mt, kp);
+        void** dst = mode == 0 ? &c->tc_synth : &c->tc_anal;
+        if (cudaMalloc(dst, tab.size() * 2) != cudaSuccess ||
+            cudaMemcpy(*dst, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+          st = CS_ERR_ALLOC;
+        if (mode == 0) {
+          c->tc_mt_synth = mt;
+          c->tc_kpad_synth = kp;
+        } else {
+          c->tc_mt_anal = mt;
+          c->tc_kpad_anal = kp;
+        }
+      }
+      if (st == CS_OK && (cudaMalloc((void**)&c->dev_err, sizeof(int)) != cudaSuccess ||
+                          cudaMemset(c->dev_err, 0, sizeof(int)) != cudaSuccess))
+        st = CS_ERR_ALLOC;
+    }
+    if (st == CS_OK) {
       size_t nr = c->host.w_r.size();
       if (cudaMalloc((void**)&c->w_r_dev, nr * sizeof(double)) != cudaSuccess ||
           cudaMemcpy(c->w_r_dev, c->host.w_r.data(), nr * sizeof(double),
@@ -394,6 +453,9 @@ cs_status cs_basis_free(cs_ctx* c) {
     }
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->w_r_dev) cudaFree(c->w_r_dev);
+    if (c->tc_synth) cudaFree(c->tc_synth);
+    if (c->tc_anal) cudaFree(c->tc_anal);
+    if (c->dev_err) cudaFree(c->dev_err);
   }
   delete c;
   return CS_OK;
@@ -532,9 +594,9 @@ cs_status cs_apply_H(cs_ctx* c, int n_s, const void* X, void* HX, long long ld,
   if (prec == CS_FP64)
     return hx_core<double>(c, n_s, (const double*)X, ld, (double*)HX, ld, EP_APPLY, 0, 0, 0,
                            nullptr, (char*)work, st);
-  if (prec == CS_FP32)
+  if (prec == CS_FP32 || prec == CS_MIXED_BF16)
     return hx_core<float>(c, n_s, (const float*)X, ld, (float*)HX, ld, EP_APPLY, 0, 0, 0,
-                          nullptr, (char*)work, st);
+                          nullptr, (char*)work, st, prec == CS_MIXED_BF16);
   return fail(c, CS_ERR_ARG, "unknown precision");
 }
 
@@ -549,7 +611,9 @@ cs_status cs_cheb_filter(cs_ctx* c, int n_s, void* X, long long ld, int degree, 
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CS_FP64) return cheb_core<double>(c, n_s, (double*)X, ld, degree, a, b, a0, (char*)work, st);
-  if (prec == CS_FP32) return cheb_core<float>(c, n_s, (float*)X, ld, degree, a, b, a0, (char*)work, st);
+  if (prec == CS_FP32 || prec == CS_MIXED_BF16)
+    return cheb_core<float>(c, n_s, (float*)X, ld, degree, a, b, a0, (char*)work, st,
+                            prec == CS_MIXED_BF16);
   return fail(c, CS_ERR_ARG, "unknown precision");
 }
 
@@ -649,7 +713,10 @@ cs_status cs_chfsi(cs_ctx* c, int n_s, int n_want, double* X, long long ld, int 
   if (n_want < 1 || n_want > n_s || degree < 1 || max_iter < 1 || !v0 || !theta || !resid ||
       !work)
     return fail(c, CS_ERR_ARG, "bad ChFSI arguments");
-  if (prec != CS_FP64 && prec != CS_FP32) return fail(c, CS_ERR_ARG, "unknown precision");
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
+    return fail(c, CS_ERR_ARG, "unknown precision");
+  if (prec == CS_MIXED_BF16 && c->n_p > 0)
+    return fail(c, CS_ERR_STATE, "CS_MIXED_BF16 does not apply projectors");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   const HostTables& H = c->host;
   cudaStream_t st = (cudaStream_t)stream;
@@ -693,10 +760,22 @@ cs_status cs_chfsi_step(cs_ctx* c, int n_s, double* X, long long ld, int degree,
   if (degree < 1 || !theta || !resid || !work) return fail(c, CS_ERR_ARG, "bad ChFSI step arguments");
   if (!(a < b) || !(a0 < a)) return fail(c, CS_ERR_ARG, "need a0 < a < b");
   if (n_s > 1024) return fail(c, CS_ERR_ARG, "n_s > 1024 not supported");
-  if (prec != CS_FP64 && prec != CS_FP32) return fail(c, CS_ERR_ARG, "unknown precision");
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
+    return fail(c, CS_ERR_ARG, "unknown precision");
+  if (prec == CS_MIXED_BF16 && c->n_p > 0)
+    return fail(c, CS_ERR_STATE, "CS_MIXED_BF16 does not apply projectors");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   return chfsi_step_core(c, n_s, X, ld, degree, a, b, a0, prec, theta, resid, (char*)work,
                          (cudaStream_t)stream);
+}
+
+cs_status cs_device_error(cs_ctx* c, int* code) {
+  cs_status s = need_device(c);
+  if (s != CS_OK) return s;
+  if (!code) return fail(c, CS_ERR_ARG, "NULL code");
+  CS_CHECK_CUDA(c, cudaMemcpy(code, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CS_CHECK_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+  return CS_OK;
 }
 
 cs_status cs_profile_begin(cs_ctx* c) {

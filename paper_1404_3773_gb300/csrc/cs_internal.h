@@ -31,6 +31,10 @@ struct HostTables {
 std::string build_host_tables(double R, int lmax, int nmax, const cs_quadrature& q,
                               HostTables& out);
 
+// split-BF16 radial tables for the tensor-core path (tc_radial.cu); mode 0 synthesis, 1 analysis
+void build_tc_tables(const HostTables& H, int mode, std::vector<uint16_t>& out, int& m_tiles,
+                     int& kpad);
+
 // packed offset of (m, l) inside one theta row: sum_{m'<m} (L - m') + (l - m)
 __host__ __device__ inline int theta_off(int L, int m) { return m * L - (m * (m - 1)) / 2; }
 __host__ __device__ inline int theta_row_len(int L) { return L * (L + 1) / 2; }
@@ -60,6 +64,10 @@ struct cs_ctx {
   cs::DevTables<double> d64;
   cs::DevTables<float> d32;
   double* w_r_dev = nullptr; // radial weights (for forward transforms of grid data)
+  void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
+  void* tc_anal = nullptr;
+  int tc_mt_synth = 0, tc_kpad_synth = 0, tc_mt_anal = 0, tc_kpad_anal = 0;
+  int* dev_err = nullptr;    // device error word (bounded waits); 0 = ok
   std::string err;
   long long launches = 0;
   // measurement hooks (cs_profile_begin / cs_profile_end)

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "cs_internal.h"
 #include "hx_kernels.cuh"
@@ -400,9 +401,29 @@ static cudaError_t launch_angular_st(const AngArgs<T>& a, int st, T* G, T* gout,
   return cudaGetLastError();
 }
 
+// Which ANG_FULL kernel runs: the row-pair kernel (angular_rp.cu) when one of its tiles fits
+// in shared memory, else the row-stream kernel above. CS_ANGULAR_KERNEL=stream|rp|rpN
+// overrides the choice (N = tile variant), for tuning.
+template <typename T>
+static int angular_choice() {
+  const char* e = getenv("CS_ANGULAR_KERNEL");
+  if (e) {
+    if (e[0] == 's') return -2;
+    if (e[0] == 'r' && e[1] == 'p') return e[2] ? atoi(e + 2) : -1;
+  }
+  return -1;
+}
+
 template <typename T>
 cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T* gin,
                            cudaStream_t stream) {
+  if (mode == ANG_FULL) {
+    int choice = angular_choice<T>();
+    if (choice != -2) {
+      cudaError_t e = launch_angular_rp<T>(a, G, choice, stream);
+      if (e != cudaErrorInvalidConfiguration) return e;
+    }
+  }
   int st = pick_states_per_cta<T>(a.L, a.n_phi, a.Q4);
   if (st == 0) return cudaErrorInvalidConfiguration;
   if (mode == ANG_FULL) return launch_angular_st<T, ANG_FULL>(a, st, G, gout, gin, stream);

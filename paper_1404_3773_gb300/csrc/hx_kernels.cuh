@@ -43,12 +43,31 @@ int pick_states_per_cta(int L, int n_phi, int Q4);
 template <typename T>
 cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T* gin,
                            cudaStream_t stream);
+// one-warp-per-row-pair variant of the ANG_FULL angular kernel (angular_rp.cu);
+// variant -1 = first (states per CTA, row pairs per chunk) tile that fits shared memory
+template <typename T>
+cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream_t stream);
+
 template <typename T>
 cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,
                                 int n_r, int S, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_radial_anal(const T* G, const T* rad, int L, int N, int n_r, int S,
                                const Epilogue<T>& ep, cudaStream_t stream);
+
+// ---------------------------------------------------------------- tensor-core radial GEMMs
+struct HostTables;
+// split-BF16 radial tables in the canonical tcgen05 operand layout (tc_radial.cu)
+struct TcTables {
+  const void* synth = nullptr;  // __nv_bfloat16, [l][m tile][k chunk][hi|lo][128 x 64]
+  const void* anal = nullptr;
+  int m_tiles_synth = 0, kpad_synth = 0, m_tiles_anal = 0, kpad_anal = 0;
+};
+cudaError_t launch_tc_radial_synth(const TcTables& tt, const HostTables& H, const float* X,
+                                   long long ldx, float* G, int S, int* err,
+                                   cudaStream_t stream);
+cudaError_t launch_tc_radial_anal(const TcTables& tt, const HostTables& H, const float* G, int S,
+                                  const Epilogue<float>& ep, int* err, cudaStream_t stream);
 
 // ---------------------------------------------------------------- dense FP64 pieces
 // C (na x nb, column-major, ldc) = A^T B, A: d x na (lda), B: d x nb (ldb), split over d

@@ -12,30 +12,59 @@
 namespace cs {
 
 // ------------------------------------------------------------------ Gram  C = A^T B
-constexpr int GT = 64;   // output tile
-constexpr int GK = 16;   // rows of d per step
-constexpr int GROWS = 512;  // rows of d per chunk (multiple of GK)
+// Tiles of (16U) x (16U) outputs, U <= 6 picked from n so that 80 states are one tile; the
+// d rows are split into chunks so that about two CTAs run per SM; partial products of the
+// chunks are summed in a fixed order (deterministic).
+constexpr int GK = 16;      // rows of d per step
+constexpr int kTargetCtas = 2 * 152;
 
-static int gram_chunks(long long d) { return (int)((d + GROWS - 1) / GROWS); }
-
-size_t gram_partial_elems(long long d, int na, int nb) {
-  return (size_t)gram_chunks(d) * (size_t)na * (size_t)nb;
+static int tile_u(int n) {
+  int tiles = (n + 95) / 96;
+  int u = (n + 16 * tiles - 1) / (16 * tiles);
+  return u < 1 ? 1 : (u > 6 ? 6 : u);
 }
 
+static void gram_shape(long long d, int na, int nb, int& u, int& ta, int& tb, int& chunks,
+                       long long& rows) {
+  u = tile_u(na > nb ? na : nb);
+  ta = (na + 16 * u - 1) / (16 * u);
+  tb = (nb + 16 * u - 1) / (16 * u);
+  int want = kTargetCtas / (ta * tb);
+  if (want < 1) want = 1;
+  rows = (d + want - 1) / want;
+  rows = ((rows + GK - 1) / GK) * GK;
+  if (rows < GK) rows = GK;
+  chunks = (int)((d + rows - 1) / rows);
+}
+
+size_t gram_partial_elems(long long d, int na, int nb) {
+  int u, ta, tb, chunks;
+  long long rows;
+  gram_shape(d, na, nb, u, ta, tb, chunks, rows);
+  return (size_t)chunks * (size_t)na * (size_t)nb;
+}
+
+template <int U>
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ A, long long lda,
                                                        const double* __restrict__ B,
                                                        long long ldb, long long d, int na,
-                                                       int nb, double* __restrict__ partial) {
-  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+                                                       int nb, long long rows,
+                                                       double* __restrict__ partial) {
+  constexpr int T = 16 * U;
+  const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
   const int chunk = blockIdx.z;
-  const long long r0 = (long long)chunk * GROWS;
-  const long long r1 = min(d, r0 + GROWS);
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
+  const long long r0 = (long long)chunk * rows;
+  const long long r1 = min(d, r0 + rows);
+  __shared__ double As[GK][T + 1];
+  __shared__ double Bs[GK][T + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4] = {};
+  double acc[U][U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
   for (long long rb = r0; rb < r1; rb += GK) {
-    for (int idx = tid; idx < GK * GT; idx += 256) {
+    for (int idx = tid; idx < GK * T; idx += 256) {
       int rr = idx % GK, cc = idx / GK;
       long long r = rb + rr;
       int i = i0 + cc, j = j0 + cc;
@@ -45,68 +74,94 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < GK; ++rr) {
-      double a[4], b[4];
+      double a[U], b[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[rr][tx + 16 * u];
+      for (int u = 0; u < U; ++u) a[u] = As[rr][tx + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[rr][ty + 16 * v];
+      for (int v = 0; v < U; ++v) b[v] = Bs[rr][ty + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
   double* P = partial + (size_t)chunk * na * nb;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
       if (i < na && j < nb) P[i + (size_t)j * na] = acc[u][v];
     }
 }
 
+// 32 elements x 8 chunk slices per 256-thread block; slices summed in a fixed order
 __global__ void k_gram_reduce(const double* __restrict__ partial, int chunks, int na, int nb,
                               double* __restrict__ C, int ldc) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= na * nb) return;
+  __shared__ double red[8][33];
+  const int el = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + el;
+  const int E = na * nb;
   double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += partial[(size_t)c * na * nb + e];
-  int i = e % na, j = e / na;
-  C[i + (size_t)j * ldc] = s;
+  if (e < E)
+    for (int c = sl; c < chunks; c += 8) s += partial[(size_t)c * E + e];
+  red[sl][el] = s;
+  __syncthreads();
+  if (sl == 0 && e < E) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][el];
+    int i = e % na, j = e / na;
+    C[i + (size_t)j * ldc] = t;
+  }
 }
 
 cudaError_t launch_gram(const double* A, long long lda, const double* B, long long ldb,
                         long long d, int na, int nb, double* C, int ldc, double* partial,
                         cudaStream_t stream) {
-  int chunks = gram_chunks(d);
-  dim3 grid((na + GT - 1) / GT, (nb + GT - 1) / GT, chunks);
-  k_gram_partial<<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, partial);
+  int u, ta, tb, chunks;
+  long long rows;
+  gram_shape(d, na, nb, u, ta, tb, chunks, rows);
+  dim3 grid(ta, tb, chunks);
+  switch (u) {
+    case 1: k_gram_partial<1><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 2: k_gram_partial<2><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 3: k_gram_partial<3><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 4: k_gram_partial<4><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 5: k_gram_partial<5><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    default: k_gram_partial<6><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+  }
   int tot = na * nb;
-  k_gram_reduce<<<(tot + 255) / 256, 256, 0, stream>>>(partial, chunks, na, nb, C, ldc);
+  k_gram_reduce<<<(tot + 31) / 32, 256, 0, stream>>>(partial, chunks, na, nb, C, ldc);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ C = alpha A Q + beta C
+// 64 rows x (16U) columns per CTA; U from n so that 80 states are one column tile.
+template <int U>
 __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, long long lda,
                                                   const double* __restrict__ Q, int ldq,
                                                   long long d, int K, int n, double alpha,
                                                   double beta, double* C, long long ldc) {
-  const long long r0 = (long long)blockIdx.x * GT;
-  const int j0 = blockIdx.y * GT;
-  __shared__ double As[GK][GT + 1];  // As[k][r]
-  __shared__ double Qs[GK][GT + 1];  // Qs[k][j]
+  constexpr int BM = 64, BN = 16 * U;
+  const long long r0 = (long long)blockIdx.x * BM;
+  const int j0 = blockIdx.y * BN;
+  __shared__ double As[GK][BM + 1];  // As[k][r]
+  __shared__ double Qs[GK][BN + 1];  // Qs[k][j]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4] = {};
+  double acc[4][U];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
   for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int idx = tid; idx < GK * GT; idx += 256) {
-      int rr = idx % GT, kk = idx / GT;
+    for (int idx = tid; idx < GK * BM; idx += 256) {
+      int rr = idx % BM, kk = idx / BM;
       long long r = r0 + rr;
       int k = k0 + kk;
       As[kk][rr] = (r < d && k < K) ? A[r + (long long)k * lda] : 0.0;
     }
-    for (int idx = tid; idx < GK * GT; idx += 256) {
+    for (int idx = tid; idx < GK * BN; idx += 256) {
       int kk = idx % GK, jj = idx / GK;
       int k = k0 + kk, j = j0 + jj;
       Qs[kk][jj] = (k < K && j < n) ? Q[k + (long long)j * ldq] : 0.0;
@@ -114,20 +169,20 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, l
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
+      double a[4], b[U];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Qs[kk][ty + 16 * v];
+      for (int v = 0; v < U; ++v) b[v] = Qs[kk][ty + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < U; ++v) {
     int j = j0 + ty + 16 * v;
     if (j >= n) continue;
 #pragma unroll
@@ -143,8 +198,16 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, l
 cudaError_t launch_gemm_nn(const double* A, long long lda, const double* Q, int ldq,
                            long long d, int k, int n, double alpha, double beta, double* C,
                            long long ldc, cudaStream_t stream) {
-  dim3 grid((unsigned)((d + GT - 1) / GT), (n + GT - 1) / GT);
-  k_gemm_nn<<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc);
+  const int u = tile_u(n);
+  dim3 grid((unsigned)((d + 63) / 64), (n + 16 * u - 1) / (16 * u));
+  switch (u) {
+    case 1: k_gemm_nn<1><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    case 2: k_gemm_nn<2><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    case 3: k_gemm_nn<3><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    case 4: k_gemm_nn<4><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    case 5: k_gemm_nn<5><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    default: k_gemm_nn<6><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+  }
   return cudaGetLastError();
 }
 
@@ -239,26 +302,30 @@ cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work
 // (p, q) rotate at once; n-1 rounds form a sweep. The rotation zeroing A_pq is the
 // classical symmetric Schur rotation (t = sign(tau)/(|tau| + sqrt(1 + tau^2))); the
 // annihilated pair is then set to zero exactly. A pair is rotated only if
-// |A_pq| > 1e-15 sqrt(|A_pp A_qq|) (and above an absolute floor tied to ||A||_F); the
-// iteration stops after a sweep without rotations (at most 50 sweeps).
+// |A_pq| > 1e-15 ||A||_F (below that the eigenvalues move by O(1e-30 ||A||^2 / gap)); the
+// iteration stops after a sweep without rotations (at most 50 sweeps). Round r of the
+// tournament pairs position i with position np-1-i, where position 0 holds player 0 and
+// position p >= 1 holds player 1 + (p - 1 + r) mod (np - 1).
 // One CTA; A (n x n) in work, V output. Odd n is padded by one dummy index.
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain, int n,
                                                   double* __restrict__ theta,
-                                                  double* __restrict__ V,
+                                                  double* __restrict__ Vout,
                                                   double* __restrict__ work,
                                                   int* __restrict__ status) {
   extern __shared__ double sh[];
   const int np = (n + 1) & ~1;  // even player count
   const int half = np / 2;
-  int* pos = reinterpret_cast<int*>(sh);   // [np] players at positions
-  int* pp = pos + np;                      // [half]
+  int* pp = reinterpret_cast<int*>(sh) + np;  // [half] (first np ints unused)
   int* qq = pp + half;                     // [half]
   double* cs = reinterpret_cast<double*>(qq + half);  // [half]; 2*np ints = 8-byte aligned
   double* sn = cs + half;                             // [half]
   __shared__ double red[32];
   __shared__ int rotations;
   __shared__ double floor_abs;
-  double* A = work;
+  // working copies: in shared memory when they fit (n <= 112), else in global memory
+  double* A = SMEM ? sn + half : work;
+  double* V = SMEM ? sn + half + (size_t)n * n : Vout;
   const int tid = threadIdx.x, nt = blockDim.x;
   double fro = 0.0;
   for (int e = tid; e < n * n; e += nt) {
@@ -270,12 +337,11 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain,
   }
   for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
   if ((tid & 31) == 0) red[tid >> 5] = fro;
-  for (int i = tid; i < np; i += nt) pos[i] = i;
   __syncthreads();
   if (tid == 0) {
     double f = 0.0;
     for (int w = 0; w < (nt + 31) / 32; ++w) f += red[w];
-    floor_abs = 1e-300 + 1e-18 * sqrt(f);
+    floor_abs = 1e-300 + 1e-15 * sqrt(f);
   }
   __syncthreads();
   int sweep = 0;
@@ -287,13 +353,15 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain,
     for (int round = 0; round < np - 1; ++round) {
       // pairs from the current positions: (pos[i], pos[np-1-i])
       for (int i = tid; i < half; i += nt) {
-        int a = pos[i], b = pos[np - 1 - i];
+        const int pa = i, pb = np - 1 - i;
+        int a = (pa == 0) ? 0 : 1 + (pa - 1 + round) % (np - 1);
+        int b = 1 + (pb - 1 + round) % (np - 1);
         int p = min(a, b), q = max(a, b);
         double c = 1.0, s = 0.0;
         if (q < n) {
           double apq = A[p + (size_t)q * n];
           double app = A[p + (size_t)p * n], aqq = A[q + (size_t)q * n];
-          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs) {
+          if (fabs(apq) > floor_abs) {
             double tau = (aqq - app) / (2.0 * apq);
             double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = rsqrt(1.0 + t * t);
@@ -334,18 +402,13 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain,
         V[row + (size_t)q * n] = s * vp + c * vq;
       }
       __syncthreads();
-      // the rotation annihilates A_pq; remove its rounding residue, rotate positions
+      // the rotation annihilates A_pq; remove its rounding residue
       for (int i = tid; i < half; i += nt) {
         int p = pp[i], q = qq[i];
         if (q < n) {
           A[p + (size_t)q * n] = 0.0;
           A[q + (size_t)p * n] = 0.0;
         }
-      }
-      if (tid == 0) {
-        int last = pos[np - 1];
-        for (int i = np - 1; i > 1; --i) pos[i] = pos[i - 1];
-        pos[1] = last;
       }
       __syncthreads();
     }
@@ -359,6 +422,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain,
   double* tmpv = work + (size_t)n * n;  // n diagonal values
   for (int i = tid; i < n; i += nt) tmpv[i] = A[i + (size_t)i * n];
   __syncthreads();
+  double* Vtmp = SMEM ? Vout : A;  // A is free once its diagonal is saved
   for (int i = tid; i < n; i += nt) {
     double vi = tmpv[i];
     int rank = 0;
@@ -367,11 +431,11 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain,
       rank += (vj < vi) || (vj == vi && j < i);
     }
     theta[rank] = vi;
-    // column i of V goes to column rank of A's storage (A no longer needed)
-    for (int r = 0; r < n; ++r) A[r + (size_t)rank * n] = V[r + (size_t)i * n];
+    for (int r = 0; r < n; ++r) Vtmp[r + (size_t)rank * n] = V[r + (size_t)i * n];
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += nt) V[e] = A[e];
+  if (!SMEM)
+    for (int e = tid; e < n * n; e += nt) Vout[e] = A[e];
   if (tid == 0) status[0] = converged ? sweep + 1 : -(sweep + 1);
 }
 
@@ -379,9 +443,17 @@ cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, 
                               int* status, cudaStream_t stream) {
   int np = (n + 1) & ~1;
   int half = np / 2;
-  size_t smem = (size_t)(np + 2 * half) * sizeof(int) + 2 * half * sizeof(double) + 16;
+  size_t smem = (size_t)(np + 2 * half) * sizeof(int) + 2 * half * sizeof(double) + 16;  // pp, qq, cs, sn
   int threads = n <= 64 ? 256 : 1024;
-  k_jacobi<<<1, threads, smem, stream>>>(A, n, theta, V, work, status);
+  size_t smem_full = smem + 2 * (size_t)n * n * sizeof(double);
+  if (smem_full <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_full);
+    if (e != cudaSuccess) return e;
+    k_jacobi<true><<<1, threads, smem_full, stream>>>(A, n, theta, V, work, status);
+  } else {
+    k_jacobi<false><<<1, threads, smem, stream>>>(A, n, theta, V, work, status);
+  }
   return cudaGetLastError();
 }
 

@@ -141,3 +141,36 @@ def test_launch_count_advances():
     n0 = cs.cs_launch_count(ctx)
     cs.cs_apply_H(ctx, Xd, torch.empty_like(Xd))
     assert cs.cs_launch_count(ctx) - n0 == 3
+
+
+@pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "odd_theta_phi_not_mult4"])
+def test_apply_H_mixed_bf16_error(case):
+    """Split-BF16 tensor-core radial contractions (tcgen05) + FP32 angular sums: error vs
+    the FP64 oracle within 1e-4 (split BF16 keeps about 16 significant bits)."""
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, dtype=torch.float32, ld=ctx.d + 4)
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_MIXED_BF16)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    assert fro <= 1e-4 and col <= 1e-3, (fro, col)
+    assert cs.cs_device_error(ctx) == 0
+
+
+def test_apply_H_mixed_bf16_full_size():
+    torch, cs = need_gpu()
+    w = W.erf_cluster_32()
+    register(w)
+    ctx = make_ctx(w)
+    X = w.x_block(16)
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, dtype=torch.float32)
+    HXd = torch.empty_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_MIXED_BF16)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    assert fro <= 1e-4, fro
