@@ -48,7 +48,10 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
                          gram_partial_elems(T.d, kMaxLanczos + 1, 1));
   if (np) part = std::max(part, gram_partial_elems(T.d, (int)np, n_s));
   o.part = take(part * 8);
-  o.small = take((5 * ns * ns + 8 * ns + 4 * kMaxLanczos * kMaxLanczos + 1024) * 8);
+  // small matrices: Gram / Rayleigh-Ritz matrix, rotation, and the eigensolver scratch
+  // (8 m^2 + 3 m + 4 doubles), with m = max(n_s, Lanczos size)
+  const size_t mm = std::max<size_t>(ns, kMaxLanczos + 2);
+  o.small = take((12 * mm * mm + 32 * mm + 4096) * 8);
   o.lanV = take(d * (kMaxLanczos + 2) * 8);
   o.status = take(64 * sizeof(int));
   // last, so that every other offset is the same for both precisions

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <utility>
 
 #include "hx_kernels.cuh"
 
@@ -212,14 +213,21 @@ cudaError_t launch_gemm_nn(const double* A, long long lda, const double* Q, int 
 }
 
 // ------------------------------------------------------------------ Cholesky-QR factor
-// One CTA. Lc = work (n x n column-major, lower), Dv = work + n*n.
+// One CTA. With column scaling D = diag(M)^(-1/2): D M D = L L^T (right-looking Cholesky,
+// one column per step), then U = D R^{-1} = D (L^{-1})^T, each thread forming one column of
+// L^{-1} by forward substitution. Working matrices in shared memory when 2 n^2 doubles fit
+// (n <= 112), else in `work` (global).
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict__ M, int n,
                                                          double* __restrict__ U,
                                                          double* __restrict__ work,
                                                          int* __restrict__ status) {
-  double* Lc = work;
-  double* Dv = work + (size_t)n * n;
+  extern __shared__ double shc[];
+  double* Lc = SMEM ? shc : work;                      // n x n, lower
+  double* Yi = SMEM ? shc + (size_t)n * n : U;         // n x n, (L^{-1})^T (upper)
+  double* Dv = SMEM ? shc + 2 * (size_t)n * n : work + (size_t)n * n;
   __shared__ int fail;
+  __shared__ double ljj;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) fail = 0;
   __syncthreads();
@@ -240,11 +248,10 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
   for (int e = tid; e < n * n; e += nt) {
     int i = e % n, j = e / n;
     Lc[e] = (i >= j) ? Dv[i] * M[e] * Dv[j] : 0.0;
+    Yi[e] = 0.0;
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle of Lc
   for (int j = 0; j < n; ++j) {
-    __shared__ double ljj;
     if (tid == 0) {
       double p = Lc[j + (size_t)j * n];
       if (!(p > 0.0) || !isfinite(p)) {
@@ -269,191 +276,553 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
     }
     __syncthreads();
   }
-  // U = D R^{-1} = D (L^{-1})^T : column c of L^{-1} by forward substitution (thread per c)
+  // y = L^{-1} e_c (y_i = 0 for i < c), stored as Yi[c + i n] = (L^{-1})[i][c]
   for (int c = tid; c < n; c += nt) {
-    for (int i = 0; i < n; ++i) U[i + (size_t)c * n] = 0.0;
-  }
-  __syncthreads();
-  for (int c = tid; c < n; c += nt) {
-    // y = L^{-1} e_c, y_i = 0 for i < c; store y_i into U[c][i] (row c of U^T = col c ...)
     for (int i = c; i < n; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) s -= Lc[i + (size_t)k * n] * U[c + (size_t)k * n];
-      U[c + (size_t)i * n] = s / Lc[i + (size_t)i * n];
+      for (int k = c; k < i; ++k) s -= Lc[i + (size_t)k * n] * Yi[c + (size_t)k * n];
+      Yi[c + (size_t)i * n] = s / Lc[i + (size_t)i * n];
     }
   }
   __syncthreads();
-  // U currently holds (L^{-1})^T (upper): U[c][i] = (L^{-1})[i][c]; scale rows by D
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e % n;
-    U[e] *= Dv[i];
-  }
+  for (int e = tid; e < n * n; e += nt) U[e] = Dv[e % n] * Yi[e];
   if (tid == 0) status[0] = 0;
 }
 
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream) {
-  k_cholqr_factor<<<1, 1024, 0, stream>>>(M, n, U, work, status);
+  size_t smem = (2 * (size_t)n * n + n) * sizeof(double);
+  if (smem <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_cholqr_factor<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cholqr_factor<true><<<1, 1024, smem, stream>>>(M, n, U, work, status);
+  } else {
+    k_cholqr_factor<false><<<1, 1024, 0, stream>>>(M, n, U, work, status);
+  }
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ parallel Jacobi
-// Cyclic Jacobi with round-robin (tournament) ordering: in each round n/2 disjoint pairs
-// (p, q) rotate at once; n-1 rounds form a sweep. The rotation zeroing A_pq is the
-// classical symmetric Schur rotation (t = sign(tau)/(|tau| + sqrt(1 + tau^2))); the
-// annihilated pair is then set to zero exactly. A pair is rotated only if
-// |A_pq| > 1e-15 ||A||_F (below that the eigenvalues move by O(1e-30 ||A||^2 / gap)); the
-// iteration stops after a sweep without rotations (at most 50 sweeps). Round r of the
-// tournament pairs position i with position np-1-i, where position 0 holds player 0 and
-// position p >= 1 holds player 1 + (p - 1 + r) mod (np - 1).
-// One CTA; A (n x n) in work, V output. Odd n is padded by one dummy index.
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Ain, int n,
-                                                  double* __restrict__ theta,
-                                                  double* __restrict__ Vout,
-                                                  double* __restrict__ work,
-                                                  int* __restrict__ status) {
-  extern __shared__ double sh[];
-  const int np = (n + 1) & ~1;  // even player count
-  const int half = np / 2;
-  int* pp = reinterpret_cast<int*>(sh) + np;  // [half] (first np ints unused)
-  int* qq = pp + half;                     // [half]
-  double* cs = reinterpret_cast<double*>(qq + half);  // [half]; 2*np ints = 8-byte aligned
-  double* sn = cs + half;                             // [half]
-  __shared__ double red[32];
-  __shared__ int rotations;
-  __shared__ double floor_abs;
-  // working copies: in shared memory when they fit (n <= 112), else in global memory
-  double* A = SMEM ? sn + half : work;
-  double* V = SMEM ? sn + half + (size_t)n * n : Vout;
+// ------------------------------------------------------------------ symmetric eigensolver
+// One CTA, for the Rayleigh-Ritz matrix (Sec. 3.2.1) and the Lanczos tridiagonal:
+//  1. Householder reduction of sym(A) to tridiagonal form T = Q^T A Q: for k = 0 .. n-3,
+//     v = x - alpha e_1 (x = A[k+1:, k], alpha = -sign(x_0) |x|), v /= |v|, p = A v,
+//     w = p - (v.p) v, A <- A - 2 (v w^T + w v^T) on the trailing block;
+//  2. Q accumulated from the reflectors (applied in reverse order to the identity);
+//  3. implicit QL iterations with a Wilkinson-type shift on (d, e): one thread generates the
+//     plane rotations of an iteration, then every thread applies them, in order, to its
+//     own row of Z (initially Q), so the columns of Z become the eigenvectors;
+//  4. eigenvalues sorted ascending with their vectors.
+// Working matrices in shared memory when they fit (n <= 112), else in `work`.
+template <typename T>
+struct EigEps;
+template <>
+struct EigEps<float> {
+  static __device__ float v() { return 1.1920929e-7f; }
+};
+template <>
+struct EigEps<double> {
+  static __device__ double v() { return 2.220446049250313e-16; }
+};
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_sym_eig(const double* __restrict__ Ain, int n,
+                                                   double* __restrict__ theta,
+                                                   double* __restrict__ Vout,
+                                                   T* __restrict__ work,
+                                                   int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char she_raw[];
+  T* she = reinterpret_cast<T*>(she_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
-  double fro = 0.0;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e % n, j = e / n;
-    double a = 0.5 * (Ain[i + (size_t)j * n] + Ain[j + (size_t)i * n]);
-    A[e] = a;
-    V[e] = (i == j) ? 1.0 : 0.0;
-    fro += a * a;
-  }
-  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
-  if ((tid & 31) == 0) red[tid >> 5] = fro;
-  __syncthreads();
-  if (tid == 0) {
-    double f = 0.0;
-    for (int w = 0; w < (nt + 31) / 32; ++w) f += red[w];
-    floor_abs = 1e-300 + 1e-15 * sqrt(f);
-  }
-  __syncthreads();
-  int sweep = 0;
-  bool converged = false;
-  const int max_sweeps = 50;
-  for (sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) rotations = 0;
+  T* A = SMEM ? she : work;                                  // n x n
+  T* Z = SMEM ? she + (size_t)n * n : work + (size_t)n * n;  // n x n
+  T* small = SMEM ? she + 2 * (size_t)n * n : work + 2 * (size_t)n * n;
+  T* d = small;           // n
+  T* e = d + n;           // n
+  T* vv = e + n;          // n   Householder vector
+  T* pw = vv + n;         // n   p, then w
+  T* rc = pw + n;         // n   rotation cosines
+  T* rs = rc + n;         // n   rotation sines
+  T* dsort = rs + n;      // n
+  __shared__ T red[32];
+  __shared__ int ctl[4];  // 0: rotation count, 1: failure flag, 2: m, 3: converged
+
+  auto block_sum = [&](T v) -> T {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
-    for (int round = 0; round < np - 1; ++round) {
-      // pairs from the current positions: (pos[i], pos[np-1-i])
-      for (int i = tid; i < half; i += nt) {
-        const int pa = i, pb = np - 1 - i;
-        int a = (pa == 0) ? 0 : 1 + (pa - 1 + round) % (np - 1);
-        int b = 1 + (pb - 1 + round) % (np - 1);
-        int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = A[p + (size_t)q * n];
-          double app = A[p + (size_t)p * n], aqq = A[q + (size_t)q * n];
-          if (fabs(apq) > floor_abs) {
-            double tau = (aqq - app) / (2.0 * apq);
-            double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = rsqrt(1.0 + t * t);
-            s = t * c;
-            atomicAdd(&rotations, 1);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    T t = T(0);
+    const int nw = (nt + 31) / 32;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+  };
+
+  for (int idx = tid; idx < n * n; idx += nt) {
+    int i = idx % n, j = idx / n;
+    A[idx] = (T)(0.5 * (Ain[i + (size_t)j * n] + Ain[j + (size_t)i * n]));
+  }
+  if (tid == 0) ctl[1] = 0;
+  __syncthreads();
+
+  // 1. tridiagonalisation; reflector k is kept in A[k+1:, k] (unit vector), alpha in e[k]
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // length of x
+    T xs = T(0);
+    for (int i = tid; i < m; i += nt) {
+      T x = A[(k + 1 + i) + (size_t)k * n];
+      xs += x * x;
+    }
+    const T xnorm = sqrt(block_sum(xs));
+    const T x0 = A[(k + 1) + (size_t)k * n];
+    const T alpha = (x0 >= T(0)) ? -xnorm : xnorm;
+    // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2 = 2 (|x|^2 - alpha x0)
+    const T vnorm2 = T(2) * (xnorm * xnorm - alpha * x0);
+    const bool skip = !(vnorm2 > T(0));
+    const T inv = skip ? T(0) : rsqrt(vnorm2);
+    for (int i = tid; i < m; i += nt) {
+      T x = A[(k + 1 + i) + (size_t)k * n];
+      vv[i] = skip ? T(0) : (i == 0 ? x - alpha : x) * inv;
+    }
+    __syncthreads();
+    if (skip) {
+      if (tid == 0) {
+        e[k] = x0;
+        for (int i = 0; i < m; ++i) A[(k + 1 + i) + (size_t)k * n] = T(0);
+      }
+      __syncthreads();
+      continue;
+    }
+    // p = A_sub v  (trailing block rows/cols k+1 .. n-1)
+    T kp = T(0);
+    for (int i = tid; i < m; i += nt) {
+      T s = T(0);
+      for (int j = 0; j < m; ++j) s += A[(k + 1 + i) + (size_t)(k + 1 + j) * n] * vv[j];
+      pw[i] = s;
+      kp += vv[i] * s;
+    }
+    const T K = block_sum(kp);
+    for (int i = tid; i < m; i += nt) pw[i] -= K * vv[i];
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += nt) {
+      int i = idx % m, j = idx / m;
+      A[(k + 1 + i) + (size_t)(k + 1 + j) * n] -= T(2) * (vv[i] * pw[j] + pw[i] * vv[j]);
+    }
+    __syncthreads();
+    // keep the reflector in column k below the subdiagonal slot
+    for (int i = tid; i < m; i += nt) A[(k + 1 + i) + (size_t)k * n] = vv[i];
+    if (tid == 0) e[k] = alpha;
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) d[i] = A[i + (size_t)i * n];
+  if (tid == 0) {
+    if (n >= 2) e[n - 2] = A[(n - 1) + (size_t)(n - 2) * n];
+    e[n - 1] = T(0);  // (entries k < n-2 are the alphas stored above)
+  }
+  __syncthreads();
+  // 2. Z = H_0 H_1 ... H_{n-3}: start from I, apply reflectors in reverse order
+  for (int idx = tid; idx < n * n; idx += nt) Z[idx] = ((idx % n) == (idx / n)) ? T(1) : T(0);
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarps = (nt + 31) / 32;
+  for (int k = n - 3; k >= 0; --k) {
+    const int m = n - k - 1;
+    const T* vk = A + (k + 1) + (size_t)k * n;
+    for (int j = warp; j < n; j += nwarps) {  // one warp per column, lanes over rows
+      T* zc = Z + (k + 1) + (size_t)j * n;
+      T t = T(0);
+      for (int i = lane; i < m; i += 32) t += vk[i] * zc[i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      t *= T(2);
+      for (int i = lane; i < m; i += 32) zc[i] -= t * vk[i];
+    }
+    __syncthreads();
+  }
+  // 3. implicit QL on (d, e), e[i] couples i and i+1
+  const T eps = EigEps<T>::v();
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0;; ++iter) {
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          T dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= eps * dd) break;
+        }
+        ctl[0] = 0;
+        if (m != l) {
+          if (iter >= 60) {
+            ctl[1] = 1;
           } else {
-            q = n;  // no rotation for this pair
+            T g = (d[l + 1] - d[l]) / (T(2) * e[l]);
+            T r = hypot(g, T(1));
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            T s = T(1), c = T(1), p = T(0);
+            int i = m - 1, cnt = 0;
+            bool early = false;
+            for (; i >= l; --i) {
+              T f = s * e[i], b = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == T(0)) {
+                d[i + 1] -= p;
+                e[m] = T(0);
+                early = true;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + T(2) * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              rc[cnt] = c;
+              rs[cnt] = s;
+              ++cnt;
+            }
+            if (!early) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = T(0);
+            }
+            ctl[0] = cnt;
+            ctl[2] = m;
           }
         }
-        pp[i] = p;
-        qq[i] = q;
-        cs[i] = c;
-        sn[i] = s;
+        ctl[3] = (m == l) ? 1 : 0;
       }
       __syncthreads();
-      // rows: A <- J^T A  (rows p, q of every column)
-      for (int e = tid; e < half * n; e += nt) {
-        int i = e % half, col = e / half;
-        int p = pp[i], q = qq[i];
-        if (q >= n) continue;
-        double c = cs[i], s = sn[i];
-        double ap = A[p + (size_t)col * n], aq = A[q + (size_t)col * n];
-        A[p + (size_t)col * n] = c * ap - s * aq;
-        A[q + (size_t)col * n] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J and V <- V J
-      for (int e = tid; e < half * n; e += nt) {
-        int i = e % half, row = e / half;
-        int p = pp[i], q = qq[i];
-        if (q >= n) continue;
-        double c = cs[i], s = sn[i];
-        double ap = A[row + (size_t)p * n], aq = A[row + (size_t)q * n];
-        A[row + (size_t)p * n] = c * ap - s * aq;
-        A[row + (size_t)q * n] = s * ap + c * aq;
-        double vp = V[row + (size_t)p * n], vq = V[row + (size_t)q * n];
-        V[row + (size_t)p * n] = c * vp - s * vq;
-        V[row + (size_t)q * n] = s * vp + c * vq;
-      }
-      __syncthreads();
-      // the rotation annihilates A_pq; remove its rounding residue
-      for (int i = tid; i < half; i += nt) {
-        int p = pp[i], q = qq[i];
-        if (q < n) {
-          A[p + (size_t)q * n] = 0.0;
-          A[q + (size_t)p * n] = 0.0;
+      const int cnt = ctl[0], m = ctl[2];
+      const bool stop = ctl[1] || ctl[3];
+      __syncthreads();  // everyone has read ctl before thread 0 writes it again
+      if (stop) break;
+      // apply the rotations (in generation order i = m-1, m-2, ...) to each row of Z
+      for (int row = tid; row < n; row += nt) {
+        for (int t = 0; t < cnt; ++t) {
+          const int i = m - 1 - t;
+          const T c = rc[t], s = rs[t];
+          const T zi = Z[row + (size_t)i * n], zi1 = Z[row + (size_t)(i + 1) * n];
+          Z[row + (size_t)(i + 1) * n] = s * zi + c * zi1;
+          Z[row + (size_t)i * n] = c * zi - s * zi1;
         }
       }
       __syncthreads();
     }
-    if (rotations == 0) {
-      converged = true;
-      break;
-    }
+    const bool failed_now = ctl[1] != 0;
     __syncthreads();
+    if (failed_now) break;
   }
-  // sort ascending: rank of each diagonal entry (ties by index), permute V columns
-  double* tmpv = work + (size_t)n * n;  // n diagonal values
-  for (int i = tid; i < n; i += nt) tmpv[i] = A[i + (size_t)i * n];
+  const bool failed = ctl[1] != 0;
+  // 4. sort ascending (rank of each value, ties by index) and permute the vectors
+  for (int i = tid; i < n; i += nt) dsort[i] = d[i];
   __syncthreads();
-  double* Vtmp = SMEM ? Vout : A;  // A is free once its diagonal is saved
   for (int i = tid; i < n; i += nt) {
-    double vi = tmpv[i];
+    const T vi = dsort[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double vj = tmpv[j];
+      const T vj = dsort[j];
       rank += (vj < vi) || (vj == vi && j < i);
     }
-    theta[rank] = vi;
-    for (int r = 0; r < n; ++r) Vtmp[r + (size_t)rank * n] = V[r + (size_t)i * n];
+    if (theta) theta[rank] = (double)vi;
+    for (int r = 0; r < n; ++r) Vout[r + (size_t)rank * n] = (double)Z[r + (size_t)i * n];
+  }
+  if (tid == 0) status[0] = failed ? -1 : 1;
+}
+
+// ---- FP64 refinement of an FP32 eigendecomposition (Ogita-Aishima iterative refinement
+// for symmetric eigenproblems): with R = I - V^T V, S = V^T A V, lam_i = S_ii/(1 - R_ii),
+// E_ij = (S_ij + lam_j R_ij)/(lam_j - lam_i) for separated pairs and R_ij/2 for pairs in a
+// cluster, V <- V (I + E); each step squares the error. A pair counts as clustered when
+// |lam_i - lam_j| <= max(delta, 1e3 |S_ij + lam_j R_ij|) (first-order mixing above 1e-3),
+// delta = 2(|S - diag(lam)|_F + |A|_F |R|_F); clusters are finished by an exact FP64 Jacobi
+// on their (small) block. The FP32 vectors are first made orthonormal to FP64 precision by
+// Newton-Schulz steps V <- V (3I - V^T V)/2, so that delta starts at the FP32 error of S.
+// All FP64 work here is wide (n x n GEMM tiles over many CTAs), which matters on a GPU
+// whose FP64 pipe is narrow: the FP32 factorisation carries the long serial chains.
+
+// C (n x n) = op(A) B, op(A) = A^T if TA; 16 x 16 output tiles, one element per thread
+template <bool TA>
+__global__ void __launch_bounds__(256) k_small_gemm(const double* __restrict__ A,
+                                                     const double* __restrict__ B, int n,
+                                                     double* __restrict__ C) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    const int ka = k0 + ty, kb = k0 + tx;
+    // As[kk][ii] = op(A)[i][k], Bs[kk][jj] = B[k][j]
+    As[ty][tx] = (i < n && ka < n) ? (TA ? A[ka + (size_t)i * n] : A[i + (size_t)ka * n]) : 0.0;
+    Bs[tx][ty] = (j < n && kb < n) ? B[kb + (size_t)j * n] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+    __syncthreads();
+  }
+  if (i < n && j < n) C[i + (size_t)j * n] = acc;
+}
+
+static cudaError_t small_gemm(bool ta, const double* A, const double* B, int n, double* C,
+                              cudaStream_t st) {
+  dim3 grid((n + 15) / 16, (n + 15) / 16);
+  if (ta) k_small_gemm<true><<<grid, 256, 0, st>>>(A, B, n, C);
+  else k_small_gemm<false><<<grid, 256, 0, st>>>(A, B, n, C);
+  return cudaGetLastError();
+}
+
+// lam (n), scal[0] = delta, scal[1] = |A|_F; one CTA
+__global__ void __launch_bounds__(1024) k_oa_norms(const double* __restrict__ A,
+                                                    const double* __restrict__ S,
+                                                    const double* __restrict__ G, int n,
+                                                    double* __restrict__ lam,
+                                                    double* __restrict__ scal) {
+  __shared__ double red[3][32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lam[i] = S[i + (size_t)i * n] / G[i + (size_t)i * n];
+  __syncthreads();
+  double a2 = 0.0, s2 = 0.0, r2 = 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e % n, j = e / n;
+    const double a = A[e];
+    const double sv = S[e] - (i == j ? lam[i] : 0.0);
+    const double rv = (i == j ? 1.0 : 0.0) - G[e];
+    a2 += a * a;
+    s2 += sv * sv;
+    r2 += rv * rv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = a2;
+    red[1][tid >> 5] = s2;
+    red[2][tid >> 5] = r2;
   }
   __syncthreads();
-  if (!SMEM)
-    for (int e = tid; e < n * n; e += nt) Vout[e] = A[e];
-  if (tid == 0) status[0] = converged ? sweep + 1 : -(sweep + 1);
+  if (tid == 0) {
+    double ta = 0.0, ts = 0.0, tr = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) {
+      ta += red[0][w];
+      ts += red[1][w];
+      tr += red[2][w];
+    }
+    scal[1] = sqrt(ta);
+    scal[0] = 2.0 * (sqrt(ts) + sqrt(ta) * sqrt(tr));
+  }
+}
+
+// M = 1.5 I - 0.5 G (Newton-Schulz factor), grid over elements
+__global__ void k_ns_factor(const double* __restrict__ G, int n, double* __restrict__ M) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int i = e % n, j = e / n;
+  M[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+}
+
+// Ep = I + E (n x n), grid over elements
+__global__ void k_oa_update(const double* __restrict__ S, const double* __restrict__ G, int n,
+                            const double* __restrict__ lam, const double* __restrict__ scal,
+                            double* __restrict__ Ep) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int i = e % n, j = e / n;
+  const double r = (i == j ? 1.0 : 0.0) - G[e];
+  double v;
+  if (i == j) {
+    v = 0.5 * r;
+  } else {
+    const double num = S[e] + lam[j] * r;
+    const double dl = lam[j] - lam[i];
+    const double lim = fmax(scal[0], 1e3 * fabs(num));
+    v = (fabs(dl) > lim) ? num / dl : 0.5 * r;
+  }
+  Ep[e] = (i == j ? 1.0 : 0.0) + v;
+}
+
+// one CTA: theta_i = S_ii/G_ii; sort; clusters (consecutive gaps <= max(delta, 1e5 max|S_ij|))
+// diagonalised by an exact FP64 Jacobi per cluster (one thread per cluster, blocks kept in
+// Vout as scratch); then Vout = (sorted V) * blockdiag(J). scratch: 2 n^2 + 2 n doubles.
+// status[0] = -2 if a cluster Jacobi did not converge (the FP32 stage leaves -1 / 1).
+__global__ void __launch_bounds__(1024) k_oa_final(const double* __restrict__ S,
+                                                    const double* __restrict__ G,
+                                                    const double* __restrict__ V, int n,
+                                                    const double* __restrict__ scal,
+                                                    double* __restrict__ theta,
+                                                    double* __restrict__ Vout,
+                                                    double* __restrict__ scratch,
+                                                    int* __restrict__ status) {
+  __shared__ double red[32];
+  __shared__ double dc_sh;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* lam = scratch;                                       // n   sorted eigenvalues
+  int* perm = reinterpret_cast<int*>(scratch + n);             // n   sorted -> original
+  int* cstart = perm + n;                                      // n   first column of cluster
+  double* Jb = scratch + 2 * (size_t)n;                        // n^2 (k x k blocks, ld n)
+  double* Vs = Jb + (size_t)n * n;                             // n^2 sorted vectors
+  double mo = 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e % n, j = e / n;
+    if (i != j) mo = fmax(mo, fabs(S[e]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mo = fmax(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mo;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, red[w]);
+    dc_sh = fmax(scal[0], 1e3 * m);
+  }
+  for (int i = tid; i < n; i += nt) {
+    const double vi = S[i + (size_t)i * n] / G[i + (size_t)i * n];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double vj = S[j + (size_t)j * n] / G[j + (size_t)j * n];
+      rank += (vj < vi) || (vj == vi && j < i);
+    }
+    lam[rank] = vi;
+    perm[rank] = i;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
+    const int r = e % n, c = e / n;
+    Vs[e] = V[r + (size_t)perm[c] * n];
+  }
+  const double dc = dc_sh;
+  for (int c = tid; c < n; c += nt) {
+    int i0 = c;
+    while (i0 > 0 && lam[i0] - lam[i0 - 1] <= dc) --i0;
+    cstart[c] = i0;
+  }
+  __syncthreads();
+  bool fail = false;
+  for (int i0 = tid; i0 < n; i0 += nt) {
+    if (cstart[i0] != i0) continue;  // not the first column of its cluster
+    int i1 = i0;
+    while (i1 + 1 < n && cstart[i1 + 1] == i0) ++i1;
+    const int k = i1 - i0 + 1;
+    double* J = Jb + (size_t)i0 * n + i0;    // k x k, leading dimension n
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) J[a + (size_t)b * n] = (a == b) ? 1.0 : 0.0;
+    if (k == 1) continue;
+    double* B = Vout + (size_t)i0 * n + i0;  // cluster block of S in sorted order
+    double bn = 0.0;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        const double v = S[perm[i0 + a] + (size_t)perm[i0 + b] * n];
+        B[a + (size_t)b * n] = v;
+        bn += v * v;
+      }
+    bn = sqrt(bn);
+    bool done = false;
+    for (int sweep = 0; sweep < 50 && !done; ++sweep) {
+      int rot = 0;
+      for (int p = 0; p < k; ++p)
+        for (int q = p + 1; q < k; ++q) {
+          const double apq = B[p + (size_t)q * n];
+          if (!(fabs(apq) > 1e-15 * bn)) continue;
+          ++rot;
+          const double app = B[p + (size_t)p * n], aqq = B[q + (size_t)q * n];
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+          for (int x = 0; x < k; ++x) {  // B <- G^T B (rows p, q)
+            const double bp = B[p + (size_t)x * n], bq = B[q + (size_t)x * n];
+            B[p + (size_t)x * n] = c * bp - s * bq;
+            B[q + (size_t)x * n] = s * bp + c * bq;
+          }
+          for (int x = 0; x < k; ++x) {  // B <- B G, J <- J G (columns p, q)
+            const double bp = B[x + (size_t)p * n], bq = B[x + (size_t)q * n];
+            B[x + (size_t)p * n] = c * bp - s * bq;
+            B[x + (size_t)q * n] = s * bp + c * bq;
+            const double jp = J[x + (size_t)p * n], jq = J[x + (size_t)q * n];
+            J[x + (size_t)p * n] = c * jp - s * jq;
+            J[x + (size_t)q * n] = s * jp + c * jq;
+          }
+          B[p + (size_t)q * n] = 0.0;
+          B[q + (size_t)p * n] = 0.0;
+        }
+      done = (rot == 0);
+    }
+    if (!done) fail = true;
+    // ascending order inside the cluster (insertion sort; J's columns follow)
+    for (int a = 1; a < k; ++a)
+      for (int b = a; b > 0 && B[b + (size_t)b * n] < B[(b - 1) + (size_t)(b - 1) * n]; --b) {
+        const double tmp = B[b + (size_t)b * n];
+        B[b + (size_t)b * n] = B[(b - 1) + (size_t)(b - 1) * n];
+        B[(b - 1) + (size_t)(b - 1) * n] = tmp;
+        for (int x = 0; x < k; ++x) {
+          const double tj = J[x + (size_t)b * n];
+          J[x + (size_t)b * n] = J[x + (size_t)(b - 1) * n];
+          J[x + (size_t)(b - 1) * n] = tj;
+        }
+      }
+    for (int a = 0; a < k; ++a) lam[i0 + a] = B[a + (size_t)a * n];
+  }
+  if (fail) status[0] = -2;
+  __syncthreads();
+  // Vout[:, c] = sum over the cluster of c: Vs[:, a] J[a][c]
+  for (int e = tid; e < n * n; e += nt) {
+    const int r = e % n, c = e / n;
+    const int i0 = cstart[c];
+    int i1 = c;
+    while (i1 + 1 < n && cstart[i1 + 1] == i0) ++i1;
+    double acc = 0.0;
+    for (int a = i0; a <= i1; ++a) acc = fma(Vs[r + (size_t)a * n], Jb[a + (size_t)c * n], acc);
+    Vout[e] = acc;
+  }
+  for (int i = tid; i < n; i += nt) theta[i] = lam[i];
 }
 
 cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, double* work,
                               int* status, cudaStream_t stream) {
-  int np = (n + 1) & ~1;
-  int half = np / 2;
-  size_t smem = (size_t)(np + 2 * half) * sizeof(int) + 2 * half * sizeof(double) + 16;  // pp, qq, cs, sn
-  int threads = n <= 64 ? 256 : 1024;
-  size_t smem_full = smem + 2 * (size_t)n * n * sizeof(double);
-  if (smem_full <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_full);
+  const size_t n2 = (size_t)n * n;
+  double* V0 = work;
+  double* V1 = V0 + n2;
+  double* P = V1 + n2;
+  double* S = P + n2;
+  double* G = S + n2;
+  double* Ep = G + n2;
+  double* lam = Ep + n2;          // n
+  double* scal = lam + n;         // 4
+  double* scratch = scal + 4;     // 2 n^2 + 2 n (final step)
+  const int threads = 256;
+  // 1. FP32 eigendecomposition of sym(A) -> V0 (FP64 copy of the FP32 vectors)
+  size_t smem = (2 * n2 + 7 * (size_t)n) * sizeof(float);
+  cudaError_t e;
+  if (smem <= 200 * 1024) {
+    e = cudaFuncSetAttribute(k_sym_eig<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_jacobi<true><<<1, threads, smem_full, stream>>>(A, n, theta, V, work, status);
+    k_sym_eig<float, true><<<1, threads, smem, stream>>>(A, n, nullptr, V0, nullptr, status);
   } else {
-    k_jacobi<false><<<1, threads, smem, stream>>>(A, n, theta, V, work, status);
+    k_sym_eig<float, false><<<1, threads, 0, stream>>>(A, n, nullptr, V0,
+                                                       reinterpret_cast<float*>(P), status);
   }
+  // 2. orthonormalise to FP64 precision (Newton-Schulz), then refine in FP64
+  double* Vc = V0;
+  double* Vn = V1;
+  for (int it = 0; it < 3; ++it) {
+    if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;   // G = V^T V
+    k_ns_factor<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(G, n, Ep);
+    if ((e = small_gemm(false, Vc, Ep, n, Vn, stream)) != cudaSuccess) return e;
+    std::swap(Vc, Vn);
+  }
+  for (int it = 0; it < 4; ++it) {
+    if ((e = small_gemm(false, A, Vc, n, P, stream)) != cudaSuccess) return e;   // P = A V
+    if ((e = small_gemm(true, Vc, P, n, S, stream)) != cudaSuccess) return e;    // S = V^T A V
+    if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;   // G = V^T V
+    k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
+    k_oa_update<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(S, G, n, lam, scal, Ep);
+    if ((e = small_gemm(false, Vc, Ep, n, Vn, stream)) != cudaSuccess) return e;  // V (I + E)
+    std::swap(Vc, Vn);
+  }
+  if ((e = small_gemm(false, A, Vc, n, P, stream)) != cudaSuccess) return e;
+  if ((e = small_gemm(true, Vc, P, n, S, stream)) != cudaSuccess) return e;
+  if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;
+  k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
+  // 3. sort, clusters, output
+  k_oa_final<<<1, 1024, 0, stream>>>(S, G, Vc, n, scal, theta, V, scratch, status);
   return cudaGetLastError();
 }
 
