@@ -215,6 +215,34 @@ cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
 cs_status cs_apply_H_noalloc(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
                              cs_precision prec, cs_stream stream);
 
+/* ------------------------------------------------------------------ batched filter */
+
+/* Many independent clusters (contexts of uneven lmax, N, grid and state count) filtered
+ * together, FP32 blocks (Sec. 3.2.1 filter, Sec. 2.2.4 H.X per cluster). One persistent
+ * launch per Chebyshev step runs the radial, angular and radial-analysis work of every
+ * cluster from one ordered work list (bounded waits between the stages of a cluster); the
+ * filter is captured once into a CUDA graph and replayed. All contexts must be on one device,
+ * have a potential and no projectors. n_s[i] states for cluster i; degree fixed per batch. */
+typedef struct cs_batch cs_batch;
+cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree,
+                          cs_batch** out);
+cs_status cs_batch_free(cs_batch* batch);
+/* DEVICE workspace needed by cs_batch_cheb_filter and cs_batch_tune (bytes). */
+cs_status cs_batch_workspace_bytes(const cs_batch* batch, size_t* bytes);
+/* X[i]: DEVICE float block of cluster i (d_i x n_s[i], leading dimension ld[i]), filtered in
+ * place with bounds (a[i], b[i], a0[i]) (HOST arrays). Enqueued on `stream`; the first call
+ * (or a call after cs_batch_tune) captures the graph, so make it outside stream capture. */
+cs_status cs_batch_cheb_filter(cs_batch* batch, float* const* X, const long long* ld,
+                               const double* a, const double* b, const double* a0, void* work,
+                               cs_stream stream);
+/* Autotuner: times one filter per angular tile variant (states per CTA x row pairs per
+ * chunk) on these blocks and keeps the fastest; X is restored afterwards. Synchronising.
+ * *chosen = variant index, *best_ms = its filter time. */
+cs_status cs_batch_tune(cs_batch* batch, float* const* X, const long long* ld, const double* a,
+                        const double* b, const double* a0, void* work, cs_stream stream,
+                        int* chosen, float* best_ms);
+const char* cs_batch_last_error(const cs_batch* batch);
+
 /* Device error word of the context (synchronising): 0 if no kernel reported a problem, else
  * the code of the first bounded wait that expired (tensor-core path). Reading clears it. A
  * non-zero word is also reported as CS_ERR_TIMEOUT by the next synchronising call. */

@@ -24,7 +24,8 @@ __all__ = [
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
     "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
-    "cs_device_error",
+    "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
+    "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
 ]
 
@@ -81,6 +82,14 @@ _SIGS = {
     "cs_profile_begin": (_i, [_vp]),
     "cs_device_error": (_i, [_vp, ctypes.POINTER(_i)]),
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
+    "cs_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, ctypes.POINTER(_vp)]),
+    "cs_batch_free": (_i, [_vp]),
+    "cs_batch_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_batch_cheb_filter": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_ll), _dp, _dp, _dp,
+                                  _vp, _vp]),
+    "cs_batch_tune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_ll), _dp, _dp, _dp, _vp, _vp,
+                           ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
+    "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
     "cs_launch_count": (_ll, [_vp]),
 }
@@ -351,6 +360,105 @@ def cs_profile_end(ctx: Context):
     n = (_ll * 4)()
     ctx.check(_lib.cs_profile_end(ctx.handle, ms, n))
     return list(ms), list(n)
+
+
+class Batch:
+    """Owns one cs_batch: many contexts filtered by one persistent launch per Chebyshev step."""
+
+    def __init__(self, handle: int, ctxs, n_s, degree: int):
+        self._h = ctypes.c_void_p(handle)
+        self.ctxs = list(ctxs)  # keep the contexts alive
+        self.n_s = list(n_s)
+        self.degree = degree
+        self._ws = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, status: int):
+        if status != 0:
+            raise CsError(status, _lib.cs_batch_last_error(self._h).decode())
+
+    def workspace(self) -> torch.Tensor:
+        if self._ws is None:
+            self._ws = torch.empty(cs_batch_workspace_bytes(self), dtype=torch.uint8,
+                                   device=f"cuda:{self.ctxs[0].device}")
+        return self._ws
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.cs_batch_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_batch_create(ctxs, n_s, degree: int) -> Batch:
+    n = len(ctxs)
+    arr = (_vp * n)(*[c.handle.value for c in ctxs])
+    ns = (_i * n)(*[int(x) for x in n_s])
+    h = _vp()
+    st = _lib.cs_batch_create(n, arr, ns, int(degree), ctypes.byref(h))
+    if st != 0:
+        raise CsError(st, "cs_batch_create failed (contexts must share a device, have a "
+                          "potential and no projectors)")
+    return Batch(h.value, ctxs, n_s, degree)
+
+
+def cs_batch_free(batch: Batch):
+    batch.close()
+
+
+def cs_batch_workspace_bytes(batch: Batch) -> int:
+    out = ctypes.c_size_t()
+    batch.check(_lib.cs_batch_workspace_bytes(batch.handle, ctypes.byref(out)))
+    return out.value
+
+
+def _batch_args(batch: Batch, Xs, a, b, a0):
+    import numpy as np
+    n = len(batch.ctxs)
+    assert len(Xs) == n
+    for X, c in zip(Xs, batch.ctxs):
+        assert X.is_cuda and X.dtype == torch.float32 and X.stride(1) == 1 and X.shape[1] >= c.d
+    ptrs = (_vp * n)(*[X.data_ptr() for X in Xs])
+    lds = (_ll * n)(*[X.stride(0) for X in Xs])
+    av = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    bv = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    a0v = np.ascontiguousarray(np.asarray(a0, dtype=np.float64))
+    return ptrs, lds, av, bv, a0v
+
+
+def cs_batch_cheb_filter(batch: Batch, Xs, a, b, a0, work=None, stream=None):
+    """Filters every block Xs[i] (float32, shape (n_s[i], ld)) in place with bounds
+    (a[i], b[i], a0[i])."""
+    ptrs, lds, av, bv, a0v = _batch_args(batch, Xs, a, b, a0)
+    work = batch.workspace() if work is None else work
+    batch.check(_lib.cs_batch_cheb_filter(batch.handle, ptrs, lds, av.ctypes.data_as(_dp),
+                                          bv.ctypes.data_as(_dp), a0v.ctypes.data_as(_dp),
+                                          _ptr(work), _stream_ptr(stream)))
+
+
+def cs_batch_tune(batch: Batch, Xs, a, b, a0, work=None, stream=None):
+    """Autotunes the angular tile variant on these blocks (restored afterwards); returns
+    (variant, filter ms)."""
+    ptrs, lds, av, bv, a0v = _batch_args(batch, Xs, a, b, a0)
+    work = batch.workspace() if work is None else work
+    ch = _i()
+    ms = ctypes.c_float()
+    batch.check(_lib.cs_batch_tune(batch.handle, ptrs, lds, av.ctypes.data_as(_dp),
+                                   bv.ctypes.data_as(_dp), a0v.ctypes.data_as(_dp), _ptr(work),
+                                   _stream_ptr(stream), ctypes.byref(ch), ctypes.byref(ms)))
+    return ch.value, ms.value
+
+
+def cs_batch_last_error(batch: Batch) -> str:
+    return _lib.cs_batch_last_error(batch.handle).decode()
 
 
 def cs_last_error(ctx: Context | None) -> str:

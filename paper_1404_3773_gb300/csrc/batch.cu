@@ -1,0 +1,497 @@
+// Batched Chebyshev filter (Sec. 3.2.1) over many independent clusters of uneven size (FP32).
+//
+// Each Chebyshev step of every cluster is one H.X (Sec. 2.2.4) in three stages: radial
+// synthesis tiles, angular blocks (one radial node x a few states), radial analysis tiles with
+// the fused kinetic + recurrence epilogue. One persistent launch runs a whole step for all
+// clusters: its CTAs take work items from a list ordered by stage through an atomic queue
+// head, and an item of a later stage waits (bounded spin) until every item of the previous
+// stage of the same cluster has finished (per-cluster completion counters, release/acquire
+// through __threadfence). Because items are taken in list order, every item an item waits
+// for was already taken by a running CTA, so the launch always makes progress. On expiry of
+// a wait the CTA records an error code in the context's device word and skips the item.
+// The filter (counter reset + one launch per step, and the final copy) is captured once into
+// a CUDA graph and replayed; per-step coefficients are read from device memory, so new bounds
+// only need a small upload. An autotuner times the angular tile variants on the real batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "angular_rp.cuh"
+#include "cs_internal.h"
+#include "hx_device.cuh"
+#include "hx_kernels.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr long long kWaitLimit = 1ll << 24;
+
+struct BCluster {
+  AngArgs<float> ang;      // L, n_r, n_theta, n_phi, Q4, S and the angular tables
+  int N;
+  const float* rad;
+  const float* half_lambda;
+  float* X;                // caller block (ld)
+  float* Yalt;             // workspace block (ld_alt)
+  float* G;                // workspace radial-node intermediate
+  long long ld, ld_alt;
+  const float* coef;       // [step][3]: cA, cB, cshift
+  int n_items[3];
+};
+
+struct BItem {
+  int cluster, stage, x, y;
+};
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+
+template <int ST, int RC>
+__global__ void __launch_bounds__(kBatchThreads) k_batch_step(const BCluster* __restrict__ cl,
+                                                               const BItem* __restrict__ items,
+                                                               int n_items, int step,
+                                                               int* __restrict__ head,
+                                                               int* __restrict__ done,
+                                                               int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int item_sh;
+  __shared__ int ok_sh;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) item_sh = atomicAdd(head, 1);
+    __syncthreads();
+    const int idx = item_sh;
+    if (idx >= n_items) break;
+    const BItem it = items[idx];
+    const BCluster& c = cl[it.cluster];
+    // dependencies: all items of the previous stage of this cluster
+    if (tid == 0) {
+      ok_sh = 1;
+      if (it.stage > 0) {
+        const int* cnt = done + 3 * it.cluster + (it.stage - 1);
+        const int target = c.n_items[it.stage - 1];
+        long long spins = 0;
+        while (ld_volatile(cnt) < target) {
+          if (++spins > kWaitLimit) {
+            atomicCAS(err, 0, 10 + it.stage);
+            ok_sh = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (ok_sh) {
+      // buffers of this step: step 1 reads X, writes Yalt; then they alternate
+      const bool odd = (step & 1) != 0;
+      float* in = odd ? c.X : c.Yalt;
+      float* out = odd ? c.Yalt : c.X;
+      const long long ld_in = odd ? c.ld : c.ld_alt;
+      const long long ld_out = odd ? c.ld_alt : c.ld;
+      if (it.stage == 0) {
+        auto As = reinterpret_cast<float(*)[RBM + 1]>(smem);
+        auto Bs = reinterpret_cast<float(*)[RBN + 1]>(smem + sizeof(float) * RBK * (RBM + 1));
+        int l, c0;
+        locate_l_tile(it.x, c.ang.S, l, c0);
+        radial_synth_tile<float>(in, ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S, l, c0,
+                                 it.y * RBM, As, Bs);
+      } else if (it.stage == 1) {
+        angular_rp_block<float, ST, RC>(c.ang, c.G, it.y, it.x * ST, smem);
+      } else {
+        auto As = reinterpret_cast<float(*)[RBM + 1]>(smem);
+        auto Bs = reinterpret_cast<float(*)[RBN + 1]>(smem + sizeof(float) * RBK * (RBM + 1));
+        Epilogue<float> ep;
+        ep.mode = EP_CHEB;
+        ep.X = in;
+        ep.ld = ld_in;
+        ep.out = out;
+        ep.ld_out = ld_out;
+        ep.Yprev = (step == 1) ? nullptr : out;
+        ep.half_lambda = c.half_lambda;
+        ep.cA = c.coef[3 * (step - 1) + 0];
+        ep.cB = c.coef[3 * (step - 1) + 1];
+        ep.cshift = c.coef[3 * (step - 1) + 2];
+        int l, c0;
+        locate_l_tile(it.x, c.ang.S, l, c0);
+        radial_anal_tile<float>(c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S, ep, l, c0,
+                                it.y * RBM, As, Bs);
+      }
+    }
+    __threadfence();  // this thread's results visible device-wide before the count
+    __syncthreads();
+    if (tid == 0) atomicAdd(done + 3 * it.cluster + it.stage, 1);
+  }
+}
+
+// copies Yalt -> X for every cluster (after an odd number of steps the result sits in Yalt)
+__global__ void k_batch_copy_back(const BCluster* __restrict__ cl, int n) {
+  const BCluster& c = cl[blockIdx.y];
+  const long long d = (long long)c.ang.L * c.ang.L * c.N;
+  const long long tot = d * c.ang.S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / d, i = e - s * d;
+    c.X[i + s * c.ld] = c.Yalt[i + s * c.ld_alt];
+  }
+}
+
+int col_tiles(int L, int S) {
+  int t = 0;
+  for (int l = 0; l < L; ++l) t += ((2 * l + 1) * S + RBN - 1) / RBN;
+  return t;
+}
+
+// angular tile variants (states per CTA, row pairs per chunk); the row-pair block needs
+// exactly RC x 32 threads, so every variant here has RC x 32 == kBatchThreads
+const int kVariants[][2] = {{4, 8}, {8, 8}, {2, 8}};
+constexpr int kNumVariants = 3;
+static_assert(8 * 32 == kBatchThreads, "batch variants assume 8 row pairs per chunk");
+
+size_t variant_smem(const std::vector<cs_ctx*>& ctxs, int v) {
+  size_t m = 2 * sizeof(float) * RBK * (RBM + 1);
+  for (cs_ctx* c : ctxs) {
+    const HostTables& H = c->host;
+    const int L = H.L, Q = c->Q4 + 1, rowlen = L * (L + 1) / 2;
+    m = std::max(m, rp_smem_elems(L, Q, rowlen, kVariants[v][0], kVariants[v][1]) * sizeof(float));
+  }
+  return m;
+}
+
+}  // namespace
+}  // namespace cs
+
+using namespace cs;
+
+struct cs_batch {
+  std::vector<cs_ctx*> ctxs;
+  std::vector<int> n_s;
+  int degree = 0;
+  int variant = -1;  // angular tile variant
+  int device = 0;
+  BCluster* d_cl = nullptr;
+  BItem* d_items = nullptr;
+  int n_items = 0;
+  float* d_coef = nullptr;        // [cluster][degree][3]
+  int* d_ctr = nullptr;           // head + 3 counters per cluster
+  std::vector<BCluster> h_cl;
+  std::vector<float> h_coef;
+  std::vector<size_t> off_alt, off_G, off_bk;  // workspace offsets per cluster
+  size_t ws_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<void*> graph_key;  // pointers the graph was captured with
+  int graph_variant = -1;
+  std::string err;
+};
+
+namespace {
+
+cs_status bfail(cs_batch* b, cs_status st, const std::string& m) {
+  if (b) b->err = m;
+  return st;
+}
+
+template <int ST, int RC>
+cudaError_t launch_step(cs_batch* b, int step, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_step<ST, RC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<ST, RC>,
+                                                    kBatchThreads, smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  const int grid = std::max(1, per_sm) * sms;
+  int* head = b->d_ctr;
+  int* done = b->d_ctr + 1;
+  int* err = b->ctxs[0]->dev_err;
+  k_batch_step<ST, RC><<<grid, kBatchThreads, smem, st>>>(b->d_cl, b->d_items, b->n_items, step,
+                                                          head, done, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_variant_step(cs_batch* b, int v, int step, cudaStream_t st) {
+  const size_t smem = variant_smem(b->ctxs, v);
+  switch (v) {
+    case 0: return launch_step<4, 8>(b, step, smem, st);
+    case 1: return launch_step<8, 8>(b, step, smem, st);
+    case 2: return launch_step<2, 8>(b, step, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// builds the item list for a variant (the angular item count depends on ST)
+cs_status build_items(cs_batch* b, int v) {
+  const int ST = kVariants[v][0];
+  std::vector<BItem> items;
+  const int nc = (int)b->ctxs.size();
+  for (int stage = 0; stage < 3; ++stage)
+    for (int ci = 0; ci < nc; ++ci) {
+      const HostTables& H = b->ctxs[ci]->host;
+      const int S = b->n_s[ci];
+      int cnt = 0;
+      if (stage == 0 || stage == 2) {
+        const int ct = col_tiles(H.L, S);
+        const int rt = (stage == 0) ? (H.n_r + RBM - 1) / RBM : (H.N + RBM - 1) / RBM;
+        for (int y = 0; y < rt; ++y)
+          for (int x = 0; x < ct; ++x) {
+            items.push_back({ci, stage, x, y});
+            ++cnt;
+          }
+      } else {
+        const int stiles = (S + ST - 1) / ST;
+        for (int k = 0; k < H.n_r; ++k)
+          for (int x = 0; x < stiles; ++x) {
+            items.push_back({ci, 1, x, k});
+            ++cnt;
+          }
+      }
+      b->h_cl[ci].n_items[stage] = cnt;
+    }
+  // a captured graph refers to the old list: drop it before the list is replaced
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_variant = -1;
+  if (b->d_items) {
+    cudaDeviceSynchronize();
+    cudaFree(b->d_items);
+  }
+  b->d_items = nullptr;
+  if (cudaMalloc((void**)&b->d_items, items.size() * sizeof(BItem)) != cudaSuccess)
+    return bfail(b, CS_ERR_ALLOC, "cudaMalloc of the work list failed");
+  if (cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return bfail(b, CS_ERR_CUDA, "upload of the work list failed");
+  b->n_items = (int)items.size();
+  return CS_OK;
+}
+
+cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const double* a,
+                     const double* bb, const double* a0, void* work, cudaStream_t st) {
+  const int nc = (int)b->ctxs.size();
+  // per-cluster coefficients of every step (scaled three-term recurrence)
+  for (int ci = 0; ci < nc; ++ci) {
+    if (!(a[ci] < bb[ci]) || !(a0[ci] < a[ci])) return bfail(b, CS_ERR_ARG, "need a0 < a < b");
+    const double cc = 0.5 * (a[ci] + bb[ci]), e = 0.5 * (bb[ci] - a[ci]);
+    const double s1 = e / (a0[ci] - cc);
+    double sig = s1;
+    float* cf = b->h_coef.data() + (size_t)ci * b->degree * 3;
+    cf[0] = (float)(s1 / e);
+    cf[1] = 0.f;
+    cf[2] = (float)cc;
+    for (int i = 1; i < b->degree; ++i) {
+      const double sn = 1.0 / (2.0 / s1 - sig);
+      cf[3 * i + 0] = (float)(2.0 * sn / e);
+      cf[3 * i + 1] = (float)(sig * sn);
+      cf[3 * i + 2] = (float)cc;
+      sig = sn;
+    }
+  }
+  if (cudaMemcpyAsync(b->d_coef, b->h_coef.data(), b->h_coef.size() * sizeof(float),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return bfail(b, CS_ERR_CUDA, "coefficient upload failed");
+  // descriptors (caller and workspace pointers)
+  std::vector<void*> key;
+  key.push_back(work);
+  for (int ci = 0; ci < nc; ++ci) {
+    if (!X[ci] || ld[ci] < b->ctxs[ci]->host.d) return bfail(b, CS_ERR_ARG, "bad block or ld");
+    b->h_cl[ci].X = X[ci];
+    b->h_cl[ci].ld = ld[ci];
+    b->h_cl[ci].Yalt = reinterpret_cast<float*>((char*)work + b->off_alt[ci]);
+    b->h_cl[ci].G = reinterpret_cast<float*>((char*)work + b->off_G[ci]);
+    key.push_back(X[ci]);
+    key.push_back((void*)(intptr_t)ld[ci]);
+  }
+  if (cudaMemcpyAsync(b->d_cl, b->h_cl.data(), nc * sizeof(BCluster), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return bfail(b, CS_ERR_CUDA, "descriptor upload failed");
+  // (re)capture the graph when the pointers or the variant changed
+  if (!b->graph || key != b->graph_key || b->graph_variant != b->variant) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+      return bfail(b, CS_ERR_CUDA, "stream creation failed");
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    const size_t ctr_bytes = (1 + 3 * (size_t)nc) * sizeof(int);
+    for (int step = 1; step <= b->degree && e == cudaSuccess; ++step) {
+      e = cudaMemsetAsync(b->d_ctr, 0, ctr_bytes, cap);
+      if (e == cudaSuccess) e = launch_variant_step(b, b->variant, step, cap);
+    }
+    if (e == cudaSuccess && (b->degree & 1)) {
+      dim3 grid(64, nc);
+      k_batch_copy_back<<<grid, 256, 0, cap>>>(b->d_cl, nc);
+      e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e2 == cudaSuccess) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return bfail(b, CS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    b->graph_key = key;
+    b->graph_variant = b->variant;
+  }
+  if (cudaGraphLaunch(b->graph, st) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "graph launch failed");
+  for (cs_ctx* c : b->ctxs) c->launches += b->degree + ((b->degree & 1) ? 1 : 0);
+  return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree,
+                          cs_batch** out) {
+  if (!out || n < 1 || !ctxs || !n_s || degree < 1) return CS_ERR_ARG;
+  *out = nullptr;
+  cs_batch* b = new (std::nothrow) cs_batch();
+  if (!b) return CS_ERR_ALLOC;
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->n_s.assign(n_s, n_s + n);
+  b->degree = degree;
+  b->device = ctxs[0]->device;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (bytes + 255) & ~size_t(255);
+    return at;
+  };
+  for (int i = 0; i < n; ++i) {
+    cs_ctx* c = ctxs[i];
+    if (!c || !c->has_device || c->device != b->device || !c->has_potential || c->n_p > 0 ||
+        n_s[i] < 1) {
+      delete b;
+      return CS_ERR_ARG;
+    }
+    const HostTables& H = c->host;
+    BCluster bc{};
+    bc.ang = AngArgs<float>{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s[i], c->d32.theta,
+                            c->d32.trig, c->d32.wv, c->d32.wkj};
+    bc.N = H.N;
+    bc.rad = c->d32.rad;
+    bc.half_lambda = c->d32.half_lambda;
+    bc.ld_alt = H.d;
+    b->h_cl.push_back(bc);
+    b->off_alt.push_back(take((size_t)H.d * n_s[i] * sizeof(float)));
+    b->off_G.push_back(take((size_t)H.n_r * H.L * H.L * n_s[i] * sizeof(float)));
+  }
+  for (int i = 0; i < n; ++i)  // tuner's copy of the blocks
+    b->off_bk.push_back(take((size_t)ctxs[i]->host.d * n_s[i] * sizeof(float)));
+  b->ws_bytes = off;
+  cudaSetDevice(b->device);
+  b->h_coef.assign((size_t)n * degree * 3, 0.f);
+  if (cudaMalloc((void**)&b->d_cl, n * sizeof(BCluster)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_coef, b->h_coef.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_ctr, (1 + 3 * (size_t)n) * sizeof(int)) != cudaSuccess) {
+    cs_batch_free(b);
+    return CS_ERR_ALLOC;
+  }
+  for (int i = 0; i < n; ++i) b->h_cl[i].coef = b->d_coef + (size_t)i * degree * 3;
+  // default variant: the first that fits shared memory
+  for (int v = 0; v < kNumVariants; ++v)
+    if (variant_smem(b->ctxs, v) <= 227 * 1024) {
+      b->variant = v;
+      break;
+    }
+  if (b->variant < 0 || build_items(b, b->variant) != CS_OK) {
+    cs_batch_free(b);
+    return CS_ERR_ARG;
+  }
+  *out = b;
+  return CS_OK;
+}
+
+cs_status cs_batch_free(cs_batch* b) {
+  if (!b) return CS_OK;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->d_cl) cudaFree(b->d_cl);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_coef) cudaFree(b->d_coef);
+  if (b->d_ctr) cudaFree(b->d_ctr);
+  delete b;
+  return CS_OK;
+}
+
+cs_status cs_batch_workspace_bytes(const cs_batch* b, size_t* bytes) {
+  if (!b || !bytes) return CS_ERR_ARG;
+  *bytes = b->ws_bytes;
+  return CS_OK;
+}
+
+cs_status cs_batch_cheb_filter(cs_batch* b, float* const* X, const long long* ld, const double* a,
+                               const double* bb, const double* a0, void* work, cs_stream stream) {
+  if (!b || !X || !ld || !a || !bb || !a0 || !work) return bfail(b, CS_ERR_ARG, "NULL argument");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "cudaSetDevice failed");
+  return run_filter(b, X, ld, a, bb, a0, work, (cudaStream_t)stream);
+}
+
+cs_status cs_batch_tune(cs_batch* b, float* const* X, const long long* ld, const double* a,
+                        const double* bb, const double* a0, void* work, cs_stream stream,
+                        int* chosen, float* best_ms) {
+  if (!b || !X || !ld || !a || !bb || !a0 || !work) return bfail(b, CS_ERR_ARG, "NULL argument");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = (int)b->ctxs.size();
+  // keep the blocks: every trial runs the filter in place
+  auto copy_all = [&](bool save) {
+    for (int i = 0; i < nc; ++i) {
+      const size_t w = (size_t)b->ctxs[i]->host.d * sizeof(float);
+      char* bk = (char*)work + b->off_bk[i];
+      cudaError_t e = save ? cudaMemcpy2DAsync(bk, w, X[i], ld[i] * sizeof(float), w, b->n_s[i],
+                                               cudaMemcpyDeviceToDevice, st)
+                           : cudaMemcpy2DAsync(X[i], ld[i] * sizeof(float), bk, w, w, b->n_s[i],
+                                               cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (copy_all(true) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "backup copy failed");
+  float best = 1e30f;
+  int best_v = b->variant;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (variant_smem(b->ctxs, v) > 227 * 1024) continue;
+    b->variant = v;
+    cs_status s = build_items(b, v);
+    if (s != CS_OK) return s;
+    // one untimed run (capture + warm-up), one timed run
+    for (int rep = 0; rep < 2; ++rep) {
+      if (copy_all(false) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "restore copy failed");
+      if (rep == 1) cudaEventRecord(e0, st);
+      if ((s = run_filter(b, X, ld, a, bb, a0, work, st)) != CS_OK) return s;
+      if (rep == 1) cudaEventRecord(e1, st);
+    }
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = best_v;
+  cs_status s = build_items(b, best_v);
+  if (s != CS_OK) return s;
+  if (copy_all(false) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "restore copy failed");
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "sync failed");
+  if (chosen) *chosen = best_v;
+  if (best_ms) *best_ms = best;
+  return CS_OK;
+}
+
+const char* cs_batch_last_error(const cs_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"

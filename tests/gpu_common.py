@@ -41,6 +41,8 @@ _WORKLOADS = {}
 
 
 def register(w):
+    old = _WORKLOADS.get(w.name)
+    assert old is None or old == w, f"two different workloads named {w.name}"
     _WORKLOADS[w.name] = w
     return w.name
 

@@ -257,9 +257,10 @@ def batched_clusters(count: int = 96, seed0: int = 4000) -> list:
     for i in range(count):
         u = uniform(seed0 + i, 4)
         natoms = 4 + int(u[0] * 45)  # 4 .. 48
-        r_place = 1.75 * (natoms / 0.25) ** (1.0 / 3.0) - 1.75
+        r_place = 1.75 * (natoms / 0.15) ** (1.0 / 3.0) - 1.75  # packing fraction 0.15
         rmin = max(8.0, r_place + 6.0)
-        R = rmin + (16.0 - rmin) * u[1] if rmin < 16.0 else rmin
+        R = rmin + (16.0 - rmin) * u[1] if rmin < 16.0 else 16.0
+        r_place = min(r_place, R - 6.0)
         lmax = int(round(12 + 20 * (R - 8.0) / 8.0))
         nmax = int(round(24 + 32 * (R - 8.0) / 8.0))
         n_s = min(128, int(math.ceil(2.4 * natoms)))
@@ -275,7 +276,8 @@ def batched_clusters(count: int = 96, seed0: int = 4000) -> list:
 def small_cluster(lmax=6, nmax=8, n_r=20, n_theta=14, n_phi=28, R=8.0, n_s=12,
                   natoms=3, seed=7001, potential="erf_cluster") -> Workload:
     """A small erf cluster for tests that compare against dense matrices."""
-    return Workload(f"small_l{lmax}_n{nmax}", R=R, lmax=lmax, nmax=nmax, n_r=n_r,
+    name = f"small_l{lmax}_n{nmax}_r{n_r}x{n_theta}x{n_phi}_R{R:g}_s{n_s}_a{natoms}_{seed}_{potential}"
+    return Workload(name, R=R, lmax=lmax, nmax=nmax, n_r=n_r,
                     n_theta=n_theta, n_phi=n_phi, radial_rule="gauss_legendre", n_s=n_s,
                     degree=8, potential=potential, natoms=natoms, atom_seed=seed,
                     r_place=3.0, min_sep=2.0, x_seed=seed + 1, n_want=n_s // 2,
