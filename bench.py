@@ -44,6 +44,29 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def reduce_max_time(local_ms: float, world: int, device=None) -> float:
+    """Max over ranks of a rank's timed milliseconds (the slowest rank sets the job time).
+    Uses the process group only for timing; nothing of the data path crosses ranks."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(applies_per_step_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job applies/s: every rank filters its own block (weak scaling)."""
+    return world * applies_per_step_per_rank / (ms_per_step / 1e3)
+
+
+def rank_block_seed(base_seed: int, rank: int) -> int:
+    """Each rank draws its own state block (independent problems, no exchange)."""
+    return base_seed + 1000 * rank
+
+
 # ------------------------------------------------------------------ algorithmic work
 def algorithmic_flops(w, n_s):
     """Per-state flop counts of one H.X (FFT count for phi, parity-folded Legendre)."""
@@ -136,7 +159,7 @@ def run_ours(args):
     cs.cs_set_potential(ctx, torch.tensor(v, dtype=torch.float64, device=dev))
     d = ctx.d
     # each rank filters its own block of states (independent seeds)
-    X0h = W.gaussian_block(w.x_seed + 1000 * rank, d, n_s)
+    X0h = W.gaussian_block(rank_block_seed(w.x_seed, rank), d, n_s)
     X0 = torch.tensor(np.ascontiguousarray(X0h.T), device=dev)
     work = ctx.workspace(n_s, prec)
     theta = torch.empty(n_s, dtype=torch.float64, device=dev)
@@ -189,16 +212,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof_ms, prof_n = cs.cs_profile_end(ctx)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max_time(total_ms, world, device=dev)
         torch.distributed.barrier()
     if rank == 0:
         time.sleep(0.3)
         clocks.stop()
     ms_per_step = total_ms / args.steps
     applies_per_step = (degree + 1) * n_s
-    value = world * applies_per_step / (ms_per_step / 1e3)
+    value = job_value(applies_per_step, world, ms_per_step)
 
     # ---- end to end through the public API: host (pinned) X in, Ritz vectors + values out
     Xh = torch.empty_like(X0, device="cpu").pin_memory()
