@@ -84,6 +84,59 @@ def dense_flops(d, n):
     return 2 * (2.0 * d * n * n + 2.0 * d * n * n) + (2.0 * d * n * n + 4.0 * d * n * n)
 
 
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
+    """Per kernel class: launches, share of device time, algorithmic TFLOP/s and the fraction
+    of the pipe that bounds it; the dominant class becomes the `roofline` object."""
+    from paper_1404_3773_gb300 import CS_MIXED_BF16
+    names = cs.profile_class_names()
+    af = algorithmic_flops(w, n_s)
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained")
+    total = max(1e-9, sum(prof_ms))
+    classes = {}
+    for i, name in enumerate(names):
+        if prof_n[i] == 0:
+            continue
+        fam = name[:-4] if name.endswith("_f32") else name
+        f32 = name.endswith("_f32")
+        per_ms = prof_ms[i] / prof_n[i]
+        if fam in ("radial_synth", "radial_anal", "angular"):
+            flops = af[fam]
+        elif fam == "dense":
+            flops = dense_flops(d, n_s) / max(1.0, prof_n[i] / steps)
+        else:
+            flops = None
+        if f32 and prec == CS_MIXED_BF16 and fam.startswith("radial") and bf16:
+            bound, peak, src = "tensor", bf16, "measured bf16 sustained (MEASURED_PEAKS.json)"
+        elif f32:
+            bound, peak, src = "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        else:
+            bound, peak, src = "alu", FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s (GB300)"
+        ach = flops / (per_ms / 1e3) / 1e12 if flops else None
+        classes[name] = {"launches": int(prof_n[i]), "ms": round(prof_ms[i], 4),
+                         "share": round(prof_ms[i] / total, 4),
+                         "avg_launch_ms": round(per_ms, 5),
+                         "flops_per_launch": flops,
+                         "achieved": round(ach, 4) if ach else None,
+                         "bound": bound, "peak": round(peak, 3), "unit": "TFLOP/s",
+                         "frac": round(ach / peak, 4) if ach else None, "peak_source": src}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    c = classes[dom]
+    roofline = {"bound": c["bound"], "kernel": dom, "achieved": c["achieved"], "peak": c["peak"],
+                "unit": "TFLOP/s", "frac": c["frac"], "traffic": None,
+                "peak_source": c["peak_source"], "flops_per_launch": c["flops_per_launch"],
+                "avg_launch_ms": c["avg_launch_ms"], "share": c["share"]}
+    return roofline, classes
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -248,31 +301,7 @@ def run_ours(args):
         return
 
     # ---- roofline of the dominant kernel class (device time measured live above)
-    names = ["radial_synth", "angular", "radial_anal", "dense_fp64"]
-    dom = int(np.argmax(prof_ms))
-    per_launch_ms = prof_ms[dom] / max(1, prof_n[dom])
-    af = algorithmic_flops(w, n_s)
-    peak_dense = FP64_PEAK_TFLOPS
-    if names[dom] == "dense_fp64":
-        flops_per_launch = dense_flops(d, n_s) / max(1, prof_n[dom] / args.steps)
-        peak = peak_dense
-        kdtype = "f64"
-    else:
-        flops_per_launch = af[names[dom]]
-        # launches of the class run in the filter precision, one per step in FP64 (RR)
-        kdtype = "f64" if prec == CS_FP64 else "f32"
-        peak = FP64_PEAK_TFLOPS if prec == CS_FP64 else FP32_PEAK_TFLOPS
-    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": names[dom], "kernel_dtype": kdtype,
-                "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300)" if peak == FP64_PEAK_TFLOPS
-                else "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "flops_per_launch": flops_per_launch,
-                "avg_launch_ms": round(per_launch_ms, 5),
-                "share": {names[i]: round(prof_ms[i] / max(1e-9, sum(prof_ms)), 4)
-                          for i in range(4)},
-                "launches": {names[i]: int(prof_n[i]) for i in range(4)}}
+    roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps)
 
     batched = None if args.no_batched else batched_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
@@ -290,6 +319,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world} (independent state blocks)"},
         "roofline": roofline,
+        "kernel_classes": classes,
         "cpu_baseline": cpu,
         "e2e": {"value": round(world * applies_per_step / (e2e_ms / 1e3), 2),
                 "unit": "applies/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -71,8 +71,9 @@ typedef enum {
   CS_FP32 = 1,       /* FP32 storage and arithmetic (FP32 FMA pipe)                      */
   CS_MIXED_BF16 = 2  /* FP32 storage; the per-l radial contractions on the tensor cores
                         (tcgen05) with operands split into two BF16 terms (hi + lo, three
-                        products, FP32 accumulation); angular sums and the recurrence in
-                        FP32. Blocks are float. Not available with projectors.           */
+                        products, FP32 accumulation), and so are the two projector
+                        products; angular sums and the recurrence in FP32. Blocks are
+                        float.                                                           */
 } cs_precision;
 
 /* ------------------------------------------------------------------ basis / context */
@@ -114,7 +115,10 @@ cs_status cs_set_potential(cs_ctx* ctx, const double* v_grid, cs_stream stream);
 /* Non-local Kleinman-Bylander part (Sec. 2.3.2): n_p rank-one projectors h_i p_i (x) p_i.
  * p_coef: DEVICE, d x n_p column-major (ld = d), the projector coefficients in this
  * basis (for grid values use cs_forward_transform first). h: HOST, n_p couplings.
- * The context copies both (FP64 and FP32). n_p = 0 removes the projectors. */
+ * The context copies both: FP64, FP32 and the split-BF16 operand tables of the tensor-core
+ * products (4 + 4 + 4 + 4 bytes per coefficient, rounded up to 128-row x 64-column tiles),
+ * then synchronises the stream. n_p = 0 removes the projectors. CS_ERR_ALLOC when the
+ * tables do not fit in device memory. */
 cs_status cs_set_projectors(cs_ctx* ctx, int n_p, const double* p_coef, const double* h,
                             cs_stream stream);
 
@@ -193,10 +197,13 @@ cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degre
 
 /* Measurement hooks: between cs_profile_begin and cs_profile_end the library records a
  * CUDA event pair on the launching stream around every kernel it launches on ctx.
- * cs_profile_end synchronises, and writes per kernel class the summed device time (ms[4])
- * and the launch count (launches[4]); classes: 0 radial synthesis GEMMs, 1 angular
- * transforms (per radial node), 2 radial analysis GEMMs with the fused epilogue, 3 dense
- * FP64 linear algebra and conversions. */
+ * cs_profile_end synchronises, and writes per kernel class the summed device time
+ * (ms[CS_PROFILE_CLASSES]) and the launch count (launches[CS_PROFILE_CLASSES]). Class =
+ * family + 5 for launches in FP32 / mixed precision (FP64 launches: family alone); families:
+ * 0 radial synthesis GEMMs, 1 angular transforms (per radial node), 2 radial analysis GEMMs
+ * with the fused epilogue, 3 dense FP64 linear algebra and conversions, 4 Kleinman-Bylander
+ * projector products. */
+#define CS_PROFILE_CLASSES 10
 cs_status cs_profile_begin(cs_ctx* ctx);
 cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
 

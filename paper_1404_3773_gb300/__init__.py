@@ -353,11 +353,19 @@ def cs_profile_begin(ctx: Context):
     ctx.check(_lib.cs_profile_begin(ctx.handle))
 
 
+PROFILE_FAMILIES = ("radial_synth", "angular", "radial_anal", "dense", "kb")
+PROFILE_CLASSES = 2 * len(PROFILE_FAMILIES)
+
+
+def profile_class_names():
+    """Names of the profile classes: family, then family + '_f32' for FP32 / mixed launches."""
+    return list(PROFILE_FAMILIES) + [f + "_f32" for f in PROFILE_FAMILIES]
+
+
 def cs_profile_end(ctx: Context):
-    """Returns (ms[4], launches[4]) per kernel class: radial synthesis, angular, radial
-    analysis + epilogue, dense linear algebra."""
-    ms = (ctypes.c_double * 4)()
-    n = (_ll * 4)()
+    """Returns (ms[10], launches[10]) per kernel class (profile_class_names())."""
+    ms = (ctypes.c_double * PROFILE_CLASSES)()
+    n = (_ll * PROFILE_CLASSES)()
     ctx.check(_lib.cs_profile_end(ctx.handle, ms, n))
     return list(ms), list(n)
 

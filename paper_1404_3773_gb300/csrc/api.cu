@@ -12,6 +12,7 @@
 
 #include "cs_internal.h"
 #include "hx_kernels.cuh"
+#include "kb_tc.h"
 
 using namespace cs;
 
@@ -22,7 +23,7 @@ thread_local std::string g_init_error;
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, total;
+  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, kbtc, total;
 };
 
 constexpr int kMaxLanczos = 64;
@@ -56,6 +57,8 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.status = take(64 * sizeof(int));
   // last, so that every other offset is the same for both precisions
   o.X32 = take(prec != CS_FP64 ? d * ns * 4 : 0);
+  // scratch of the tensor-core projector products (mixed precision with projectors)
+  o.kbtc = take(prec == CS_MIXED_BF16 && np ? kb_tc_work_bytes(kb_tc_shape(T.d, (int)np, n_s)) : 0);
   o.total = off;
   return o;
 }
@@ -115,6 +118,9 @@ struct ProfScope {
     (ctx)->launches += (nk);               \
   } while (0)
 #define CS_LAUNCH(ctx, nk, expr) CS_LAUNCH_CLS(ctx, 3, nk, expr)
+constexpr int kProfFamilies = 5;  // classes per precision (see cs_ctx::prof)
+template <typename T>
+constexpr int prof_cls(int family) { return family + (sizeof(T) == 4 ? kProfFamilies : 0); }
 
 cs_status need_device(cs_ctx* c) {
   if (!c) return CS_ERR_ARG;
@@ -191,16 +197,27 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   T* G = reinterpret_cast<T*>(work + lay.G);
   const T* kb = nullptr;
   if (c->n_p > 0) {
-    if (sizeof(T) != 8) return fail(c, CS_ERR_STATE, "projectors are supported with CS_FP64 only");
-    double* Wkb = reinterpret_cast<double*>(work + lay.Wkb);
-    double* kbZ = reinterpret_cast<double*>(work + lay.kbZ);
-    double* part = reinterpret_cast<double*>(work + lay.part);
-    // Wkb = P^T X ; kbZ = (P diag h) Wkb   (Sec. 2.3.2: a pair of matrix products)
-    CS_LAUNCH(c, 2, launch_gram(c->d64.pcoef, H.d, reinterpret_cast<const double*>(X), ldx, H.d,
-                                c->n_p, n_s, Wkb, c->n_p, part, st));
-    CS_LAUNCH(c, 1, launch_gemm_nn(c->d64.h, H.d, Wkb, c->n_p, H.d, c->n_p, n_s, 1.0, 0.0, kbZ,
-                                   H.d, st));
-    kb = reinterpret_cast<const T*>(kbZ);
+    // kb = P diag(h) P^T X  (Sec. 2.3.2: a pair of matrix products)
+    T* kbZ = reinterpret_cast<T*>(work + lay.kbZ);
+    if (tc) {
+      const Layout lm = layout(c, n_s, CS_MIXED_BF16);
+      const KbTcShape ks = kb_tc_shape(H.d, c->n_p, n_s);
+      int nl = 0;
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 4,
+                    launch_kb_tc(c->kb_tabA, c->kb_tabB, ks, reinterpret_cast<const float*>(X),
+                                 ldx, c->d32.h, reinterpret_cast<float*>(kbZ), H.d,
+                                 work + lm.kbtc, c->dev_err, st, &nl));
+    } else {
+      T* Wkb = reinterpret_cast<T*>(work + lay.Wkb);
+      T* part = reinterpret_cast<T*>(work + lay.part);
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 2,
+                    launch_gram<T>(D.pcoef, H.d, X, ldx, H.d, c->n_p, n_s, Wkb, c->n_p, part, st));
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 1, launch_scale_rows<T>(Wkb, c->n_p, n_s, c->n_p, D.h, st));
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 1,
+                    launch_gemm_nn<T>(D.pcoef, H.d, Wkb, c->n_p, H.d, c->n_p, n_s, 1.0, 0.0, kbZ,
+                                      H.d, st));
+    }
+    kb = kbZ;
   }
   TcTables tt;
   tt.synth = c->tc_synth;
@@ -211,14 +228,14 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   tt.kpad_anal = c->tc_kpad_anal;
   if (tc) {
     if (sizeof(T) != 4) return fail(c, CS_ERR_ARG, "tensor-core path needs float blocks");
-    CS_LAUNCH_CLS(c, 0, 1, launch_tc_radial_synth(tt, H, reinterpret_cast<const float*>(X), ldx,
+    CS_LAUNCH_CLS(c, prof_cls<T>(0), 1, launch_tc_radial_synth(tt, H, reinterpret_cast<const float*>(X), ldx,
                                                   reinterpret_cast<float*>(G), n_s, c->dev_err,
                                                   st));
   } else {
-    CS_LAUNCH_CLS(c, 0, 1, launch_radial_synth<T>(X, ldx, G, D.rad, H.L, H.N, H.n_r, n_s, st));
+    CS_LAUNCH_CLS(c, prof_cls<T>(0), 1, launch_radial_synth<T>(X, ldx, G, D.rad, H.L, H.N, H.n_r, n_s, st));
   }
   AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj};
-  CS_LAUNCH_CLS(c, 1, 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
+  CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
   Epilogue<T> ep;
   ep.mode = mode;
   ep.out = out;
@@ -233,11 +250,11 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   ep.cB = (T)cB;
   ep.cshift = (T)csh;
   if (tc) {
-    CS_LAUNCH_CLS(c, 2, 1, launch_tc_radial_anal(tt, H, reinterpret_cast<const float*>(G), n_s,
+    CS_LAUNCH_CLS(c, prof_cls<T>(2), 1, launch_tc_radial_anal(tt, H, reinterpret_cast<const float*>(G), n_s,
                                                  *reinterpret_cast<const Epilogue<float>*>(&ep),
                                                  c->dev_err, st));
   } else {
-    CS_LAUNCH_CLS(c, 2, 1, launch_radial_anal<T>(G, D.rad, H.L, H.N, H.n_r, n_s, ep, st));
+    CS_LAUNCH_CLS(c, prof_cls<T>(2), 1, launch_radial_anal<T>(G, D.rad, H.L, H.N, H.n_r, n_s, ep, st));
   }
   return CS_OK;
 }
@@ -458,6 +475,8 @@ cs_status cs_basis_free(cs_ctx* c) {
     if (c->w_r_dev) cudaFree(c->w_r_dev);
     if (c->tc_synth) cudaFree(c->tc_synth);
     if (c->tc_anal) cudaFree(c->tc_anal);
+    if (c->kb_tabA) cudaFree(c->kb_tabA);
+    if (c->kb_tabB) cudaFree(c->kb_tabB);
     if (c->dev_err) cudaFree(c->dev_err);
   }
   delete c;
@@ -515,28 +534,29 @@ cs_status cs_set_projectors(cs_ctx* c, int n_p, const double* p_coef, const doub
   if (n_p < 0 || (n_p > 0 && (!p_coef || !h))) return fail(c, CS_ERR_ARG, "bad projector arguments");
   cudaStream_t st = (cudaStream_t)stream;
   CS_CHECK_CUDA(c, cudaStreamSynchronize(st));
-  if (c->d64.pcoef) cudaFree(c->d64.pcoef);
-  if (c->d64.h) cudaFree(c->d64.h);
-  c->d64.pcoef = nullptr;
-  c->d64.h = nullptr;
+  for (void** p : {(void**)&c->d64.pcoef, (void**)&c->d64.h, (void**)&c->d32.pcoef,
+                   (void**)&c->d32.h, &c->kb_tabA, &c->kb_tabB}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
   c->n_p = 0;
   if (n_p == 0) return CS_OK;
   const size_t d = (size_t)c->host.d;
+  const KbTcShape ks = kb_tc_shape(c->host.d, n_p, 1);
   if (cudaMalloc((void**)&c->d64.pcoef, d * n_p * 8) != cudaSuccess ||
-      cudaMalloc((void**)&c->d64.h, d * n_p * 8) != cudaSuccess)
+      cudaMalloc((void**)&c->d32.pcoef, d * n_p * 4) != cudaSuccess ||
+      cudaMalloc(&c->kb_tabA, ks.tabA_bytes) != cudaSuccess ||
+      cudaMalloc(&c->kb_tabB, ks.tabB_bytes) != cudaSuccess)
     return fail(c, CS_ERR_ALLOC, "cudaMalloc of projector tables failed");
+  cs_status r;
+  std::vector<double> hv(h, h + n_p);
+  if ((r = upload<double>(c, &c->d64.h, hv)) != CS_OK) return r;
+  if ((r = upload<float>(c, &c->d32.h, hv)) != CS_OK) return r;
   CS_CHECK_CUDA(c, cudaMemcpyAsync(c->d64.pcoef, p_coef, d * n_p * 8, cudaMemcpyDeviceToDevice, st));
-  // d64.h holds P diag(h): column i scaled by h_i (built with a diagonal GEMM)
-  std::vector<double> diag((size_t)n_p * n_p, 0.0);
-  for (int i = 0; i < n_p; ++i) diag[(size_t)i * n_p + i] = h[i];
-  double* ddev = nullptr;
-  if (cudaMalloc((void**)&ddev, diag.size() * 8) != cudaSuccess)
-    return fail(c, CS_ERR_ALLOC, "cudaMalloc failed");
-  CS_CHECK_CUDA(c, cudaMemcpyAsync(ddev, diag.data(), diag.size() * 8, cudaMemcpyHostToDevice, st));
-  CS_LAUNCH(c, 1, launch_gemm_nn(c->d64.pcoef, (long long)d, ddev, n_p, (long long)d, n_p, n_p,
-                                 1.0, 0.0, c->d64.h, (long long)d, st));
+  CS_LAUNCH(c, 1, launch_convert_f64_to_f32(c->d64.pcoef, (long long)d, c->d32.pcoef,
+                                            (long long)d, (long long)d, n_p, st));
+  CS_LAUNCH(c, 2, build_kb_tc_tables(c->d64.pcoef, (long long)d, n_p, c->kb_tabA, c->kb_tabB, st));
   CS_CHECK_CUDA(c, cudaStreamSynchronize(st));
-  cudaFree(ddev);
   c->n_p = n_p;
   return CS_OK;
 }
@@ -718,8 +738,6 @@ cs_status cs_chfsi(cs_ctx* c, int n_s, int n_want, double* X, long long ld, int 
     return fail(c, CS_ERR_ARG, "bad ChFSI arguments");
   if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
     return fail(c, CS_ERR_ARG, "unknown precision");
-  if (prec == CS_MIXED_BF16 && c->n_p > 0)
-    return fail(c, CS_ERR_STATE, "CS_MIXED_BF16 does not apply projectors");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   const HostTables& H = c->host;
   cudaStream_t st = (cudaStream_t)stream;
@@ -765,8 +783,6 @@ cs_status cs_chfsi_step(cs_ctx* c, int n_s, double* X, long long ld, int degree,
   if (n_s > 1024) return fail(c, CS_ERR_ARG, "n_s > 1024 not supported");
   if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
     return fail(c, CS_ERR_ARG, "unknown precision");
-  if (prec == CS_MIXED_BF16 && c->n_p > 0)
-    return fail(c, CS_ERR_STATE, "CS_MIXED_BF16 does not apply projectors");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   return chfsi_step_core(c, n_s, X, ld, degree, a, b, a0, prec, theta, resid, (char*)work,
                          (cudaStream_t)stream);
@@ -792,7 +808,7 @@ cs_status cs_profile_end(cs_ctx* c, double* ms, long long* launches) {
   cs_status s = need_device(c);
   if (s != CS_OK) return s;
   if (!ms || !launches) return fail(c, CS_ERR_ARG, "NULL output");
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < CS_PROFILE_CLASSES; ++i) {
     ms[i] = 0.0;
     launches[i] = 0;
   }
@@ -800,7 +816,7 @@ cs_status cs_profile_end(cs_ctx* c, double* ms, long long* launches) {
     CS_CHECK_CUDA(c, cudaEventSynchronize(r.b));
     float t = 0.f;
     CS_CHECK_CUDA(c, cudaEventElapsedTime(&t, r.a, r.b));
-    if (r.cls >= 0 && r.cls < 4) {
+    if (r.cls >= 0 && r.cls < CS_PROFILE_CLASSES) {
       ms[r.cls] += t;
       launches[r.cls] += 1;
     }

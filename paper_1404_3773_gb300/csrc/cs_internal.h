@@ -49,7 +49,7 @@ struct DevTables {
   T* wkj = nullptr;        // [k][j] w_r w_t 2 pi / n_phi
   T* half_lambda = nullptr;// [alpha]
   T* pcoef = nullptr;      // [p][alpha] (d x n_p column-major)
-  T* h = nullptr;          // [p]
+  T* h = nullptr;          // [p] projector couplings
 };
 
 }  // namespace cs
@@ -67,10 +67,14 @@ struct cs_ctx {
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
   int tc_mt_synth = 0, tc_kpad_synth = 0, tc_mt_anal = 0, tc_kpad_anal = 0;
+  void* kb_tabA = nullptr;   // split-BF16 projector operands (kb_tc.cu), set with the projectors
+  void* kb_tabB = nullptr;
   int* dev_err = nullptr;    // device error word (bounded waits); 0 = ok
   std::string err;
   long long launches = 0;
-  // measurement hooks (cs_profile_begin / cs_profile_end)
+  // measurement hooks (cs_profile_begin / cs_profile_end): class = kernel family
+  // (0 radial synthesis, 1 angular, 2 radial analysis, 3 dense FP64, 4 projectors) + 5 when
+  // the launch runs in FP32 / mixed precision
   bool prof = false;
   struct ProfRec {
     int cls;

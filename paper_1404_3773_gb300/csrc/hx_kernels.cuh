@@ -73,14 +73,19 @@ cudaError_t launch_tc_radial_anal(const TcTables& tt, const HostTables& H, const
 // C (na x nb, column-major, ldc) = A^T B, A: d x na (lda), B: d x nb (ldb), split over d
 // into chunks whose partial products land in `partial` (gram_partial_elems doubles) and
 // are then summed in a fixed order (deterministic).
+// F = double or float (partials and sums in F).
 size_t gram_partial_elems(long long d, int na, int nb);
-cudaError_t launch_gram(const double* A, long long lda, const double* B, long long ldb,
-                        long long d, int na, int nb, double* C, int ldc, double* partial,
-                        cudaStream_t stream);
+template <typename F>
+cudaError_t launch_gram(const F* A, long long lda, const F* B, long long ldb, long long d, int na,
+                        int nb, F* C, int ldc, F* partial, cudaStream_t stream);
 // C (d x n, ldc) = alpha * A (d x k, lda) * Q (k x n, ldq) + beta * C. A must not overlap C.
-cudaError_t launch_gemm_nn(const double* A, long long lda, const double* Q, int ldq,
-                           long long d, int k, int n, double alpha, double beta, double* C,
-                           long long ldc, cudaStream_t stream);
+template <typename F>
+cudaError_t launch_gemm_nn(const F* A, long long lda, const F* Q, int ldq, long long d, int k,
+                           int n, double alpha, double beta, F* C, long long ldc,
+                           cudaStream_t stream);
+// y[p + s ld] *= h[p] for p < n_p, s < S
+template <typename F>
+cudaError_t launch_scale_rows(F* y, int n_p, int S, int ld, const F* h, cudaStream_t stream);
 // From the Gram matrix M (n x n): U = D R^{-1}, D = diag(M)^(-1/2), D M D = R^T R.
 // work: n*n + n doubles. status[0] = 0 ok, else 1 + index of the failing pivot.
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,

@@ -45,37 +45,37 @@ size_t gram_partial_elems(long long d, int na, int nb) {
   return (size_t)chunks * (size_t)na * (size_t)nb;
 }
 
-template <int U>
-__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ A, long long lda,
-                                                       const double* __restrict__ B,
+template <typename F, int U>
+__global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, long long lda,
+                                                       const F* __restrict__ B,
                                                        long long ldb, long long d, int na,
                                                        int nb, long long rows,
-                                                       double* __restrict__ partial) {
+                                                       F* __restrict__ partial) {
   constexpr int T = 16 * U;
   const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
   const int chunk = blockIdx.z;
   const long long r0 = (long long)chunk * rows;
   const long long r1 = min(d, r0 + rows);
-  __shared__ double As[GK][T + 1];
-  __shared__ double Bs[GK][T + 1];
+  __shared__ F As[GK][T + 1];
+  __shared__ F Bs[GK][T + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[U][U];
+  F acc[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = F(0);
   for (long long rb = r0; rb < r1; rb += GK) {
     for (int idx = tid; idx < GK * T; idx += 256) {
       int rr = idx % GK, cc = idx / GK;
       long long r = rb + rr;
       int i = i0 + cc, j = j0 + cc;
-      As[rr][cc] = (r < r1 && i < na) ? A[r + (long long)i * lda] : 0.0;
-      Bs[rr][cc] = (r < r1 && j < nb) ? B[r + (long long)j * ldb] : 0.0;
+      As[rr][cc] = (r < r1 && i < na) ? A[r + (long long)i * lda] : F(0);
+      Bs[rr][cc] = (r < r1 && j < nb) ? B[r + (long long)j * ldb] : F(0);
     }
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < GK; ++rr) {
-      double a[U], b[U];
+      F a[U], b[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) a[u] = As[rr][tx + 16 * u];
 #pragma unroll
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
     }
     __syncthreads();
   }
-  double* P = partial + (size_t)chunk * na * nb;
+  F* P = partial + (size_t)chunk * na * nb;
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -98,79 +98,80 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
 }
 
 // 32 elements x 8 chunk slices per 256-thread block; slices summed in a fixed order
-__global__ void k_gram_reduce(const double* __restrict__ partial, int chunks, int na, int nb,
-                              double* __restrict__ C, int ldc) {
-  __shared__ double red[8][33];
+template <typename F>
+__global__ void k_gram_reduce(const F* __restrict__ partial, int chunks, int na, int nb,
+                              F* __restrict__ C, int ldc) {
+  __shared__ F red[8][33];
   const int el = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const int e = blockIdx.x * 32 + el;
   const int E = na * nb;
-  double s = 0.0;
+  F s = F(0);
   if (e < E)
     for (int c = sl; c < chunks; c += 8) s += partial[(size_t)c * E + e];
   red[sl][el] = s;
   __syncthreads();
   if (sl == 0 && e < E) {
-    double t = 0.0;
+    F t = F(0);
     for (int k = 0; k < 8; ++k) t += red[k][el];
     int i = e % na, j = e / na;
     C[i + (size_t)j * ldc] = t;
   }
 }
 
-cudaError_t launch_gram(const double* A, long long lda, const double* B, long long ldb,
-                        long long d, int na, int nb, double* C, int ldc, double* partial,
-                        cudaStream_t stream) {
+template <typename F>
+cudaError_t launch_gram(const F* A, long long lda, const F* B, long long ldb, long long d, int na,
+                        int nb, F* C, int ldc, F* partial, cudaStream_t stream) {
   int u, ta, tb, chunks;
   long long rows;
   gram_shape(d, na, nb, u, ta, tb, chunks, rows);
   dim3 grid(ta, tb, chunks);
   switch (u) {
-    case 1: k_gram_partial<1><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 2: k_gram_partial<2><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 3: k_gram_partial<3><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 4: k_gram_partial<4><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 5: k_gram_partial<5><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    default: k_gram_partial<6><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 1: k_gram_partial<F, 1><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 2: k_gram_partial<F, 2><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 3: k_gram_partial<F, 3><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 4: k_gram_partial<F, 4><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 5: k_gram_partial<F, 5><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    default: k_gram_partial<F, 6><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
   }
   int tot = na * nb;
-  k_gram_reduce<<<(tot + 31) / 32, 256, 0, stream>>>(partial, chunks, na, nb, C, ldc);
+  k_gram_reduce<F><<<(tot + 31) / 32, 256, 0, stream>>>(partial, chunks, na, nb, C, ldc);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ C = alpha A Q + beta C
 // 64 rows x (16U) columns per CTA; U from n so that 80 states are one column tile.
-template <int U>
-__global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, long long lda,
-                                                  const double* __restrict__ Q, int ldq,
-                                                  long long d, int K, int n, double alpha,
-                                                  double beta, double* C, long long ldc) {
+template <typename F, int U>
+__global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long long lda,
+                                                  const F* __restrict__ Q, int ldq,
+                                                  long long d, int K, int n, F alpha,
+                                                  F beta, F* C, long long ldc) {
   constexpr int BM = 64, BN = 16 * U;
   const long long r0 = (long long)blockIdx.x * BM;
   const int j0 = blockIdx.y * BN;
-  __shared__ double As[GK][BM + 1];  // As[k][r]
-  __shared__ double Qs[GK][BN + 1];  // Qs[k][j]
+  __shared__ F As[GK][BM + 1];  // As[k][r]
+  __shared__ F Qs[GK][BN + 1];  // Qs[k][j]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][U];
+  F acc[4][U];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = F(0);
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int idx = tid; idx < GK * BM; idx += 256) {
       int rr = idx % BM, kk = idx / BM;
       long long r = r0 + rr;
       int k = k0 + kk;
-      As[kk][rr] = (r < d && k < K) ? A[r + (long long)k * lda] : 0.0;
+      As[kk][rr] = (r < d && k < K) ? A[r + (long long)k * lda] : F(0);
     }
     for (int idx = tid; idx < GK * BN; idx += 256) {
       int kk = idx % GK, jj = idx / GK;
       int k = k0 + kk, j = j0 + jj;
-      Qs[kk][jj] = (k < K && j < n) ? Q[k + (long long)j * ldq] : 0.0;
+      Qs[kk][jj] = (k < K && j < n) ? Q[k + (long long)j * ldq] : F(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[U];
+      F a[4], b[U];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
 #pragma unroll
@@ -190,27 +191,58 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ A, l
     for (int u = 0; u < 4; ++u) {
       long long r = r0 + tx + 16 * u;
       if (r >= d) continue;
-      double* c = C + r + (long long)j * ldc;
-      *c = (beta == 0.0) ? alpha * acc[u][v] : fma(alpha, acc[u][v], beta * *c);
+      F* c = C + r + (long long)j * ldc;
+      *c = (beta == F(0)) ? alpha * acc[u][v] : fma(alpha, acc[u][v], beta * *c);
     }
   }
 }
 
-cudaError_t launch_gemm_nn(const double* A, long long lda, const double* Q, int ldq,
-                           long long d, int k, int n, double alpha, double beta, double* C,
-                           long long ldc, cudaStream_t stream) {
+template <typename F>
+cudaError_t launch_gemm_nn(const F* A, long long lda, const F* Q, int ldq, long long d, int k,
+                           int n, double alpha, double beta, F* C, long long ldc,
+                           cudaStream_t stream) {
   const int u = tile_u(n);
   dim3 grid((unsigned)((d + 63) / 64), (n + 16 * u - 1) / (16 * u));
   switch (u) {
-    case 1: k_gemm_nn<1><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
-    case 2: k_gemm_nn<2><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
-    case 3: k_gemm_nn<3><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
-    case 4: k_gemm_nn<4><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
-    case 5: k_gemm_nn<5><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
-    default: k_gemm_nn<6><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc); break;
+    case 1: k_gemm_nn<F, 1><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 2: k_gemm_nn<F, 2><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 3: k_gemm_nn<F, 3><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 4: k_gemm_nn<F, 4><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 5: k_gemm_nn<F, 5><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    default: k_gemm_nn<F, 6><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
   }
   return cudaGetLastError();
 }
+
+template cudaError_t launch_gram<double>(const double*, long long, const double*, long long,
+                                         long long, int, int, double*, int, double*,
+                                         cudaStream_t);
+template cudaError_t launch_gram<float>(const float*, long long, const float*, long long,
+                                        long long, int, int, float*, int, float*, cudaStream_t);
+template cudaError_t launch_gemm_nn<double>(const double*, long long, const double*, int,
+                                            long long, int, int, double, double, double*,
+                                            long long, cudaStream_t);
+template cudaError_t launch_gemm_nn<float>(const float*, long long, const float*, int, long long,
+                                           int, int, double, double, float*, long long,
+                                           cudaStream_t);
+
+// y[p + s ld] *= h[p]  (rows of an n_p x S block scaled by the projector couplings)
+template <typename F>
+__global__ void k_scale_rows(F* __restrict__ y, int n_p, int S, int ld, const F* __restrict__ h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_p * S) return;
+  const int p = i % n_p, s = i / n_p;
+  y[p + (size_t)s * ld] *= h[p];
+}
+
+template <typename F>
+cudaError_t launch_scale_rows(F* y, int n_p, int S, int ld, const F* h, cudaStream_t stream) {
+  const int n = n_p * S;
+  k_scale_rows<F><<<(n + 255) / 256, 256, 0, stream>>>(y, n_p, S, ld, h);
+  return cudaGetLastError();
+}
+template cudaError_t launch_scale_rows<double>(double*, int, int, int, const double*, cudaStream_t);
+template cudaError_t launch_scale_rows<float>(float*, int, int, int, const float*, cudaStream_t);
 
 // ------------------------------------------------------------------ Cholesky-QR factor
 // One CTA. With column scaling D = diag(M)^(-1/2): D M D = L L^T (right-looking Cholesky,

@@ -23,6 +23,10 @@ CASES = {
                                                n_s=3, seed=7101),
     "lmax0_single_state": W.small_cluster(lmax=0, nmax=9, n_r=12, n_theta=1, n_phi=2, n_s=1,
                                           seed=7201),
+    # lmax 60 on a thin radial grid: the angular kernels at the 400-atom cluster's angular
+    # size (120 x 240, 3721 harmonics) with an oracle that finishes in seconds
+    "lmax60_thin_radial": W.small_cluster(lmax=60, nmax=4, n_r=6, n_theta=120, n_phi=240,
+                                          R=10.0, n_s=5, natoms=4, seed=7601),
     "gauss_jacobi": W.Workload("gj_small", R=7.0, lmax=7, nmax=10, n_r=24, n_theta=16, n_phi=30,
                                radial_rule="gauss_jacobi_r2", n_s=9, degree=6,
                                potential="erf_cluster", natoms=3, atom_seed=7301, r_place=3.0,
@@ -49,7 +53,7 @@ def test_apply_H_fp64_matches_oracle(case):
     assert torch.all(HXd[:, ctx.d:] == 0)  # padding untouched
 
 
-@pytest.mark.parametrize("case", ["small_ragged", "ho_l10"])
+@pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "lmax60_thin_radial"])
 def test_apply_H_fp32_error(case):
     torch, cs = need_gpu()
     w = CASES[case]
@@ -143,7 +147,8 @@ def test_launch_count_advances():
     assert cs.cs_launch_count(ctx) - n0 == 3
 
 
-@pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "odd_theta_phi_not_mult4"])
+@pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "odd_theta_phi_not_mult4",
+                                  "lmax60_thin_radial"])
 def test_apply_H_mixed_bf16_error(case):
     """Split-BF16 tensor-core radial contractions (tcgen05) + FP32 angular sums: error vs
     the FP64 oracle within 1e-4 (split BF16 keeps about 16 significant bits)."""

@@ -54,3 +54,21 @@ def test_kb_projector_norm():
     norms = (p ** 2).sum(axis=1) * h ** 3
     assert np.allclose(norms, 1.0, atol=1e-6)
     assert list(hh) == [1.0, 0.5, 0.5, 0.5]
+
+
+def test_torch_generators_equal_numpy_ones():
+    """The torch evaluations used for large grids reproduce the numpy input functions."""
+    import torch
+
+    from workloads.device import erf_cluster_potential_t, kb_couplings, kb_projector_values_t
+    u = W.uniform(99, 3 * 500).reshape(500, 3) * 12.0 - 6.0
+    u[0] = [0.0, 0.0, 0.0]          # on an atom: series branch
+    atoms = W.place_atoms(98, 5, 4.0, 2.0)
+    u[1] = atoms[2] + 1e-5          # near an atom
+    v_np = W.erf_cluster_potential(u, atoms, 4.0, 0.8)
+    v_t = erf_cluster_potential_t(torch.tensor(u), atoms, 4.0, 0.8).numpy()
+    assert np.max(np.abs(v_np - v_t)) <= 1e-13 * np.max(np.abs(v_np))
+    p_np, h_np = W.kb_projector_values(u, atoms, rc=1.0)
+    p_t = kb_projector_values_t(torch.tensor(u), atoms, rc=1.0, first=1, count=3).numpy()
+    assert np.max(np.abs(p_np[4:16] - p_t)) <= 1e-14
+    assert np.array_equal(h_np, kb_couplings(5))
