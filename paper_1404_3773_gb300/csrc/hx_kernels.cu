@@ -272,26 +272,40 @@ static cudaError_t launch_angular_st(const AngArgs<T>& a, int st, T* G, T* gout,
   return cudaGetLastError();
 }
 
-// Which ANG_FULL kernel runs: the row-pair kernel (angular_rp.cu) when one of its tiles fits
-// in shared memory, else the row-stream kernel above. CS_ANGULAR_KERNEL=stream|rp|rpN
+// Which ANG_FULL kernel runs. FP32: the register-blocked kernel (angular_gm.cu) when its
+// tile fits in shared memory, else the row-pair kernel (angular_rp.cu); FP64: the row-pair
+// kernel; both fall back to the row-stream kernel above. CS_ANGULAR_KERNEL=gm|gmN|rp|rpN|stream
 // overrides the choice (N = tile variant), for tuning.
-template <typename T>
-static int angular_choice() {
+static int angular_choice(int& variant) {
+  variant = -1;
   const char* e = getenv("CS_ANGULAR_KERNEL");
-  if (e) {
-    if (e[0] == 's') return -2;
-    if (e[0] == 'r' && e[1] == 'p') return e[2] ? atoi(e + 2) : -1;
+  if (!e) return 0;
+  if (e[0] == 's') return 3;
+  if (e[0] == 'r' && e[1] == 'p') {
+    variant = e[2] ? atoi(e + 2) : -1;
+    return 2;
   }
-  return -1;
+  if (e[0] == 'g' && e[1] == 'm') {
+    variant = e[2] ? atoi(e + 2) : -1;
+    return 1;
+  }
+  return 0;
 }
 
 template <typename T>
 cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T* gin,
                            cudaStream_t stream) {
   if (mode == ANG_FULL) {
-    int choice = angular_choice<T>();
-    if (choice != -2) {
-      cudaError_t e = launch_angular_rp<T>(a, G, choice, stream);
+    int variant;
+    const int choice = angular_choice(variant);
+    if constexpr (sizeof(T) == 4) {
+      if (choice == 0 || choice == 1) {
+        cudaError_t e = launch_angular_gm(a, G, variant, stream);
+        if (e != cudaErrorInvalidConfiguration) return e;
+      }
+    }
+    if (choice != 3) {
+      cudaError_t e = launch_angular_rp<T>(a, G, choice == 2 ? variant : -1, stream);
       if (e != cudaErrorInvalidConfiguration) return e;
     }
   }

@@ -48,6 +48,10 @@ cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T
 template <typename T>
 cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream_t stream);
 
+// register-blocked FP32 angular kernel (angular_gm.cu); variant 0: 8 row pairs per chunk,
+// 1: 4; cudaErrorInvalidConfiguration when no tile fits in shared memory
+cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, int variant, cudaStream_t stream);
+
 template <typename T>
 cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,
                                 int n_r, int S, cudaStream_t stream);
