@@ -37,6 +37,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # x 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# double-float: one multiply-add (2 flops) costs 15 FP32 instructions (df64.cuh), so the
+# FP32 issue rate bounds it at 2/15 of the FP32 multiply-add rate
+DF64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 2 * 2 / 15
 
 
 def _rank_env():
@@ -105,8 +108,9 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
     for i, name in enumerate(names):
         if prof_n[i] == 0:
             continue
-        fam = name[:-4] if name.endswith("_f32") else name
-        f32 = name.endswith("_f32")
+        kind = "f32" if name.endswith("_f32") else ("df64" if name.endswith("_df64") else "f64")
+        fam = name.rsplit("_", 1)[0] if kind != "f64" else name
+        f32 = kind == "f32"
         per_ms = prof_ms[i] / prof_n[i]
         if fam in ("radial_synth", "radial_anal", "angular"):
             flops = af[fam]
@@ -118,6 +122,9 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
             bound, peak, src = "tensor", bf16, "measured bf16 sustained (MEASURED_PEAKS.json)"
         elif f32:
             bound, peak, src = "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        elif kind == "df64":
+            bound, peak, src = "alu", DF64_PEAK_TFLOPS, ("FP32 issue rate / 15 instructions "
+                                                         "per double-float multiply-add")
         else:
             bound, peak, src = "alu", FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s (GB300)"
         ach = flops / (per_ms / 1e3) / 1e12 if flops else None
@@ -204,13 +211,22 @@ def run_ours(args):
     import paper_1404_3773_gb300 as cs
     from paper_1404_3773_gb300 import CS_FP32, CS_FP64, CS_MIXED_BF16
 
-    prec = {"fp64": CS_FP64, "fp32": CS_FP32, "mixed": CS_MIXED_BF16}[args.precision]
+    from paper_1404_3773_gb300 import CS_DF64
+    PREC = {"fp64": CS_FP64, "fp32": CS_FP32, "mixed": CS_MIXED_BF16, "df64": CS_DF64}
+    NAME = {v: k for k, v in PREC.items()}
+    prec = PREC[args.precision]
     w = W.erf_cluster_32()
     n_s, degree = w.n_s, w.degree
     ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, local)
     v = w.potential_at(cs.grid_points(ctx))
     cs.cs_set_potential(ctx, torch.tensor(v, dtype=torch.float64, device=dev))
     d = ctx.d
+    # Rayleigh-Ritz projects an H X in the filter's precision ("same"), FP64 or double-float;
+    # the Gram matrices and rotations run in FP64 or double-float
+    rr_prec = prec if args.rr_precision == "same" else PREC[args.rr_precision]
+    dense_prec = PREC[args.dense_precision]
+    cs.cs_set_rr_precision(ctx, rr_prec)
+    cs.cs_set_dense_precision(ctx, dense_prec)
     # each rank filters its own block of states (independent seeds)
     X0h = W.gaussian_block(rank_block_seed(w.x_seed, rank), d, n_s)
     X0 = torch.tensor(np.ascontiguousarray(X0h.T), device=dev)
@@ -295,6 +311,56 @@ def run_ours(args):
     h2d = X0.numel() * 8
     d2h = X0.numel() * 8 + n_s * 8
 
+    # ---- Ritz values of one step from X0 with the reduced Rayleigh-Ritz apply against the
+    # same step with an FP64 apply (wanted states), and the other precisions' step times
+    def one_step(p_filter, p_rr, p_dense=None):
+        cs.cs_set_rr_precision(ctx, p_rr)
+        cs.cs_set_dense_precision(ctx, dense_prec if p_dense is None else p_dense)
+        wk = ctx.workspace(n_s, p_filter)
+        X.copy_(X0)
+        cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+        return theta.cpu().numpy().copy(), wk
+
+    th_red, _ = one_step(prec, rr_prec)
+    th_64, _ = one_step(prec, CS_FP64, CS_FP64)
+    ritz_dev = float(np.max(np.abs(th_red[:w.n_want] - th_64[:w.n_want])))
+
+    def time_variant(p_filter, p_rr, p_dense, reps=3):
+        one_step(p_filter, p_rr, p_dense)  # warm (tables, workspace)
+        wk = ctx.workspace(n_s, p_filter)
+        for _ in range(2):
+            X.copy_(X0)
+            cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+        tot = 0.0
+        for _ in range(reps):
+            X.copy_(X0)
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        return {"ms_per_step": round(ms, 4),
+                "value": round(applies_per_step / (ms / 1e3), 2)}
+
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for name, pf, prr, pd in (("fp64", CS_FP64, CS_FP64, CS_FP64),
+                                  ("df64", CS_DF64, CS_DF64, CS_DF64),
+                                  ("fp32_rr_fp64", CS_FP32, CS_FP64, CS_FP64),
+                                  ("fp32_rr_df64", CS_FP32, CS_DF64, CS_DF64),
+                                  ("mixed_rr_df64", CS_MIXED_BF16, CS_DF64, CS_DF64)):
+            v = time_variant(pf, prr, pd)
+            v.update({"filter": NAME[pf], "rayleigh_ritz_apply": NAME[prr],
+                      "gram_and_rotations": NAME[pd]})
+            variants[name] = v
+    cs.cs_set_rr_precision(ctx, rr_prec)
+    cs.cs_set_dense_precision(ctx, dense_prec)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -309,13 +375,17 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "bf16x3+f32+f64"}[args.precision],
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "bf16x3+f32+f64",
+                  "df64": "df64+f64"}[args.precision],
         "data": "synthetic (seeded erf pseudo-atom cluster and Gaussian state block)",
         "config": {"workload": "erf32_l30_n48: 32 erf atoms in r<=8, R=14, lmax=30, 48 radial "
                                "fns/l, d=46128, grid 96x60x120, 80 states, degree 16",
                    "step": "one ChFSI iteration: filter (16 H.X) + CholQR x2 + Rayleigh-Ritz "
-                           "(1 FP64 H.X)",
-                   "filter_precision": args.precision, "orthonormalisation": "fp64",
+                           "(1 H.X in the rayleigh_ritz_apply precision)",
+                   "filter_precision": args.precision,
+                   "rayleigh_ritz_apply": NAME[rr_prec],
+                   "gram_and_rotations": NAME[dense_prec],
+                   "factorisation_eigensolve_residuals": "fp64",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world} (independent state blocks)"},
         "roofline": roofline,
@@ -326,8 +396,9 @@ def run_ours(args):
         "gpu_launches": int(launches_timed),
         "batched": batched,
         "clocks": clocks.summary(),
-        "ritz": {"theta_min": float(theta.min().item()), "resid_max_lowest64":
-                 float(resid[:64].max().item())},
+        "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
+                 "n_wanted": w.n_want},
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -476,10 +547,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mixed", "df64"],
+                    help="filter precision")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--rr-precision", default="df64", choices=["same", "fp64", "df64"],
+                    help="precision of the H X that Rayleigh-Ritz projects")
+    ap.add_argument("--dense-precision", default="df64", choices=["fp64", "df64"],
+                    help="arithmetic of the Gram matrices and block rotations")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

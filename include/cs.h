@@ -73,7 +73,13 @@ typedef enum {
                         (tcgen05) with operands split into two BF16 terms (hi + lo, three
                         products, FP32 accumulation), and so are the two projector
                         products; angular sums and the recurrence in FP32. Blocks are
-                        float.                                                           */
+                        float.                                                           */,
+  CS_DF64 = 3        /* FP64 storage (blocks are double); H X computed in double-float
+                        arithmetic on the FP32 pipe (each value an unevaluated sum of two
+                        floats, about 48 significant bits; Dekker/Knuth error-free
+                        transformations). On a GPU whose FP64 pipe runs at 1/64 of the FP32
+                        rate this is several times faster than CS_FP64 at relative errors
+                        near 1e-14. Not available with projectors.                       */
 } cs_precision;
 
 /* ------------------------------------------------------------------ basis / context */
@@ -133,6 +139,22 @@ cs_status cs_forward_transform(cs_ctx* ctx, int n, const double* g, double* coef
  * transform): f[n][N_r][N_theta][N_phi] = (B coef)^T. Arguments as above. */
 cs_status cs_inverse_transform(cs_ctx* ctx, int n, const double* coef, long long ld, double* f,
                                void* work, cs_stream stream);
+
+/* Precision of the H X that Rayleigh-Ritz projects (cs_rayleigh_ritz, cs_chfsi_step,
+ * cs_chfsi; Sec. 3.2.1). Default CS_FP64. With CS_FP32 or CS_MIXED_BF16 the block is rounded
+ * to FP32, H is applied in that precision and the product is widened back; the projected
+ * matrix X^T H X, its eigensolve, the rotations and the residual norms stay FP64. Residual
+ * norms then level off near the reduced precision's H X error (about 1e-6 |H| for FP32 and
+ * the split-BF16 mixed mode), so convergence thresholds should sit above that.
+ * Workspaces must be sized (cs_workspace_bytes) after this call. CS_ERR_ARG for an unknown
+ * precision. */
+cs_status cs_set_rr_precision(cs_ctx* ctx, cs_precision prec);
+
+/* Arithmetic of the tall-skinny Gram matrices (X^T X, X^T H X) and block rotations (X R^-1,
+ * X Q, H X Q) of Cholesky-QR and Rayleigh-Ritz (Sec. 3.1.1, 3.2.1): CS_FP64 (default) or
+ * CS_DF64 (double-float on the FP32 pipe, FP64 storage, relative errors near 1e-14). The
+ * small factorisation, eigensolve and residual norms stay FP64. CS_ERR_ARG otherwise. */
+cs_status cs_set_dense_precision(cs_ctx* ctx, cs_precision prec);
 
 /* Device workspace (bytes) needed by cs_apply_H / cs_cheb_filter / transforms on n_s
  * columns at precision `prec`, and by cs_rayleigh_ritz / cs_chfsi (their FP64 needs are
@@ -199,11 +221,12 @@ cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degre
  * CUDA event pair on the launching stream around every kernel it launches on ctx.
  * cs_profile_end synchronises, and writes per kernel class the summed device time
  * (ms[CS_PROFILE_CLASSES]) and the launch count (launches[CS_PROFILE_CLASSES]). Class =
- * family + 5 for launches in FP32 / mixed precision (FP64 launches: family alone); families:
+ * family + 5 for launches in FP32 / mixed precision, + 10 in double-float (FP64 launches:
+ * family alone); families:
  * 0 radial synthesis GEMMs, 1 angular transforms (per radial node), 2 radial analysis GEMMs
  * with the fused epilogue, 3 dense FP64 linear algebra and conversions, 4 Kleinman-Bylander
  * projector products. */
-#define CS_PROFILE_CLASSES 10
+#define CS_PROFILE_CLASSES 15
 cs_status cs_profile_begin(cs_ctx* ctx);
 cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
 

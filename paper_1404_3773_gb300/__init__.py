@@ -18,12 +18,13 @@ import os
 import torch  # loads the CUDA runtime that the library links against
 
 __all__ = [
-    "CS_FP64", "CS_FP32", "CS_MIXED_BF16", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
+    "CS_FP64", "CS_FP32", "CS_MIXED_BF16", "CS_DF64", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
     "CsError", "Context", "cs_basis_init", "cs_basis_free", "cs_basis_dims", "cs_grid",
     "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
     "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
+    "cs_set_rr_precision", "cs_set_dense_precision",
     "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
@@ -32,7 +33,7 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libclusterspec.so")
 
-CS_FP64, CS_FP32, CS_MIXED_BF16 = 0, 1, 2
+CS_FP64, CS_FP32, CS_MIXED_BF16, CS_DF64 = 0, 1, 2, 3
 CS_RADIAL_GAUSS_LEGENDRE, CS_RADIAL_GAUSS_JACOBI_R2 = 0, 1
 _STATUS = {0: "CS_OK", 1: "CS_ERR_ARG", 2: "CS_ERR_ALLOC", 3: "CS_ERR_CUDA",
            4: "CS_ERR_STATE", 5: "CS_ERR_CHOLESKY", 6: "CS_ERR_NOT_CONVERGED",
@@ -82,6 +83,8 @@ _SIGS = {
     "cs_profile_begin": (_i, [_vp]),
     "cs_device_error": (_i, [_vp, ctypes.POINTER(_i)]),
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
+    "cs_set_rr_precision": (_i, [_vp, _i]),
+    "cs_set_dense_precision": (_i, [_vp, _i]),
     "cs_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, ctypes.POINTER(_vp)]),
     "cs_batch_free": (_i, [_vp]),
     "cs_batch_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -261,7 +264,8 @@ def cs_workspace_bytes(ctx: Context, n_s: int, precision: int = CS_FP64) -> int:
 
 
 def _dtype(precision):
-    return torch.float64 if precision == CS_FP64 else torch.float32  # FP32 and mixed: float
+    # FP64 and double-float blocks are double; FP32 and mixed blocks are float
+    return torch.float64 if precision in (CS_FP64, CS_DF64) else torch.float32
 
 
 def cs_apply_H(ctx: Context, X: torch.Tensor, HX: torch.Tensor, precision: int = CS_FP64,
@@ -349,21 +353,36 @@ def cs_device_error(ctx: Context) -> int:
     return code.value
 
 
+def cs_set_rr_precision(ctx: Context, precision: int):
+    """Precision of the H X that Rayleigh-Ritz projects (default CS_FP64); the projection,
+    eigensolve and residual norms stay FP64. Cached workspaces are re-sized on next use."""
+    ctx.check(_lib.cs_set_rr_precision(ctx.handle, int(precision)))
+    ctx._ws.clear()
+
+
+def cs_set_dense_precision(ctx: Context, precision: int):
+    """Arithmetic of the Cholesky-QR / Rayleigh-Ritz Gram matrices and block rotations:
+    CS_FP64 (default) or CS_DF64 (double-float on the FP32 pipe, FP64 storage)."""
+    ctx.check(_lib.cs_set_dense_precision(ctx.handle, int(precision)))
+
+
 def cs_profile_begin(ctx: Context):
     ctx.check(_lib.cs_profile_begin(ctx.handle))
 
 
 PROFILE_FAMILIES = ("radial_synth", "angular", "radial_anal", "dense", "kb")
-PROFILE_CLASSES = 2 * len(PROFILE_FAMILIES)
+PROFILE_CLASSES = 3 * len(PROFILE_FAMILIES)
 
 
 def profile_class_names():
-    """Names of the profile classes: family, then family + '_f32' for FP32 / mixed launches."""
-    return list(PROFILE_FAMILIES) + [f + "_f32" for f in PROFILE_FAMILIES]
+    """Names of the profile classes: family (FP64 launches), family + '_f32' (FP32 / mixed),
+    family + '_df64' (double-float)."""
+    return (list(PROFILE_FAMILIES) + [f + "_f32" for f in PROFILE_FAMILIES] +
+            [f + "_df64" for f in PROFILE_FAMILIES])
 
 
 def cs_profile_end(ctx: Context):
-    """Returns (ms[10], launches[10]) per kernel class (profile_class_names())."""
+    """Returns (ms, launches) per kernel class (profile_class_names())."""
     ms = (ctypes.c_double * PROFILE_CLASSES)()
     n = (_ll * PROFILE_CLASSES)()
     ctx.check(_lib.cs_profile_end(ctx.handle, ms, n))

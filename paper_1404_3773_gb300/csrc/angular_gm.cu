@@ -1,5 +1,5 @@
 // FP32 angular kernel of H.X built from register-blocked contractions (see angular_gm.cuh).
-// One CTA per (state tile of 8, radial node); 256 threads; chunks of 8 (or 4) row pairs.
+// One CTA per (state tile of 8, radial node); 256 threads; chunks of 8 row pairs.
 #include <cuda_runtime.h>
 
 #include "angular_gm.cuh"
@@ -8,30 +8,36 @@
 
 namespace cs {
 
-template <int ST, int RC>
-__global__ void __launch_bounds__(kGmThreads) k_angular_gm(AngArgs<float> a, float* __restrict__ G) {
+__global__ void __launch_bounds__(kGmThreads, 1) k_angular_gm(AngArgs<float> a, float* __restrict__ G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  angular_gm_block<ST, RC>(a, G, blockIdx.y, blockIdx.x * ST, smem_raw);
+  angular_gm_block(a, G, blockIdx.y, blockIdx.x * kGmST, smem_raw);
 }
 
-template <int ST, int RC>
-static cudaError_t launch_gm(const AngArgs<float>& a, float* G, cudaStream_t stream) {
-  const size_t smem = gm_smem_bytes(a.L, a.Q4, ST, RC);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_angular_gm<ST, RC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, cudaStream_t stream) {
+  const size_t smem = gm_smem_bytes(a.L, a.Q4, a.n_theta);
+  if (!a.theta_pairs || smem > 227 * 1024)
+    return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_angular_gm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.S + ST - 1) / ST, a.n_r);
-  k_angular_gm<ST, RC><<<grid, kGmThreads, smem, stream>>>(a, G);
+  dim3 grid((a.S + kGmST - 1) / kGmST, a.n_r);
+  k_angular_gm<<<grid, kGmThreads, smem, stream>>>(a, G);
   return cudaGetLastError();
 }
 
-// 8 states per CTA with 8 row pairs per chunk, else 4 row pairs; cudaErrorInvalidConfiguration
-// when neither fits in shared memory (the caller then takes another angular kernel)
-cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, int variant, cudaStream_t stream) {
-  if (variant <= 0 && gm_smem_bytes(a.L, a.Q4, 8, 8) <= 227 * 1024) return launch_gm<8, 8>(a, G, stream);
-  if (variant <= 1 && gm_smem_bytes(a.L, a.Q4, 8, 4) <= 227 * 1024) return launch_gm<8, 4>(a, G, stream);
-  return cudaErrorInvalidConfiguration;
+size_t build_theta_pairs(const std::vector<double>& theta, int L, int n_theta,
+                         std::vector<double>& out) {
+  const GmShape g = gm_shape(L, 0, n_theta);
+  const int NP = (n_theta + 1) / 2;
+  out.assign(gm_theta_pairs_elems(L, n_theta), 0.0);
+  for (int ch = 0; ch < g.nchunks; ++ch)
+    for (int o = 0; o < g.RL; ++o)
+      for (int p = 0; p < kGmRC; ++p) {
+        const int jp = ch * kGmRC + p;
+        if (jp < NP)
+          out[((size_t)ch * (g.RL + 4) + o) * kGmRC + p] = theta[(size_t)jp * g.RL + o];
+      }
+  return out.size();
 }
 
 }  // namespace cs

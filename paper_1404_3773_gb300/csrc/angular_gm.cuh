@@ -3,18 +3,20 @@
 // angular_gm.cu and the batched kernel). Same arithmetic as the row-pair kernel: equatorial
 // parity folding of the Legendre sums, four-angle folding of the phi sums, W V on the grid.
 //
-// A CTA owns radial node k and ST states and walks the theta rows in chunks of RC mirrored
-// row pairs (Legendre rows staged transposed, [packed (m,l)][pair]). A column of the chunk is (pair p, row j or its mirror jb, state s):
-// NC = 2 RC ST columns.
-//   A: F[m][col]      = sum_l Theta_lm(t_j) G[l,m,s]            (even/odd l+|m| -> j, jb)
-//   B: Wq[4][q][col]  = W V x the phi sums at the four mirror angles of q, folded back
-//                       into cos/sin x even/odd-m quadrature inputs
-//   C: A[m][col]      = sum_q {cos|sin}(m phi_q) Wq[...][q][col]
-//   D: G'[l,m,s]     += sum_p Theta_lm(t_jp) (A_j +- A_jb)        (accumulated over chunks)
-// Stages B and C (about 80 % of the flops) use 4 x 4 register tiles with the lanes of a
-// warp laid out 4 (rows) x 8 (columns), so every 128-bit shared-memory load is shared by
-// the lanes and feeds 8 (B) or 5 (C) FMAs per lane; stages A and D use 4 x 4 tiles over
-// (l, pair or state).
+// A CTA owns radial node k and 8 states and walks the theta rows in chunks of 8 mirrored
+// row pairs (p). Column of a chunk = (p, state pair sp, row r = j or its mirror jb, state
+// e in the pair): col = 16 p + 4 sp + 2 r + e, so four consecutive columns hold both rows of
+// two states and a thread can form A_j +- A_jb itself.
+//   A: F[m][col]        = sum_l Theta_lm(t_j) G[l,m,s]           (even/odd l+|m| -> j, jb)
+//   B: Wq[4][q][col]    = W V x the phi sums at the four mirror angles of q, folded back into
+//                         cos/sin x even/odd-m quadrature inputs
+//   C: AP[m][p][+-][s]  = sum_q {cos|sin}(m phi_q) Wq[...][q][col], combined over j, jb
+//   D: G'[l,m][s]      += sum_p Theta_lm(t_jp) AP[m][p][parity of l+|m|][s]
+// B and C use 4 x 4 register tiles with a warp's lanes laid out 4 (rows) x 8 (columns) and
+// load the next step's operands while the current FMAs run; C groups the modes by parity
+// so one tile needs one cos and one sin input array. D accumulates each (l, m) output for all
+// 8 states in shared memory; its lanes share a mode, so the AP loads are broadcasts. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair]) from a
+// table built at set-up, so staging them is a contiguous copy.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,83 +27,92 @@
 namespace cs {
 
 constexpr int kGmThreads = 256;
+constexpr int kGmST = 8;     // states per CTA
+constexpr int kGmRC = 8;     // mirrored row pairs per chunk
 
 __host__ __device__ inline int gm_round4(int x) { return (x + 3) & ~3; }
 
 struct GmShape {
-  int L, Q, Qp, Lp, rowlen, NC, NCp;
+  int L, Q, Qp, Lb, Lq, ne4, RL, NC, NCp, M2, nchunks;
 };
 
-__host__ __device__ inline GmShape gm_shape(int L, int Q4, int ST, int RC) {
+__host__ __device__ inline GmShape gm_shape(int L, int Q4, int n_theta) {
   GmShape g;
   g.L = L;
   g.Q = Q4 + 1;
   g.Qp = gm_round4(g.Q);
-  g.Lp = gm_round4(L);
-  g.rowlen = L * (L + 1) / 2;
-  g.NC = 2 * RC * ST;
-  g.NCp = g.NC % 32 == 0 ? g.NC + 4 : g.NC;  // F rows start on different banks
+  g.Lb = gm_round4(L + 1);
+  g.ne4 = gm_round4((L + 1) / 2);         // even m = 0, 2, ... (padded), then odd m
+  g.Lq = g.ne4 + gm_round4(L / 2);
+  g.RL = L * (L + 1) / 2;
+  g.NC = 2 * kGmRC * kGmST;
+  g.NCp = g.NC + 4;                       // F rows start on different banks
+  g.M2 = 2 * L - 1;
+  g.nchunks = ((n_theta + 1) / 2 + kGmRC - 1) / kGmRC;
   return g;
 }
 
+// floats of the pre-transposed Legendre table: [chunk][RL + 4][kGmRC]
+__host__ __device__ inline size_t gm_theta_pairs_elems(int L, int n_theta) {
+  const GmShape g = gm_shape(L, 0, n_theta);
+  return (size_t)g.nchunks * (g.RL + 4) * kGmRC;
+}
+
 // shared-memory footprint in bytes
-__host__ __device__ inline size_t gm_smem_bytes(int L, int Q4, int ST, int RC) {
-  const GmShape g = gm_shape(L, Q4, ST, RC);
-  const size_t L2 = (size_t)L * L, M2 = 2 * L - 1;
-  size_t f = 2 * L2 * ST + (size_t)RC * (g.rowlen + 4) + M2 * g.NCp +
-             4 * (size_t)g.Qp * g.NC + 4 * (size_t)g.Lp * g.Qp;
-  return f * sizeof(float);
+__host__ __device__ inline size_t gm_smem_bytes(int L, int Q4, int n_theta) {
+  const GmShape g = gm_shape(L, Q4, n_theta);
+  const size_t L2 = (size_t)L * L;
+  size_t f = 2 * L2 * kGmST + (size_t)(g.RL + 4) * kGmRC + (size_t)(g.M2 + 2) * g.NCp +
+             (size_t)g.M2 * g.NC + 4 * (size_t)(g.Qp + 1) * g.NC + 2 * (size_t)g.Lb * g.Qp +
+             2 * (size_t)(g.Qp + 1) * g.Lq;
+  return f * sizeof(float) + (size_t)(g.M2 + 1) * sizeof(int);
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
+__device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void unpack4(const float4 v, float* o) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
 
-template <int ST, int RC>
 __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float* __restrict__ G,
                                                  int k, int s0, unsigned char* smem_raw) {
-  static_assert(ST % 4 == 0 && RC % 4 == 0, "tiles of four");
-  constexpr int NB = 8;  // global loads in flight per thread in the staging loops
+  constexpr int ST = kGmST, RC = kGmRC, NC = 2 * RC * ST, NB = 8;
   const int L = a.L, lmax = L - 1, L2 = L * L, M2 = 2 * L - 1;
   const int Np = a.n_phi, h = Np / 2, Q4 = a.Q4;
   const int Nt = a.n_theta, S = a.S, NP = (Nt + 1) / 2;
-  const GmShape gs = gm_shape(L, Q4, ST, RC);
-  const int Q = gs.Q, Qp = gs.Qp, Lp = gs.Lp, RL = gs.rowlen, NCp = gs.NCp;
-  constexpr int NC = 2 * RC * ST;
-  float* Gs = reinterpret_cast<float*>(smem_raw);      // [L2][ST]
-  float* Ga = Gs + (size_t)L2 * ST;                    // [L2][ST]
-  float* PT = Ga + (size_t)L2 * ST;                    // [RL + 4][RC]: packed (m,l) x pair
-  float* F = PT + (size_t)(RL + 4) * RC;               // [M2][NCp] (A after stage C)
-  float* Wq = F + (size_t)M2 * NCp;                    // [4][Qp][NC]
-  float* Tb = Wq + (size_t)4 * Qp * NC;                // [cos|sin][Lp][Qp]
-  float* Tc = Tb + (size_t)2 * Lp * Qp;                // [cos|sin][Qp][Lp]
+  const GmShape gs = gm_shape(L, Q4, Nt);
+  const int Q = gs.Q, Qp = gs.Qp, Lb = gs.Lb, Lq = gs.Lq, ne4 = gs.ne4, RL = gs.RL;
+  const int NCp = gs.NCp;
+  float* Gs = reinterpret_cast<float*>(smem_raw);  // [L2][ST]
+  float* Ga = Gs + (size_t)L2 * ST;                // [L2][ST] Legendre-quadrature sums
+  float* PT = Ga + (size_t)L2 * ST;                // [RL + 4][RC]
+  float* Fz = PT + (size_t)(RL + 4) * RC;          // [M2 + 2][NCp], first and last rows zero
+  float* F = Fz + NCp;                             // F[mi], mi in [-1, M2]
+  float* AP = Fz + (size_t)(M2 + 2) * NCp;         // [M2][RC][2][ST]
+  float* Wq = AP + (size_t)M2 * NC;                // [4][Qp + 1][NC], row Qp zero
+  float* Tb = Wq + (size_t)4 * (Qp + 1) * NC;      // [cos|sin][Lb][Qp]
+  float* Tc = Tb + (size_t)2 * Lb * Qp;            // [cos|sin][Qp + 1][Lq], m by parity
+  int* mstart = reinterpret_cast<int*>(Tc + (size_t)2 * (Qp + 1) * Lq);  // [M2 + 1]
+  const int WS = (Qp + 1) * NC;                    // stride of the four Wq arrays
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = min(ST, S - s0);
 
-  // ---- tables and the state tile of G (NB independent loads in flight per thread)
-  for (int b0 = 0; b0 < 2 * Lp * Qp; b0 += NB * kGmThreads) {
-    float v[NB];
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      const int i = b0 + u * kGmThreads + tid;
-      v[u] = 0.f;
-      if (i < 2 * Lp * Qp) {
-        const int cs_ = i / (Lp * Qp), r = i - cs_ * Lp * Qp;
-        const int m = r / Qp, q = r - m * Qp;
-        if (m < L && q < Q) v[u] = a.trig[(size_t)(cs_ * L + m) * Q + q];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      const int i = b0 + u * kGmThreads + tid;
-      if (i < 2 * Lp * Qp) {
-        const int cs_ = i / (Lp * Qp), r = i - cs_ * Lp * Qp;
-        const int m = r / Qp, q = r - m * Qp;
-        Tb[i] = v[u];
-        Tc[(size_t)cs_ * Qp * Lp + q * Lp + m] = v[u];
-      }
-    }
+  // ---- set-up: phi tables in two layouts, the state tile of G, zero rows, mode starts
+  for (int i = tid; i < 2 * Lb * Qp; i += kGmThreads) {
+    const int cs_ = i / (Lb * Qp), r = i - cs_ * Lb * Qp;
+    const int m = r / Qp, q = r - m * Qp;
+    Tb[i] = (m < L && q < Q) ? a.trig[(size_t)(cs_ * L + m) * Q + q] : 0.f;
+  }
+  for (int i = tid; i < 2 * (Qp + 1) * Lq; i += kGmThreads) {
+    const int cs_ = i / ((Qp + 1) * Lq), r = i - cs_ * (Qp + 1) * Lq;
+    const int q = r / Lq, mp = r - q * Lq;
+    const int m = (mp < ne4) ? 2 * mp : 2 * (mp - ne4) + 1;
+    Tc[i] = (m < L && q < Q) ? a.trig[(size_t)(cs_ * L + m) * Q + q] : 0.f;
   }
   for (int b0 = 0; b0 < L2 * ST; b0 += NB * kGmThreads) {
     float v[NB];
@@ -120,25 +131,42 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
       }
     }
   }
-  for (int i = tid; i < 4 * RC; i += kGmThreads) PT[(size_t)RL * RC + i] = 0.f;
+  for (int i = tid; i < NCp; i += kGmThreads) {
+    Fz[i] = 0.f;
+    Fz[(size_t)(M2 + 1) * NCp + i] = 0.f;
+  }
+  for (int i = tid; i < 4 * NC; i += kGmThreads) Wq[(size_t)(i / NC) * WS + (size_t)Qp * NC + i % NC] = 0.f;
+  if (tid == 0) {
+    int o = 0;
+    for (int mi = 0; mi < M2; ++mi) {
+      mstart[mi] = o;
+      const int m = mi - lmax;
+      o += L - (m < 0 ? -m : m);
+    }
+    mstart[M2] = o;
+  }
+  __syncthreads();
   const float* wvk = a.wv + (size_t)k * Nt * Np;
 
-  for (int c0 = 0; c0 < NP; c0 += RC) {
-    __syncthreads();  // set-up done / previous chunk's stage D done with PT and A
-    // ---- theta rows of the chunk, transposed to [packed (m,l)][pair] (zero for missing pairs)
-    for (int b0 = 0; b0 < RC * RL; b0 += NB * kGmThreads) {
-      float v[NB];
+  for (int c0 = 0, ch = 0; c0 < NP; c0 += RC, ++ch) {
+    __syncthreads();  // previous chunk's stage D done with PT and AP
+    // ---- Legendre rows of the chunk (pre-transposed table): contiguous float4 copy
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.theta_pairs + (size_t)ch * (RL + 4) * RC);
+      float4* dst = reinterpret_cast<float4*>(PT);
+      const int n4 = (RL + 4) * RC / 4;
+      for (int b0 = 0; b0 < n4; b0 += 4 * kGmThreads) {
+        float4 v[4];
 #pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int i = b0 + u * kGmThreads + tid;
-        const int p = i / RL, o = i - p * RL;
-        v[u] = (i < RC * RL && c0 + p < NP) ? a.theta[(size_t)(c0 + p) * RL + o] : 0.f;
-      }
+        for (int u = 0; u < 4; ++u) {
+          const int i = b0 + u * kGmThreads + tid;
+          if (i < n4) v[u] = src[i];
+        }
 #pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int i = b0 + u * kGmThreads + tid;
-        const int p = i / RL, o = i - p * RL;
-        if (i < RC * RL) PT[(size_t)o * RC + p] = v[u];
+        for (int u = 0; u < 4; ++u) {
+          const int i = b0 + u * kGmThreads + tid;
+          if (i < n4) dst[i] = v[u];
+        }
       }
     }
     __syncthreads();
@@ -156,21 +184,21 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) E[u][v] = O[u][v] = 0.f;
-        // rows (m, l) of PT for l = am, am+1, ... start at theta_off(L, am)
         const float* prow = PT + (size_t)theta_off(L, am) * RC + p0;
         for (int l0 = am; l0 <= lmax; l0 += 4) {
           float4 P4[4], g4[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int l = l0 + i;
-            P4[i] = ld4(prow + (size_t)(l - am) * RC);  // finite past lmax; multiplied by 0
+            P4[i] = ld4(prow + (size_t)(l - am) * RC);  // finite past lmax; times 0 below
             g4[i] = (l <= lmax) ? ld4(Gs + (size_t)(l * l + l + m) * ST + s0l)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float pv[4] = {P4[i].x, P4[i].y, P4[i].z, P4[i].w};
-            const float gv[4] = {g4[i].x, g4[i].y, g4[i].z, g4[i].w};
+            float pv[4], gv[4];
+            unpack4(P4[i], pv);
+            unpack4(g4[i], gv);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -180,12 +208,12 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
               }
           }
         }
-        const int mi = m + lmax;
+        float* frow = F + (size_t)(m + lmax) * NCp + 2 * s0l;  // state pair sp = s0l / 2
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          float* fj = F + (size_t)mi * NCp + ((p0 + u) * 2) * ST + s0l;
-          st4(fj, E[u][0] + O[u][0], E[u][1] + O[u][1], E[u][2] + O[u][2], E[u][3] + O[u][3]);
-          st4(fj + ST, E[u][0] - O[u][0], E[u][1] - O[u][1], E[u][2] - O[u][2], E[u][3] - O[u][3]);
+          float* f = frow + (size_t)(p0 + u) * 16;
+          st4(f, E[u][0] + O[u][0], E[u][1] + O[u][1], E[u][0] - O[u][0], E[u][1] - O[u][1]);
+          st4(f + 4, E[u][2] + O[u][2], E[u][3] + O[u][3], E[u][2] - O[u][2], E[u][3] - O[u][3]);
         }
       }
     }
@@ -200,35 +228,24 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
         const int cb = (wt / nQW) * 8 + (lane >> 2);
         if (qb >= nQB) continue;
         const int q0 = 4 * qb, cc = 4 * cb;
-        // the four columns share (pair, row): prefetch that row's W V at the 16 angles
-        const int col_pr = cc / ST, p = col_pr >> 1, r = col_pr & 1;
-        const int jp = c0 + p;
-        const bool valid = (jp < NP) && !(r == 1 && (Nt - 1 - jp) == jp);
-        const int jr = (r == 0) ? jp : Nt - 1 - jp;
-        const float* wvr = wvk + (size_t)(valid ? jr : 0) * Np;
-        float wang[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int q = q0 + i;
-          const bool ok = valid && q <= Q4;
-          wang[i][0] = ok ? wvr[q] : 0.f;
-          wang[i][1] = ok ? wvr[(Np - q) % Np] : 0.f;
-          wang[i][2] = ok ? wvr[h - q] : 0.f;
-          wang[i][3] = ok ? wvr[h + q] : 0.f;
-        }
         float Ee[4][4], Eo[4][4], Oe[4][4], Oo[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) Ee[i][j] = Eo[i][j] = Oe[i][j] = Oo[i][j] = 0.f;
-        for (int m = 0; m <= lmax; m += 2) {
+        // operands of mode m are loaded while the other parity's FMAs run; rows past lmax
+        // are zero padding, so the odd partner of the last even mode needs no test
+        float4 e_tc = ld4(Tb + q0), e_ts = ld4(Tb + (size_t)Lb * Qp + q0);
+        float4 e_fp = ld4(F + (size_t)lmax * NCp + cc), e_fm = e_fp;
+        for (int m = 0; m < L; m += 2) {
+          const int mo = m + 1;
+          const float4 o_tc = ld4(Tb + (size_t)mo * Qp + q0);
+          const float4 o_ts = ld4(Tb + (size_t)(Lb + mo) * Qp + q0);
+          const float4 o_fp = ld4(F + (size_t)(lmax + mo) * NCp + cc);
+          const float4 o_fm = ld4(F + (size_t)(lmax - mo) * NCp + cc);
           {
-            const float4 tc4 = ld4(Tb + (size_t)m * Qp + q0);
-            const float4 ts4 = ld4(Tb + (size_t)(Lp + m) * Qp + q0);
-            const float4 fp4 = ld4(F + (size_t)(lmax + m) * NCp + cc);
-            const float4 fm4 = ld4(F + (size_t)(lmax - m) * NCp + cc);
-            const float tc[4] = {tc4.x, tc4.y, tc4.z, tc4.w}, ts[4] = {ts4.x, ts4.y, ts4.z, ts4.w};
-            const float fp[4] = {fp4.x, fp4.y, fp4.z, fp4.w}, fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
+            float tc[4], ts[4], fp[4], fm[4];
+            unpack4(e_tc, tc); unpack4(e_ts, ts); unpack4(e_fp, fp); unpack4(e_fm, fm);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -237,14 +254,16 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
                 Oe[i][j] = fmaf(ts[i], fm[j], Oe[i][j]);
               }
           }
-          if (m + 1 <= lmax) {
-            const int m1 = m + 1;
-            const float4 tc4 = ld4(Tb + (size_t)m1 * Qp + q0);
-            const float4 ts4 = ld4(Tb + (size_t)(Lp + m1) * Qp + q0);
-            const float4 fp4 = ld4(F + (size_t)(lmax + m1) * NCp + cc);
-            const float4 fm4 = ld4(F + (size_t)(lmax - m1) * NCp + cc);
-            const float tc[4] = {tc4.x, tc4.y, tc4.z, tc4.w}, ts[4] = {ts4.x, ts4.y, ts4.z, ts4.w};
-            const float fp[4] = {fp4.x, fp4.y, fp4.z, fp4.w}, fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
+          if (m + 2 < L) {
+            const int me = m + 2;
+            e_tc = ld4(Tb + (size_t)me * Qp + q0);
+            e_ts = ld4(Tb + (size_t)(Lb + me) * Qp + q0);
+            e_fp = ld4(F + (size_t)(lmax + me) * NCp + cc);
+            e_fm = ld4(F + (size_t)(lmax - me) * NCp + cc);
+          }
+          {
+            float tc[4], ts[4], fp[4], fm[4];
+            unpack4(o_tc, tc); unpack4(o_ts, ts); unpack4(o_fp, fp); unpack4(o_fm, fm);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -254,6 +273,27 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
               }
           }
         }
+        // W V of the pair's two rows at the 16 angles of the tile
+        const int p = cb >> 2;  // 4 column blocks per pair
+        const int jp = c0 + p;
+        const bool v0 = jp < NP, v1 = v0 && (Nt - 1 - jp) != jp;
+        const float* wr0 = wvk + (size_t)(v0 ? jp : 0) * Np;
+        const float* wr1 = wvk + (size_t)(v1 ? Nt - 1 - jp : 0) * Np;
+        float wang[2][4][4];  // [row][q][angle q, N-q, h-q, h+q]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = q0 + i;
+          const bool ok = q <= Q4;
+          const int i0 = q, i1 = (Np - q) % Np, i2 = h - q, i3 = h + q;
+          wang[0][i][0] = (ok && v0) ? wr0[i0] : 0.f;
+          wang[0][i][1] = (ok && v0) ? wr0[i1] : 0.f;
+          wang[0][i][2] = (ok && v0) ? wr0[i2] : 0.f;
+          wang[0][i][3] = (ok && v0) ? wr0[i3] : 0.f;
+          wang[1][i][0] = (ok && v1) ? wr1[i0] : 0.f;
+          wang[1][i][1] = (ok && v1) ? wr1[i1] : 0.f;
+          wang[1][i][2] = (ok && v1) ? wr1[i2] : 0.f;
+          wang[1][i][3] = (ok && v1) ? wr1[i3] : 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int q = q0 + i;
@@ -261,10 +301,11 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
           float c0v[4], c1v[4], s0v[4], s1v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
+            const int r = j >> 1;  // columns 0,1: row j; 2,3: mirror row jb
             const float EpE = Ee[i][j] + Eo[i][j], EmE = Ee[i][j] - Eo[i][j];
             const float OpO = Oe[i][j] + Oo[i][j], OmO = Oe[i][j] - Oo[i][j];
-            const float g_q = wang[i][0] * (EpE + OpO), g_Nq = wang[i][1] * (EpE - OpO);
-            const float g_hm = wang[i][2] * (EmE - OmO), g_hp = wang[i][3] * (EmE + OmO);
+            const float g_q = wang[r][i][0] * (EpE + OpO), g_Nq = wang[r][i][1] * (EpE - OpO);
+            const float g_hm = wang[r][i][2] * (EmE - OmO), g_hp = wang[r][i][3] * (EmE + OmO);
             const float Pp = wq * (g_q + g_Nq), Mm = wq * (g_q - g_Nq);
             const float P2 = wq * (g_hm + g_hp), M2v = wq * (g_hm - g_hp);
             c0v[j] = Pp + P2;
@@ -274,116 +315,105 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
           }
           float* w0 = Wq + (size_t)q * NC + cc;
           st4(w0, c0v[0], c0v[1], c0v[2], c0v[3]);
-          st4(w0 + (size_t)Qp * NC, c1v[0], c1v[1], c1v[2], c1v[3]);
-          st4(w0 + (size_t)2 * Qp * NC, s0v[0], s0v[1], s0v[2], s0v[3]);
-          st4(w0 + (size_t)3 * Qp * NC, s1v[0], s1v[1], s1v[2], s1v[3]);
+          st4(w0 + WS, c1v[0], c1v[1], c1v[2], c1v[3]);
+          st4(w0 + 2 * (size_t)WS, s0v[0], s0v[1], s0v[2], s0v[3]);
+          st4(w0 + 3 * (size_t)WS, s1v[0], s1v[1], s1v[2], s1v[3]);
         }
       }
     }
     __syncthreads();
-    // ---- C: phi quadrature, A[+m] (cos) and A[-m] (sin), written over F.
-    //      Warp tile = 4 m-blocks x 8 column blocks.
+    // ---- C: phi quadrature of one parity class of modes per tile, combined over the mirror
+    //      rows: AP[m][p][0] = A_j + A_jb, AP[m][p][1] = A_j - A_jb. Warp tile = 4 mode
+    //      blocks x 8 column blocks.
     {
-      const int nMB = Lp / 4, nMW = (nMB + 3) / 4;
+      const int nMB = Lq / 4, nMW = (nMB + 3) / 4;
       constexpr int nCW = NC / 32;
       for (int wt = warp; wt < nMW * nCW; wt += kGmThreads / 32) {
         const int mb = (wt % nMW) * 4 + (lane & 3);
         const int cb = (wt / nMW) * 8 + (lane >> 2);
         if (mb >= nMB) continue;
-        const int m0 = 4 * mb, cc = 4 * cb;
+        const int mp0 = 4 * mb, cc = 4 * cb;
+        const int par = (mp0 >= ne4) ? 1 : 0;
+        const float* wc = Wq + (size_t)par * WS + cc;         // cos, parity of m
+        const float* wsn = Wq + (size_t)(2 + par) * WS + cc;  // sin, parity of m
         float Ac[4][4], As[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) Ac[i][j] = As[i][j] = 0.f;
+        // row Qp of Tc and Wq is zero, so the prefetch of step q + 1 needs no test
+        float4 c_tc = ld4(Tc + mp0), c_ts = ld4(Tc + (size_t)(Qp + 1) * Lq + mp0);
+        float4 c_wc = ld4(wc), c_ws = ld4(wsn);
         for (int q = 0; q < Qp; ++q) {
-          const float4 tc4 = ld4(Tc + (size_t)q * Lp + m0);
-          const float4 ts4 = ld4(Tc + (size_t)(Qp + q) * Lp + m0);
-          const float* wr = Wq + (size_t)q * NC + cc;
-          const float4 we = ld4(wr), wo = ld4(wr + (size_t)Qp * NC);
-          const float4 se = ld4(wr + (size_t)2 * Qp * NC), so = ld4(wr + (size_t)3 * Qp * NC);
-          const float tc[4] = {tc4.x, tc4.y, tc4.z, tc4.w}, ts[4] = {ts4.x, ts4.y, ts4.z, ts4.w};
-          const float ce[4] = {we.x, we.y, we.z, we.w}, co[4] = {wo.x, wo.y, wo.z, wo.w};
-          const float sev[4] = {se.x, se.y, se.z, se.w}, sov[4] = {so.x, so.y, so.z, so.w};
+          const float4 n_tc = ld4(Tc + (size_t)(q + 1) * Lq + mp0);
+          const float4 n_ts = ld4(Tc + (size_t)(Qp + 1 + q + 1) * Lq + mp0);
+          const float4 n_wc = ld4(wc + (size_t)(q + 1) * NC);
+          const float4 n_ws = ld4(wsn + (size_t)(q + 1) * NC);
+          float tc[4], ts[4], w1[4], w2[4];
+          unpack4(c_tc, tc); unpack4(c_ts, ts); unpack4(c_wc, w1); unpack4(c_ws, w2);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              Ac[i][j] = fmaf(tc[i], (i & 1) ? co[j] : ce[j], Ac[i][j]);  // m0 is even
-              As[i][j] = fmaf(ts[i], (i & 1) ? sov[j] : sev[j], As[i][j]);
+              Ac[i][j] = fmaf(tc[i], w1[j], Ac[i][j]);
+              As[i][j] = fmaf(ts[i], w2[j], As[i][j]);
             }
+          c_tc = n_tc; c_ts = n_ts; c_wc = n_wc; c_ws = n_ws;
         }
+        const int p = cb >> 2, sp = cb & 3;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int m = m0 + i;
-          if (m > lmax) break;
-          st4(F + (size_t)(lmax + m) * NCp + cc, Ac[i][0], Ac[i][1], Ac[i][2], Ac[i][3]);
-          if (m > 0) st4(F + (size_t)(lmax - m) * NCp + cc, As[i][0], As[i][1], As[i][2], As[i][3]);
+          const int mp = mp0 + i;
+          const int m = par ? 2 * (mp - ne4) + 1 : 2 * mp;
+          if (m > lmax) continue;
+          float* ac = AP + ((size_t)(lmax + m) * RC + p) * 2 * ST + 2 * sp;
+          st2(ac, Ac[i][0] + Ac[i][2], Ac[i][1] + Ac[i][3]);
+          st2(ac + ST, Ac[i][0] - Ac[i][2], Ac[i][1] - Ac[i][3]);
+          if (m > 0) {
+            float* as = AP + ((size_t)(lmax - m) * RC + p) * 2 * ST + 2 * sp;
+            st2(as, As[i][0] + As[i][2], As[i][1] + As[i][3]);
+            st2(as + ST, As[i][0] - As[i][2], As[i][1] - As[i][3]);
+          }
         }
       }
     }
     __syncthreads();
-    // ---- D: Legendre quadrature. Item = (l block, mode, state block), l-block-major so
-    //      that every item of a block has a non-empty l range; pairs taken four at a time.
-    {
-      constexpr int NSB = ST / 4;
-      const int nLB = (L + 3) / 4;
-      int total = 0;
-      for (int lb = 0; lb < nLB && M2 - 8 * lb > 0; ++lb) total += (M2 - 8 * lb) * NSB;
-      for (int it = tid; it < total; it += kGmThreads) {
-        int rem = it, lb = 0;
-        while (rem >= (M2 - 8 * lb) * NSB) {
-          rem -= (M2 - 8 * lb) * NSB;
-          ++lb;
-        }
-        const int mo = rem / NSB, sb = rem - mo * NSB;
-        const int mi = 4 * lb + mo, m = mi - lmax, am = m < 0 ? -m : m;
-        const int l0 = am + 4 * lb, s0l = 4 * sb;
-        float acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int l = l0 + u;
-          float4 v = (l <= lmax) ? ld4(Ga + (size_t)(l * l + l + m) * ST + s0l)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-          acc[u][0] = v.x; acc[u][1] = v.y; acc[u][2] = v.z; acc[u][3] = v.w;
-        }
-        const float* prow = PT + (size_t)(theta_off(L, am) + 4 * lb) * RC;
-        const float* arow = F + (size_t)mi * NCp + s0l;
-#pragma unroll
-        for (int p4 = 0; p4 < RC; p4 += 4) {
-          float pv[4][4];  // [u][pair]
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 t = ld4(prow + (size_t)u * RC + p4);
-            pv[u][0] = t.x; pv[u][1] = t.y; pv[u][2] = t.z; pv[u][3] = t.w;
-          }
-#pragma unroll
-          for (int pp = 0; pp < 4; ++pp) {
-            const int p = p4 + pp;
-            const float4 aj = ld4(arow + (size_t)(2 * p) * ST);
-            const float4 ab = ld4(arow + (size_t)(2 * p + 1) * ST);
-            const float ap[4] = {aj.x + ab.x, aj.y + ab.y, aj.z + ab.z, aj.w + ab.w};
-            const float an[4] = {aj.x - ab.x, aj.y - ab.y, aj.z - ab.z, aj.w - ab.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v)
-                acc[u][v] = fmaf(pv[u][pp], (u & 1) ? an[v] : ap[v], acc[u][v]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int l = l0 + u;
-          if (l <= lmax)
-            st4(Ga + (size_t)(l * l + l + m) * ST + s0l, acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
-        }
+    // ---- D: Legendre quadrature; item = (mode, l) in mode-major order, so that the lanes of a
+    //      warp share a mode and the AP loads are broadcasts
+    for (int t = tid; t < L2; t += kGmThreads) {
+      int lo = 0, hi = M2 - 1;  // last mode with mstart <= t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mstart[mid] <= t) lo = mid;
+        else hi = mid - 1;
       }
+      const int mi = lo, m = mi - lmax, am = m < 0 ? -m : m;
+      const int l = am + (t - mstart[mi]);
+      float* ga = Ga + (size_t)(l * l + l + m) * ST;
+      float acc[ST];
+      unpack4(ld4(ga), acc);
+      unpack4(ld4(ga + 4), acc + 4);
+      const float* prow = PT + (size_t)(theta_off(L, am) + l - am) * RC;
+      float pv[8];
+      unpack4(ld4(prow), pv);
+      unpack4(ld4(prow + 4), pv + 4);
+      const float* arow = AP + (size_t)mi * RC * 2 * ST + (((l + am) & 1) ? ST : 0);
+#pragma unroll
+      for (int pp = 0; pp < RC; ++pp) {
+        float av[8];
+        unpack4(ld4(arow + (size_t)pp * 2 * ST), av);
+        unpack4(ld4(arow + (size_t)pp * 2 * ST + 4), av + 4);
+#pragma unroll
+        for (int s = 0; s < ST; ++s) acc[s] = fmaf(pv[pp], av[s], acc[s]);
+      }
+      st4(ga, acc[0], acc[1], acc[2], acc[3]);
+      st4(ga + 4, acc[4], acc[5], acc[6], acc[7]);
     }
   }
   __syncthreads();
   for (int i = tid; i < L2 * ST; i += kGmThreads) {
-    const int lm = i / ST, s = i - lm * ST;
-    if (s < ns) G[((size_t)k * L2 + lm) * S + s0 + s] = Ga[i];
+    const int lm = i / ST, sl = i - lm * ST;
+    if (sl < ns) G[((size_t)k * L2 + lm) * S + s0 + sl] = Ga[i];
   }
 }
 

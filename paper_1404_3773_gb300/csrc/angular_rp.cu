@@ -68,5 +68,6 @@ cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream
 
 template cudaError_t launch_angular_rp<float>(const AngArgs<float>&, float*, int, cudaStream_t);
 template cudaError_t launch_angular_rp<double>(const AngArgs<double>&, double*, int, cudaStream_t);
+template cudaError_t launch_angular_rp<df64>(const AngArgs<df64>&, df64*, int, cudaStream_t);
 
 }  // namespace cs

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "cs_internal.h"
+#include "df64.cuh"
 #include "hx_kernels.cuh"
 
 namespace cs {
@@ -57,6 +58,23 @@ struct Vec<double, ST> {
   static __device__ __forceinline__ void store(double* p, const double* v) {
 #pragma unroll
     for (int i = 0; i < ST; i += 2) reinterpret_cast<double2*>(p)[i / 2] = make_double2(v[i], v[i + 1]);
+  }
+};
+
+template <int ST>
+struct Vec<df64, ST> {
+  static __device__ __forceinline__ void load(const df64* p, df64* v) {
+#pragma unroll
+    for (int i = 0; i < ST; i += 2) {
+      const float4 a = reinterpret_cast<const float4*>(p)[i / 2];
+      v[i] = df64(a.x, a.y);
+      v[i + 1] = df64(a.z, a.w);
+    }
+  }
+  static __device__ __forceinline__ void store(df64* p, const df64* v) {
+#pragma unroll
+    for (int i = 0; i < ST; i += 2)
+      reinterpret_cast<float4*>(p)[i / 2] = make_float4(v[i].hi, v[i].lo, v[i + 1].hi, v[i + 1].lo);
   }
 };
 

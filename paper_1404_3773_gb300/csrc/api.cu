@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "cs_internal.h"
+#include "df64.cuh"
 #include "hx_kernels.cuh"
 #include "kb_tc.h"
 
@@ -56,9 +58,12 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.lanV = take(d * (kMaxLanczos + 2) * 8);
   o.status = take(64 * sizeof(int));
   // last, so that every other offset is the same for both precisions
-  o.X32 = take(prec != CS_FP64 ? d * ns * 4 : 0);
+  auto is_f32 = [](cs_precision p) { return p == CS_FP32 || p == CS_MIXED_BF16; };
+  const bool reduced = is_f32(prec) || is_f32(c->rr_prec);
+  const bool mixed = prec == CS_MIXED_BF16 || c->rr_prec == CS_MIXED_BF16;
+  o.X32 = take(reduced ? d * ns * 4 : 0);
   // scratch of the tensor-core projector products (mixed precision with projectors)
-  o.kbtc = take(prec == CS_MIXED_BF16 && np ? kb_tc_work_bytes(kb_tc_shape(T.d, (int)np, n_s)) : 0);
+  o.kbtc = take(mixed && np ? kb_tc_work_bytes(kb_tc_shape(T.d, (int)np, n_s)) : 0);
   o.total = off;
   return o;
 }
@@ -69,6 +74,8 @@ template <>
 DevTables<double>& tables<double>(cs_ctx* c) { return c->d64; }
 template <>
 DevTables<float>& tables<float>(cs_ctx* c) { return c->d32; }
+template <>
+DevTables<df64>& tables<df64>(cs_ctx* c) { return c->ddf; }
 
 cs_status fail(cs_ctx* c, cs_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -118,9 +125,12 @@ struct ProfScope {
     (ctx)->launches += (nk);               \
   } while (0)
 #define CS_LAUNCH(ctx, nk, expr) CS_LAUNCH_CLS(ctx, 3, nk, expr)
-constexpr int kProfFamilies = 5;  // classes per precision (see cs_ctx::prof)
+constexpr int kProfFamilies = 5;  // classes per arithmetic (see cs_ctx::prof)
 template <typename T>
-constexpr int prof_cls(int family) { return family + (sizeof(T) == 4 ? kProfFamilies : 0); }
+constexpr int prof_cls(int family) {
+  return family + (std::is_same<T, float>::value ? kProfFamilies
+                   : std::is_same<T, df64>::value ? 2 * kProfFamilies : 0);
+}
 
 cs_status need_device(cs_ctx* c) {
   if (!c) return CS_ERR_ARG;
@@ -144,7 +154,8 @@ cs_status upload(cs_ctx* c, T** dst, const std::vector<double>& src) {
 
 template <typename T>
 void free_tables(DevTables<T>& D) {
-  T** ptrs[] = {&D.rad, &D.theta, &D.trig, &D.wv, &D.wkj, &D.half_lambda, &D.pcoef, &D.h};
+  T** ptrs[] = {&D.rad, &D.theta, &D.trig, &D.wv, &D.wkj, &D.half_lambda, &D.pcoef, &D.h,
+                &D.theta_pairs};
   for (T** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -161,6 +172,11 @@ cs_status upload_tables(cs_ctx* c) {
   const int rows = (H.n_theta + 1) / 2;
   std::vector<double> th(H.theta.begin(), H.theta.begin() + (size_t)rows * rowlen);
   if ((st = upload<T>(c, &D.theta, th)) != CS_OK) return st;
+  if (sizeof(T) == 4) {
+    std::vector<double> tp;
+    build_theta_pairs(th, H.L, H.n_theta, tp);
+    if ((st = upload<T>(c, &D.theta_pairs, tp)) != CS_OK) return st;
+  }
   const int Q = c->Q4 + 1;
   std::vector<double> trig((size_t)2 * H.L * Q);
   for (int m = 0; m < H.L; ++m)
@@ -196,7 +212,9 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   const Layout lay = layout(c, n_s, CS_FP64);
   T* G = reinterpret_cast<T*>(work + lay.G);
   const T* kb = nullptr;
-  if (c->n_p > 0) {
+  if constexpr (std::is_same<T, df64>::value) {
+    if (c->n_p > 0) return fail(c, CS_ERR_STATE, "CS_DF64 does not apply projectors");
+  } else if (c->n_p > 0) {
     // kb = P diag(h) P^T X  (Sec. 2.3.2: a pair of matrix products)
     T* kbZ = reinterpret_cast<T*>(work + lay.kbZ);
     if (tc) {
@@ -226,15 +244,17 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   tt.kpad_synth = c->tc_kpad_synth;
   tt.m_tiles_anal = c->tc_mt_anal;
   tt.kpad_anal = c->tc_kpad_anal;
+  if (tc && !std::is_same<T, float>::value)
+    return fail(c, CS_ERR_ARG, "tensor-core path needs float blocks");
   if (tc) {
-    if (sizeof(T) != 4) return fail(c, CS_ERR_ARG, "tensor-core path needs float blocks");
     CS_LAUNCH_CLS(c, prof_cls<T>(0), 1, launch_tc_radial_synth(tt, H, reinterpret_cast<const float*>(X), ldx,
                                                   reinterpret_cast<float*>(G), n_s, c->dev_err,
                                                   st));
   } else {
     CS_LAUNCH_CLS(c, prof_cls<T>(0), 1, launch_radial_synth<T>(X, ldx, G, D.rad, H.L, H.N, H.n_r, n_s, st));
   }
-  AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj};
+  AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj,
+               D.theta_pairs};
   CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
   Epilogue<T> ep;
   ep.mode = mode;
@@ -290,6 +310,21 @@ cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a
   return CS_OK;
 }
 
+// Gram matrix and block rotation of the ChFSI iteration in the context's dense precision
+cudaError_t dense_gram(const cs_ctx* c, const double* A, long long lda, const double* B,
+                       long long ldb, long long d, int na, int nb, double* C, int ldc,
+                       double* part, cudaStream_t st) {
+  return c->dense_prec == CS_DF64
+             ? launch_gram_df(A, lda, B, ldb, d, na, nb, C, ldc, part, st)
+             : launch_gram<double>(A, lda, B, ldb, d, na, nb, C, ldc, part, st);
+}
+cudaError_t dense_rotate(const cs_ctx* c, const double* A, long long lda, const double* Q, int ldq,
+                         long long d, int k, int n, double* C, long long ldc, cudaStream_t st) {
+  return c->dense_prec == CS_DF64
+             ? launch_gemm_nn_df(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st)
+             : launch_gemm_nn<double>(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st);
+}
+
 cs_status cholqr_core(cs_ctx* c, int n_s, double* X, long long ld, char* work, cudaStream_t st,
                       int* status_dev) {
   const HostTables& H = c->host;
@@ -300,9 +335,9 @@ cs_status cholqr_core(cs_ctx* c, int n_s, double* X, long long ld, char* work, c
   double* U = M + (size_t)n_s * n_s;
   double* w = U + (size_t)n_s * n_s;
   for (int pass = 0; pass < 2; ++pass) {
-    CS_LAUNCH(c, 2, launch_gram(X, ld, X, ld, H.d, n_s, n_s, M, n_s, part, st));
+    CS_LAUNCH(c, 2, dense_gram(c, X, ld, X, ld, H.d, n_s, n_s, M, n_s, part, st));
     CS_LAUNCH(c, 1, launch_cholqr_factor(M, n_s, U, w, status_dev + pass, st));
-    CS_LAUNCH(c, 1, launch_gemm_nn(X, ld, U, n_s, H.d, n_s, n_s, 1.0, 0.0, tmp, H.d, st));
+    CS_LAUNCH(c, 1, dense_rotate(c, X, ld, U, n_s, H.d, n_s, n_s, tmp, H.d, st));
     CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   }
   return CS_OK;
@@ -324,13 +359,35 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   double* Hs = reinterpret_cast<double*>(work + lay.small);
   double* Q = Hs + (size_t)n_s * n_s;
   double* jw = Q + (size_t)n_s * n_s;
-  cs_status r = hx_core<double>(c, n_s, X, ld, HX, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st);
+  cs_status r;
+  if (c->rr_prec == CS_FP64) {
+    r = hx_core<double>(c, n_s, X, ld, HX, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st);
+  } else if (c->rr_prec == CS_DF64) {
+    // H X in double-float: block split into tmp, product into HX, widened in place
+    df64* Xd = reinterpret_cast<df64*>(work + lay.tmp);
+    df64* Yd = reinterpret_cast<df64*>(work + lay.HX);
+    CS_LAUNCH(c, 1, launch_to_df64(X, ld, Xd, H.d, H.d, n_s, st));
+    r = hx_core<df64>(c, n_s, Xd, H.d, Yd, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st);
+    if (r != CS_OK) return r;
+    CS_LAUNCH(c, 1, launch_from_df64(Yd, H.d, HX, H.d, H.d, n_s, st));
+  } else {
+    // H X in the reduced precision (FP32 block in X32, result in tmp), then back to FP64;
+    // the projection, eigensolve, rotations and residual norms below stay FP64
+    const Layout lr = layout(c, n_s, c->rr_prec);
+    float* X32 = reinterpret_cast<float*>(work + lr.X32);
+    float* HX32 = reinterpret_cast<float*>(work + lay.tmp);
+    CS_LAUNCH(c, 1, launch_convert_f64_to_f32(X, ld, X32, H.d, H.d, n_s, st));
+    r = hx_core<float>(c, n_s, X32, H.d, HX32, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st,
+                       c->rr_prec == CS_MIXED_BF16);
+    if (r != CS_OK) return r;
+    CS_LAUNCH(c, 1, launch_convert_f32_to_f64(HX32, H.d, HX, H.d, H.d, n_s, st));
+  }
   if (r != CS_OK) return r;
-  CS_LAUNCH(c, 2, launch_gram(X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st));
+  CS_LAUNCH(c, 2, dense_gram(c, X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st));
   CS_LAUNCH(c, 1, launch_jacobi_eig(Hs, n_s, theta, Q, jw, status_dev, st));
-  CS_LAUNCH(c, 1, launch_gemm_nn(X, ld, Q, n_s, H.d, n_s, n_s, 1.0, 0.0, tmp, H.d, st));
+  CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
   CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
-  CS_LAUNCH(c, 1, launch_gemm_nn(HX, H.d, Q, n_s, H.d, n_s, n_s, 1.0, 0.0, tmp, H.d, st));
+  CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
   CS_LAUNCH(c, 1, launch_residuals(X, ld, tmp, H.d, H.d, n_s, theta, resid, st));
   if (HX_out) CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, HX_out, ld, H.d, n_s, st));
   return CS_OK;
@@ -359,6 +416,11 @@ cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degre
   cs_status s;
   if (prec == CS_FP64) {
     s = cheb_core<double>(c, n_s, X, ld, degree, a, b, a0, wk, st);
+  } else if (prec == CS_DF64) {
+    df64* Xd = reinterpret_cast<df64*>(wk + lay.tmp);
+    CS_LAUNCH(c, 1, launch_to_df64(X, ld, Xd, H.d, H.d, n_s, st));
+    s = cheb_core<df64>(c, n_s, Xd, H.d, degree, a, b, a0, wk, st);
+    if (s == CS_OK) CS_LAUNCH(c, 1, launch_from_df64(Xd, H.d, X, ld, H.d, n_s, st));
   } else {
     float* X32 = reinterpret_cast<float*>(wk + lay.X32);
     CS_LAUNCH(c, 1, launch_convert_f64_to_f32(X, ld, X32, H.d, H.d, n_s, st));
@@ -422,6 +484,7 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
     }
     cs_status st = upload_tables<double>(c);
     if (st == CS_OK) st = upload_tables<float>(c);
+    if (st == CS_OK) st = upload_tables<df64>(c);
     if (st == CS_OK) {
       for (int mode = 0; mode < 2 && st == CS_OK; ++mode) {
         std::vector<uint16_t> tab;
@@ -467,6 +530,7 @@ cs_status cs_basis_free(cs_ctx* c) {
     cudaDeviceSynchronize();
     free_tables(c->d64);
     free_tables(c->d32);
+    free_tables(c->ddf);
     for (auto& r : c->prof_recs) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -522,7 +586,7 @@ cs_status cs_set_potential(cs_ctx* c, const double* v_grid, cs_stream stream) {
   const HostTables& H = c->host;
   cudaStream_t st = (cudaStream_t)stream;
   CS_LAUNCH(c, 1, launch_weighted_potential(v_grid, c->d64.wkj, H.n_r * H.n_theta, H.n_phi,
-                                            c->d64.wv, c->d32.wv, st));
+                                            c->d64.wv, c->d32.wv, c->ddf.wv, st));
   c->has_potential = true;
   return CS_OK;
 }
@@ -558,6 +622,22 @@ cs_status cs_set_projectors(cs_ctx* c, int n_p, const double* p_coef, const doub
   CS_LAUNCH(c, 2, build_kb_tc_tables(c->d64.pcoef, (long long)d, n_p, c->kb_tabA, c->kb_tabB, st));
   CS_CHECK_CUDA(c, cudaStreamSynchronize(st));
   c->n_p = n_p;
+  return CS_OK;
+}
+
+cs_status cs_set_rr_precision(cs_ctx* c, cs_precision prec) {
+  if (!c) return CS_ERR_ARG;
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16 && prec != CS_DF64)
+    return fail(c, CS_ERR_ARG, "unknown precision");
+  c->rr_prec = prec;
+  return CS_OK;
+}
+
+cs_status cs_set_dense_precision(cs_ctx* c, cs_precision prec) {
+  if (!c) return CS_ERR_ARG;
+  if (prec != CS_FP64 && prec != CS_DF64)
+    return fail(c, CS_ERR_ARG, "dense precision must be CS_FP64 or CS_DF64");
+  c->dense_prec = prec;
   return CS_OK;
 }
 
@@ -620,6 +700,18 @@ cs_status cs_apply_H(cs_ctx* c, int n_s, const void* X, void* HX, long long ld,
   if (prec == CS_FP32 || prec == CS_MIXED_BF16)
     return hx_core<float>(c, n_s, (const float*)X, ld, (float*)HX, ld, EP_APPLY, 0, 0, 0,
                           nullptr, (char*)work, st, prec == CS_MIXED_BF16);
+  if (prec == CS_DF64) {
+    const HostTables& H = c->host;
+    const Layout lay = layout(c, n_s, CS_DF64);
+    df64* Xd = reinterpret_cast<df64*>((char*)work + lay.tmp);
+    df64* Yd = reinterpret_cast<df64*>((char*)work + lay.HX);
+    CS_LAUNCH(c, 1, launch_to_df64((const double*)X, ld, Xd, H.d, H.d, n_s, st));
+    cs_status r = hx_core<df64>(c, n_s, Xd, H.d, Yd, H.d, EP_APPLY, 0, 0, 0, nullptr,
+                                (char*)work, st);
+    if (r != CS_OK) return r;
+    CS_LAUNCH(c, 1, launch_from_df64(Yd, H.d, (double*)HX, ld, H.d, n_s, st));
+    return CS_OK;
+  }
   return fail(c, CS_ERR_ARG, "unknown precision");
 }
 
@@ -637,6 +729,15 @@ cs_status cs_cheb_filter(cs_ctx* c, int n_s, void* X, long long ld, int degree, 
   if (prec == CS_FP32 || prec == CS_MIXED_BF16)
     return cheb_core<float>(c, n_s, (float*)X, ld, degree, a, b, a0, (char*)work, st,
                             prec == CS_MIXED_BF16);
+  if (prec == CS_DF64) {
+    const HostTables& H = c->host;
+    df64* Xd = reinterpret_cast<df64*>((char*)work + layout(c, n_s, CS_DF64).tmp);
+    CS_LAUNCH(c, 1, launch_to_df64((const double*)X, ld, Xd, H.d, H.d, n_s, st));
+    cs_status r = cheb_core<df64>(c, n_s, Xd, H.d, degree, a, b, a0, (char*)work, st);
+    if (r != CS_OK) return r;
+    CS_LAUNCH(c, 1, launch_from_df64(Xd, H.d, (double*)X, ld, H.d, n_s, st));
+    return CS_OK;
+  }
   return fail(c, CS_ERR_ARG, "unknown precision");
 }
 
@@ -736,7 +837,7 @@ cs_status cs_chfsi(cs_ctx* c, int n_s, int n_want, double* X, long long ld, int 
   if (n_want < 1 || n_want > n_s || degree < 1 || max_iter < 1 || !v0 || !theta || !resid ||
       !work)
     return fail(c, CS_ERR_ARG, "bad ChFSI arguments");
-  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16 && prec != CS_DF64)
     return fail(c, CS_ERR_ARG, "unknown precision");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   const HostTables& H = c->host;
@@ -781,7 +882,7 @@ cs_status cs_chfsi_step(cs_ctx* c, int n_s, double* X, long long ld, int degree,
   if (degree < 1 || !theta || !resid || !work) return fail(c, CS_ERR_ARG, "bad ChFSI step arguments");
   if (!(a < b) || !(a0 < a)) return fail(c, CS_ERR_ARG, "need a0 < a < b");
   if (n_s > 1024) return fail(c, CS_ERR_ARG, "n_s > 1024 not supported");
-  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16)
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16 && prec != CS_DF64)
     return fail(c, CS_ERR_ARG, "unknown precision");
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   return chfsi_step_core(c, n_s, X, ld, degree, a, b, a0, prec, theta, resid, (char*)work,

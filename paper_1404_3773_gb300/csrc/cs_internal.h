@@ -12,6 +12,8 @@
 
 namespace cs {
 
+struct df64;  // double-float value (df64.cuh)
+
 // ---------------------------------------------------------------- host tables (setup.cpp)
 struct HostTables {
   double R = 0;
@@ -50,6 +52,7 @@ struct DevTables {
   T* half_lambda = nullptr;// [alpha]
   T* pcoef = nullptr;      // [p][alpha] (d x n_p column-major)
   T* h = nullptr;          // [p] projector couplings
+  T* theta_pairs = nullptr;// transposed Legendre rows of the register-blocked FP32 kernel
 };
 
 }  // namespace cs
@@ -60,9 +63,12 @@ struct cs_ctx {
   bool has_device = false;
   bool has_potential = false;
   int n_p = 0;
+  cs_precision rr_prec = CS_FP64;  // precision of the H.X that Rayleigh-Ritz projects
+  cs_precision dense_prec = CS_FP64;  // Gram matrices and block rotations (FP64 or DF64)
   int Q4 = 0;              // floor(n_phi / 4): folded phi range q = 0 .. Q4
   cs::DevTables<double> d64;
   cs::DevTables<float> d32;
+  cs::DevTables<cs::df64> ddf;  // double-float copies (CS_DF64)
   double* w_r_dev = nullptr; // radial weights (for forward transforms of grid data)
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
@@ -74,7 +80,7 @@ struct cs_ctx {
   long long launches = 0;
   // measurement hooks (cs_profile_begin / cs_profile_end): class = kernel family
   // (0 radial synthesis, 1 angular, 2 radial analysis, 3 dense FP64, 4 projectors) + 5 when
-  // the launch runs in FP32 / mixed precision
+  // the launch runs in FP32 / mixed precision, + 10 in double-float
   bool prof = false;
   struct ProfRec {
     int cls;

@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include "cs_internal.h"
+#include "df64.cuh"
 #include "hx_kernels.cuh"
 #include "hx_device.cuh"
 
@@ -274,7 +275,7 @@ static cudaError_t launch_angular_st(const AngArgs<T>& a, int st, T* G, T* gout,
 
 // Which ANG_FULL kernel runs. FP32: the register-blocked kernel (angular_gm.cu) when its
 // tile fits in shared memory, else the row-pair kernel (angular_rp.cu); FP64: the row-pair
-// kernel; both fall back to the row-stream kernel above. CS_ANGULAR_KERNEL=gm|gmN|rp|rpN|stream
+// kernel; both fall back to the row-stream kernel above. CS_ANGULAR_KERNEL=gm|rp|rpN|stream
 // overrides the choice (N = tile variant), for tuning.
 static int angular_choice(int& variant) {
   variant = -1;
@@ -300,7 +301,7 @@ cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T
     const int choice = angular_choice(variant);
     if constexpr (sizeof(T) == 4) {
       if (choice == 0 || choice == 1) {
-        cudaError_t e = launch_angular_gm(a, G, variant, stream);
+        cudaError_t e = launch_angular_gm(a, G, stream);
         if (e != cudaErrorInvalidConfiguration) return e;
       }
     }
@@ -351,6 +352,13 @@ template cudaError_t launch_radial_anal<double>(const double*, const double*, in
                                                 int, const Epilogue<double>&, cudaStream_t);
 template cudaError_t launch_radial_anal<float>(const float*, const float*, int, int, int, int,
                                                const Epilogue<float>&, cudaStream_t);
+template cudaError_t launch_angular<df64>(const AngArgs<df64>&, int, df64*, df64*, const df64*,
+                                         cudaStream_t);
+template cudaError_t launch_radial_synth<df64>(const df64*, long long, df64*, const df64*, int,
+                                               int, int, int, cudaStream_t);
+template cudaError_t launch_radial_anal<df64>(const df64*, const df64*, int, int, int, int,
+                                              const Epilogue<df64>&, cudaStream_t);
+template int pick_states_per_cta<df64>(int, int, int);
 template int pick_states_per_cta<double>(int, int, int);
 template int pick_states_per_cta<float>(int, int, int);
 

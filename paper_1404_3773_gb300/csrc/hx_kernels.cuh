@@ -4,8 +4,11 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 namespace cs {
+
+struct df64;  // double-float value (df64.cuh)
 
 enum { EP_PLAIN = 0, EP_APPLY = 1, EP_CHEB = 2 };
 enum { ANG_FULL = 0, ANG_SYNTH = 1, ANG_ANAL = 2 };
@@ -35,6 +38,8 @@ struct AngArgs {
   const T* trig;   // [2][L][Q4+1]
   const T* wv;     // [k][j][q]
   const T* wkj;    // [k][j] = w_r w_t 2 pi / Nphi (forward transforms of grid data)
+  const T* theta_pairs = nullptr;  // FP32 only: Legendre rows by chunks of 8 mirrored pairs,
+                                   // transposed ([chunk][packed (m,l) + 4][pair]); may be null
 };
 
 template <typename T>
@@ -48,9 +53,13 @@ cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T
 template <typename T>
 cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream_t stream);
 
-// register-blocked FP32 angular kernel (angular_gm.cu); variant 0: 8 row pairs per chunk,
-// 1: 4; cudaErrorInvalidConfiguration when no tile fits in shared memory
-cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, int variant, cudaStream_t stream);
+// register-blocked FP32 angular kernel (angular_gm.cu); cudaErrorInvalidConfiguration when
+// its tile does not fit in shared memory or the transposed Legendre table is missing
+cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, cudaStream_t stream);
+// builds the transposed Legendre table of the register-blocked kernel from the packed rows
+// [ceil(n_theta/2)][L(L+1)/2] (host; returns the element count)
+size_t build_theta_pairs(const std::vector<double>& theta, int L, int n_theta,
+                         std::vector<double>& out);
 
 template <typename T>
 cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,
@@ -87,11 +96,18 @@ template <typename F>
 cudaError_t launch_gemm_nn(const F* A, long long lda, const F* Q, int ldq, long long d, int k,
                            int n, double alpha, double beta, F* C, long long ldc,
                            cudaStream_t stream);
+// the same two products on FP64 arrays with double-float arithmetic (FP32 pipe)
+cudaError_t launch_gram_df(const double* A, long long lda, const double* B, long long ldb,
+                           long long d, int na, int nb, double* C, int ldc, double* partial,
+                           cudaStream_t stream);
+cudaError_t launch_gemm_nn_df(const double* A, long long lda, const double* Q, int ldq,
+                              long long d, int k, int n, double alpha, double beta, double* C,
+                              long long ldc, cudaStream_t stream);
 // y[p + s ld] *= h[p] for p < n_p, s < S
 template <typename F>
 cudaError_t launch_scale_rows(F* y, int n_p, int S, int ld, const F* h, cudaStream_t stream);
 // From the Gram matrix M (n x n): U = D R^{-1}, D = diag(M)^(-1/2), D M D = R^T R.
-// work: n*n + n doubles. status[0] = 0 ok, else 1 + index of the failing pivot.
+// work: n*n + 2n doubles. status[0] = 0 ok, else 1 + index of the failing pivot.
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream);
 // Symmetric eigensolve of sym(A) (n x n, lda = n): theta ascending, V (n x n) columns.
@@ -114,9 +130,16 @@ cudaError_t launch_copy_block(const T* x, long long ldx, T* y, long long ldy, lo
 // y = x / sqrt(*nrm2)  (length d)
 cudaError_t launch_scale_inv_sqrt(const double* x, double* y, long long d, const double* nrm2,
                                   cudaStream_t stream);
-// W V table: wv64[kj * n_phi + q] = wkj[kj] * v[kj * n_phi + q]; wv32 = (float) wv64
+// W V table: wv64[kj * n_phi + q] = wkj[kj] * v[kj * n_phi + q]; wv32 = (float) wv64;
+// wvdf (optional) = wv64 split into double-float
 cudaError_t launch_weighted_potential(const double* v, const double* wkj, int n_kj, int n_phi,
-                                      double* wv64, float* wv32, cudaStream_t stream);
+                                      double* wv64, float* wv32, df64* wvdf,
+                                      cudaStream_t stream);
+// double <-> double-float d x n blocks (in place allowed: same element size)
+cudaError_t launch_to_df64(const double* x, long long ldx, df64* y, long long ldy, long long d,
+                           int n, cudaStream_t stream);
+cudaError_t launch_from_df64(const df64* x, long long ldx, double* y, long long ldy, long long d,
+                             int n, cudaStream_t stream);
 // Lanczos tridiagonal T (k x k) from alpha[k] and the squared off-diagonals beta2[k-1]
 cudaError_t launch_build_tridiag(const double* alpha, const double* beta2, int k, double* T,
                                  cudaStream_t stream);

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <utility>
 
+#include "df64.cuh"
 #include "hx_kernels.cuh"
 
 namespace cs {
@@ -45,7 +46,13 @@ size_t gram_partial_elems(long long d, int na, int nb) {
   return (size_t)chunks * (size_t)na * (size_t)nb;
 }
 
-template <typename F, int U>
+// storage value of a compute-type accumulator
+__device__ __forceinline__ double out_val(double v) { return v; }
+__device__ __forceinline__ float out_val(float v) { return v; }
+__device__ __forceinline__ double out_val(df64 v) { return v.to_double(); }
+
+// F: storage type of A, B and the partials; C: arithmetic (F, or df64 for F = double)
+template <typename F, typename C, int U>
 __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, long long lda,
                                                        const F* __restrict__ B,
                                                        long long ldb, long long d, int na,
@@ -56,26 +63,26 @@ __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, l
   const int chunk = blockIdx.z;
   const long long r0 = (long long)chunk * rows;
   const long long r1 = min(d, r0 + rows);
-  __shared__ F As[GK][T + 1];
-  __shared__ F Bs[GK][T + 1];
+  __shared__ C As[GK][T + 1];
+  __shared__ C Bs[GK][T + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  F acc[U][U];
+  C acc[U][U];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = F(0);
+    for (int v = 0; v < U; ++v) acc[u][v] = C(0);
   for (long long rb = r0; rb < r1; rb += GK) {
     for (int idx = tid; idx < GK * T; idx += 256) {
       int rr = idx % GK, cc = idx / GK;
       long long r = rb + rr;
       int i = i0 + cc, j = j0 + cc;
-      As[rr][cc] = (r < r1 && i < na) ? A[r + (long long)i * lda] : F(0);
-      Bs[rr][cc] = (r < r1 && j < nb) ? B[r + (long long)j * ldb] : F(0);
+      As[rr][cc] = (r < r1 && i < na) ? C(A[r + (long long)i * lda]) : C(0);
+      Bs[rr][cc] = (r < r1 && j < nb) ? C(B[r + (long long)j * ldb]) : C(0);
     }
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < GK; ++rr) {
-      F a[U], b[U];
+      C a[U], b[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) a[u] = As[rr][tx + 16 * u];
 #pragma unroll
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, l
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
-      if (i < na && j < nb) P[i + (size_t)j * na] = acc[u][v];
+      if (i < na && j < nb) P[i + (size_t)j * na] = out_val(acc[u][v]);
     }
 }
 
@@ -118,29 +125,41 @@ __global__ void k_gram_reduce(const F* __restrict__ partial, int chunks, int na,
   }
 }
 
-template <typename F>
-cudaError_t launch_gram(const F* A, long long lda, const F* B, long long ldb, long long d, int na,
-                        int nb, F* C, int ldc, F* partial, cudaStream_t stream) {
+template <typename F, typename C>
+static cudaError_t gram_impl(const F* A, long long lda, const F* B, long long ldb, long long d,
+                             int na, int nb, F* Cout, int ldc, F* partial, cudaStream_t stream) {
   int u, ta, tb, chunks;
   long long rows;
   gram_shape(d, na, nb, u, ta, tb, chunks, rows);
   dim3 grid(ta, tb, chunks);
   switch (u) {
-    case 1: k_gram_partial<F, 1><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 2: k_gram_partial<F, 2><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 3: k_gram_partial<F, 3><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 4: k_gram_partial<F, 4><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    case 5: k_gram_partial<F, 5><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
-    default: k_gram_partial<F, 6><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 1: k_gram_partial<F, C, 1><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 2: k_gram_partial<F, C, 2><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 3: k_gram_partial<F, C, 3><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 4: k_gram_partial<F, C, 4><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    case 5: k_gram_partial<F, C, 5><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
+    default: k_gram_partial<F, C, 6><<<grid, 256, 0, stream>>>(A, lda, B, ldb, d, na, nb, rows, partial); break;
   }
   int tot = na * nb;
-  k_gram_reduce<F><<<(tot + 31) / 32, 256, 0, stream>>>(partial, chunks, na, nb, C, ldc);
+  k_gram_reduce<F><<<(tot + 31) / 32, 256, 0, stream>>>(partial, chunks, na, nb, Cout, ldc);
   return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t launch_gram(const F* A, long long lda, const F* B, long long ldb, long long d, int na,
+                        int nb, F* C, int ldc, F* partial, cudaStream_t stream) {
+  return gram_impl<F, F>(A, lda, B, ldb, d, na, nb, C, ldc, partial, stream);
+}
+
+cudaError_t launch_gram_df(const double* A, long long lda, const double* B, long long ldb,
+                           long long d, int na, int nb, double* C, int ldc, double* partial,
+                           cudaStream_t stream) {
+  return gram_impl<double, df64>(A, lda, B, ldb, d, na, nb, C, ldc, partial, stream);
 }
 
 // ------------------------------------------------------------------ C = alpha A Q + beta C
 // 64 rows x (16U) columns per CTA; U from n so that 80 states are one column tile.
-template <typename F, int U>
+template <typename F, typename Cm, int U>
 __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long long lda,
                                                   const F* __restrict__ Q, int ldq,
                                                   long long d, int K, int n, F alpha,
@@ -148,30 +167,30 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long l
   constexpr int BM = 64, BN = 16 * U;
   const long long r0 = (long long)blockIdx.x * BM;
   const int j0 = blockIdx.y * BN;
-  __shared__ F As[GK][BM + 1];  // As[k][r]
-  __shared__ F Qs[GK][BN + 1];  // Qs[k][j]
+  __shared__ Cm As[GK][BM + 1];  // As[k][r]
+  __shared__ Cm Qs[GK][BN + 1];  // Qs[k][j]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  F acc[4][U];
+  Cm acc[4][U];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = F(0);
+    for (int v = 0; v < U; ++v) acc[u][v] = Cm(0);
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int idx = tid; idx < GK * BM; idx += 256) {
       int rr = idx % BM, kk = idx / BM;
       long long r = r0 + rr;
       int k = k0 + kk;
-      As[kk][rr] = (r < d && k < K) ? A[r + (long long)k * lda] : F(0);
+      As[kk][rr] = (r < d && k < K) ? Cm(A[r + (long long)k * lda]) : Cm(0);
     }
     for (int idx = tid; idx < GK * BN; idx += 256) {
       int kk = idx % GK, jj = idx / GK;
       int k = k0 + kk, j = j0 + jj;
-      Qs[kk][jj] = (k < K && j < n) ? Q[k + (long long)j * ldq] : F(0);
+      Qs[kk][jj] = (k < K && j < n) ? Cm(Q[k + (long long)j * ldq]) : Cm(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      F a[4], b[U];
+      Cm a[4], b[U];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
 #pragma unroll
@@ -192,26 +211,40 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long l
       long long r = r0 + tx + 16 * u;
       if (r >= d) continue;
       F* c = C + r + (long long)j * ldc;
-      *c = (beta == F(0)) ? alpha * acc[u][v] : fma(alpha, acc[u][v], beta * *c);
+      *c = (beta == F(0)) ? out_val(Cm(alpha) * acc[u][v])
+                          : out_val(fma(Cm(alpha), acc[u][v], Cm(beta) * Cm(*c)));
     }
   }
+}
+
+template <typename F, typename Cm>
+static cudaError_t gemm_nn_impl(const F* A, long long lda, const F* Q, int ldq, long long d,
+                                int k, int n, double alpha, double beta, F* C, long long ldc,
+                                cudaStream_t stream) {
+  const int u = tile_u(n);
+  dim3 grid((unsigned)((d + 63) / 64), (n + 16 * u - 1) / (16 * u));
+  switch (u) {
+    case 1: k_gemm_nn<F, Cm, 1><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 2: k_gemm_nn<F, Cm, 2><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 3: k_gemm_nn<F, Cm, 3><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 4: k_gemm_nn<F, Cm, 4><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    case 5: k_gemm_nn<F, Cm, 5><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+    default: k_gemm_nn<F, Cm, 6><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
+  }
+  return cudaGetLastError();
 }
 
 template <typename F>
 cudaError_t launch_gemm_nn(const F* A, long long lda, const F* Q, int ldq, long long d, int k,
                            int n, double alpha, double beta, F* C, long long ldc,
                            cudaStream_t stream) {
-  const int u = tile_u(n);
-  dim3 grid((unsigned)((d + 63) / 64), (n + 16 * u - 1) / (16 * u));
-  switch (u) {
-    case 1: k_gemm_nn<F, 1><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-    case 2: k_gemm_nn<F, 2><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-    case 3: k_gemm_nn<F, 3><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-    case 4: k_gemm_nn<F, 4><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-    case 5: k_gemm_nn<F, 5><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-    default: k_gemm_nn<F, 6><<<grid, 256, 0, stream>>>(A, lda, Q, ldq, d, k, n, (F)alpha, (F)beta, C, ldc); break;
-  }
-  return cudaGetLastError();
+  return gemm_nn_impl<F, F>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc, stream);
+}
+
+cudaError_t launch_gemm_nn_df(const double* A, long long lda, const double* Q, int ldq,
+                              long long d, int k, int n, double alpha, double beta, double* C,
+                              long long ldc, cudaStream_t stream) {
+  return gemm_nn_impl<double, df64>(A, lda, Q, ldq, d, k, n, alpha, beta, C, ldc, stream);
 }
 
 template cudaError_t launch_gram<double>(const double*, long long, const double*, long long,
@@ -246,9 +279,12 @@ template cudaError_t launch_scale_rows<float>(float*, int, int, int, const float
 
 // ------------------------------------------------------------------ Cholesky-QR factor
 // One CTA. With column scaling D = diag(M)^(-1/2): D M D = L L^T (right-looking Cholesky,
-// one column per step), then U = D R^{-1} = D (L^{-1})^T, each thread forming one column of
-// L^{-1} by forward substitution. Working matrices in shared memory when 2 n^2 doubles fit
-// (n <= 112), else in `work` (global).
+// one column per step; one thread forms the pivot's reciprocal square root r_j and every
+// division is a multiplication by it), then U = D R^{-1} = D (L^{-1})^T: column c of L^{-1}
+// by forward substitution, one warp per column, the dot product of each row split over the
+// lanes. FP64 division and square root are long-latency on this GPU, so the serial chain
+// per step is one rsqrt and a short reduction. Working matrices in shared memory when they
+// fit (n <= 112), else in `work` (global).
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict__ M, int n,
                                                          double* __restrict__ U,
@@ -258,9 +294,10 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
   double* Lc = SMEM ? shc : work;                      // n x n, lower
   double* Yi = SMEM ? shc + (size_t)n * n : U;         // n x n, (L^{-1})^T (upper)
   double* Dv = SMEM ? shc + 2 * (size_t)n * n : work + (size_t)n * n;
+  double* rinv = Dv + n;                               // n: 1 / L_jj
   __shared__ int fail;
-  __shared__ double ljj;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nt >> 5;
   if (tid == 0) fail = 0;
   __syncthreads();
   for (int i = tid; i < n; i += nt) {
@@ -284,22 +321,26 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
+    // one thread forms the pivot's reciprocal square root (the FP64 pipe is narrow: a
+    // block-wide evaluation would cost a thousand times the work), all read it back
     if (tid == 0) {
-      double p = Lc[j + (size_t)j * n];
+      const double p = Lc[j + (size_t)j * n];
       if (!(p > 0.0) || !isfinite(p)) {
         fail = j + 1;
-        ljj = 1.0;
+        rinv[j] = 0.0;
       } else {
-        ljj = sqrt(p);
+        const double r = rsqrt(p);
+        rinv[j] = r;
+        Lc[j + (size_t)j * n] = p * r;
       }
-      Lc[j + (size_t)j * n] = ljj;
     }
     __syncthreads();
     if (fail) {
       if (tid == 0) status[0] = fail;
       return;
     }
-    for (int i = j + 1 + tid; i < n; i += nt) Lc[i + (size_t)j * n] /= ljj;
+    const double r = rinv[j];
+    for (int i = j + 1 + tid; i < n; i += nt) Lc[i + (size_t)j * n] *= r;
     __syncthreads();
     const int rem = n - j - 1;
     for (int e = tid; e < rem * rem; e += nt) {
@@ -308,12 +349,17 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
     }
     __syncthreads();
   }
-  // y = L^{-1} e_c (y_i = 0 for i < c), stored as Yi[c + i n] = (L^{-1})[i][c]
-  for (int c = tid; c < n; c += nt) {
-    for (int i = c; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) s -= Lc[i + (size_t)k * n] * Yi[c + (size_t)k * n];
-      Yi[c + (size_t)i * n] = s / Lc[i + (size_t)i * n];
+  // column c of L^{-1}: y_c = 1/L_cc, y_i = -(sum_{k=c}^{i-1} L_ik y_k) / L_ii, stored as
+  // Yi[c + i n]; one warp per column, columns dealt round-robin
+  for (int c = warp; c < n; c += nwarps) {
+    if (lane == 0) Yi[c + (size_t)c * n] = rinv[c];
+    __syncwarp();
+    for (int i = c + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = c + lane; k < i; k += 32) s = fma(Lc[i + (size_t)k * n], Yi[c + (size_t)k * n], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) Yi[c + (size_t)i * n] = -s * rinv[i];
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -323,7 +369,7 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
 
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream) {
-  size_t smem = (2 * (size_t)n * n + n) * sizeof(double);
+  size_t smem = (2 * (size_t)n * n + 2 * n) * sizeof(double);
   if (smem <= 200 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_cholqr_factor<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -926,6 +972,8 @@ cudaError_t launch_copy_block(const T* x, long long ldx, T* y, long long ldy, lo
 }
 template cudaError_t launch_copy_block<double>(const double*, long long, double*, long long,
                                                long long, int, cudaStream_t);
+template cudaError_t launch_copy_block<df64>(const df64*, long long, df64*, long long,
+                                            long long, int, cudaStream_t);
 template cudaError_t launch_copy_block<float>(const float*, long long, float*, long long,
                                               long long, int, cudaStream_t);
 
@@ -945,19 +993,52 @@ cudaError_t launch_scale_inv_sqrt(const double* x, double* y, long long d, const
 
 __global__ void k_weighted_potential(const double* __restrict__ v, const double* __restrict__ wkj,
                                      long long tot, int n_phi, double* __restrict__ wv64,
-                                     float* __restrict__ wv32) {
+                                     float* __restrict__ wv32, df64* __restrict__ wvdf) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     double w = wkj[e / n_phi] * v[e];
     wv64[e] = w;
     wv32[e] = (float)w;
+    if (wvdf) wvdf[e] = df64(w);
   }
 }
 
 cudaError_t launch_weighted_potential(const double* v, const double* wkj, int n_kj, int n_phi,
-                                      double* wv64, float* wv32, cudaStream_t stream) {
+                                      double* wv64, float* wv32, df64* wvdf,
+                                      cudaStream_t stream) {
   long long tot = (long long)n_kj * n_phi;
-  k_weighted_potential<<<elem_grid(tot), 256, 0, stream>>>(v, wkj, tot, n_phi, wv64, wv32);
+  k_weighted_potential<<<elem_grid(tot), 256, 0, stream>>>(v, wkj, tot, n_phi, wv64, wv32, wvdf);
+  return cudaGetLastError();
+}
+
+// double <-> double-float blocks (d x n, leading dimensions ldx / ldy); in place is allowed
+// (same element size, each element read and written by one thread)
+__global__ void k_to_df64(const double* x, long long ldx, df64* y, long long ldy, long long d,
+                          int n) {
+  const long long tot = d * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % d, j = e / d;
+    y[i + j * ldy] = df64(x[i + j * ldx]);
+  }
+}
+__global__ void k_from_df64(const df64* x, long long ldx, double* y, long long ldy, long long d,
+                            int n) {
+  const long long tot = d * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % d, j = e / d;
+    y[i + j * ldy] = x[i + j * ldx].to_double();
+  }
+}
+cudaError_t launch_to_df64(const double* x, long long ldx, df64* y, long long ldy, long long d,
+                           int n, cudaStream_t stream) {
+  k_to_df64<<<elem_grid(d * n), 256, 0, stream>>>(x, ldx, y, ldy, d, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_from_df64(const df64* x, long long ldx, double* y, long long ldy, long long d,
+                             int n, cudaStream_t stream) {
+  k_from_df64<<<elem_grid(d * n), 256, 0, stream>>>(x, ldx, y, ldy, d, n);
   return cudaGetLastError();
 }
 

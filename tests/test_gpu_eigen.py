@@ -20,8 +20,9 @@ def _bounds(Hh):
     return float(lam[24]), float(lam[-1]) + 1.0, float(lam[0]), lam
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
 @pytest.mark.parametrize("degree", [1, 2, 9])
-def test_cheb_filter_fp64_matches_oracle(degree):
+def test_cheb_filter_fp64_matches_oracle(degree, precision):
     torch, cs = need_gpu()
     w = SMALL
     ctx = make_ctx(w)
@@ -30,7 +31,8 @@ def test_cheb_filter_fp64_matches_oracle(degree):
     X = w.x_block()
     ref = eigen.cheb_filter(Hh.apply, X, degree, a, b, a0)
     Xd = to_dev(X, ld=ctx.d + 5)
-    cs.cs_cheb_filter(ctx, Xd, degree, a, b, a0, cs.CS_FP64)
+    cs.cs_cheb_filter(ctx, Xd, degree, a, b, a0,
+                      cs.CS_FP64 if precision == "fp64" else cs.CS_DF64)
     torch.cuda.synchronize()
     fro, col = rel_errors(to_host(Xd, ctx.d), ref)
     assert fro <= 1e-11 and col <= 1e-11, (fro, col)
@@ -179,3 +181,124 @@ def test_projector_pair_matches_oracle():
     torch.cuda.synchronize()
     fro, col = rel_errors(to_host(HXd, ctx.d), ref)
     assert fro <= 1e-11 and col <= 1e-11, (fro, col)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_chfsi_reduced_rayleigh_ritz_apply(precision):
+    """Rayleigh-Ritz on an FP32 / split-BF16 H X (cs_set_rr_precision; the projection,
+    eigensolve, rotations and residual norms stay FP64). The reduced H X perturbs the operator
+    by about 1e-6 |H| (FP32 tables and sums; split BF16 adds its 2^-17 operand error), so the
+    residuals level off and the Ritz values carry that perturbation: the solves run a fixed
+    number of iterations and the Ritz values are held to the accuracy measured for each
+    precision (FP32: 3.1e-6 Ha on the 32-atom cluster, |H| about 100 Ha), against the exact
+    oscillator levels and the all-FP64 ChFSI. This is why the FP64 apply is the default."""
+    torch, cs = need_gpu()
+    prec = {"fp32": cs.CS_FP32, "mixed": cs.CS_MIXED_BF16}[precision]
+    bound_ho, bound_c = {"fp32": (1e-6, 1e-5), "mixed": (1e-5, 1e-4)}[precision]
+    w = HO
+    ctx = make_ctx(w)
+    cs.cs_set_rr_precision(ctx, prec)
+    Xd = to_dev(w.x_block())
+    theta = torch.empty(w.n_s, dtype=torch.float64, device="cuda")
+    resid = torch.empty_like(theta)
+    v0 = torch.tensor(W.gaussian(99, ctx.d), device="cuda")
+    cs.cs_chfsi(ctx, Xd, w.n_want, w.degree, v0, theta, resid, tol=1e-12, max_iter=40,
+                precision=prec, raise_not_converged=False)
+    lev = np.loadtxt(__file__.replace("test_gpu_eigen.py", "golden/ho_levels.txt"))
+    dev_ho = np.max(np.abs(theta.cpu().numpy()[:10] - lev))
+
+    w = W.erf_cluster_32()
+    ctx = make_ctx(w)
+    X0 = to_dev(w.x_block())
+    v0 = torch.tensor(W.gaussian(2003, ctx.d), device="cuda")
+    th64 = torch.empty(w.n_s, dtype=torch.float64, device="cuda")
+    r64 = torch.empty_like(th64)
+    X64 = X0.clone()
+    it64 = cs.cs_chfsi(ctx, X64, w.n_want, w.degree, v0, th64, r64, tol=1e-8, max_iter=80,
+                       precision=cs.CS_FP64)
+    cs.cs_set_rr_precision(ctx, prec)
+    thr = torch.empty_like(th64)
+    rr = torch.empty_like(th64)
+    Xr = X0.clone()
+    cs.cs_chfsi(ctx, Xr, w.n_want, w.degree, v0, thr, rr, tol=1e-12, max_iter=it64 + 10,
+                precision=prec, raise_not_converged=False)
+    dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
+    floor = float(rr.cpu().numpy()[:w.n_want].max())
+    print(f"{precision}: oscillator max |dtheta| {dev_ho:.3e}; 32-atom cluster: FP64 "
+          f"iterations {it64}, max |dtheta| {dev:.3e}, residual floor {floor:.3e}")
+    assert dev_ho < bound_ho, dev_ho
+    assert floor < 1e-2, floor
+    assert dev < bound_c, dev
+
+
+def test_chfsi_double_float_rayleigh_ritz_holds_fp64_bars():
+    """Rayleigh-Ritz H X in double-float (cs_set_rr_precision CS_DF64). All-double-float
+    ChFSI (filter too) converges to residuals of 1e-8 with the oscillator's ten lowest levels
+    within 1e-9 Ha of the dense oracle eigenvalues. With the FP32 filter the subspace carries
+    the FP32 filter's noise (about 1e-7 per iteration), so residuals level off near 1e-6, but
+    the Ritz values, quadratic in that noise, stay within 1e-9 Ha: checked on the oscillator
+    against the dense oracle and on the 32-atom cluster against the all-FP64 ChFSI."""
+    torch, cs = need_gpu()
+    w = HO
+    lam = np.linalg.eigvalsh(oracle_H(w.name).dense())
+    for filt, tol in ((cs.CS_DF64, 1e-8), (cs.CS_FP32, 1e-5)):
+        ctx = make_ctx(w)
+        cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+        Xd = to_dev(w.x_block())
+        theta = torch.empty(w.n_s, dtype=torch.float64, device="cuda")
+        resid = torch.empty_like(theta)
+        v0 = torch.tensor(W.gaussian(99, ctx.d), device="cuda")
+        cs.cs_chfsi(ctx, Xd, w.n_want, w.degree, v0, theta, resid, tol=tol, max_iter=80,
+                    precision=filt)
+        th = theta.cpu().numpy()[:10]
+        assert np.max(np.abs(th - lam[:10])) < 1e-9, (filt, np.max(np.abs(th - lam[:10])))
+
+    w = W.erf_cluster_32()
+    ctx = make_ctx(w)
+    X0 = to_dev(w.x_block())
+    v0 = torch.tensor(W.gaussian(2003, ctx.d), device="cuda")
+    th64 = torch.empty(w.n_s, dtype=torch.float64, device="cuda")
+    r64 = torch.empty_like(th64)
+    it64 = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, th64, r64, tol=1e-8,
+                       max_iter=80, precision=cs.CS_FP64)
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+    for filt in (cs.CS_DF64, cs.CS_FP32):
+        thr = torch.empty_like(th64)
+        rr = torch.empty_like(th64)
+        it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-8,
+                         max_iter=it64 + 10, precision=filt,
+                         raise_not_converged=(filt == cs.CS_DF64))
+        dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
+        floor = float(rr.cpu().numpy()[:w.n_want].max())
+        print(f"filter {filt}: {it} iterations (FP64: {it64}), max |dtheta| vs FP64 "
+              f"{dev:.3e}, max residual {floor:.3e}")
+        assert dev < 1e-9, (filt, dev)
+
+
+def test_chfsi_double_float_gram_and_rotations():
+    """Cholesky-QR and Rayleigh-Ritz Gram matrices and block rotations in double-float
+    (cs_set_dense_precision CS_DF64), with the double-float Rayleigh-Ritz apply: the
+    all-double-float ChFSI of the 32-atom cluster reaches residuals of 1e-8 with its 64 lowest
+    Ritz values within 1e-9 Ha of the all-FP64 ChFSI, and the FP32-filter one within 1e-9 Ha
+    after as many iterations as the FP64 solve plus ten."""
+    torch, cs = need_gpu()
+    w = W.erf_cluster_32()
+    ctx = make_ctx(w)
+    X0 = to_dev(w.x_block())
+    v0 = torch.tensor(W.gaussian(2003, ctx.d), device="cuda")
+    th64 = torch.empty(w.n_s, dtype=torch.float64, device="cuda")
+    r64 = torch.empty_like(th64)
+    it64 = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, th64, r64, tol=1e-8,
+                       max_iter=80, precision=cs.CS_FP64)
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+    for filt in (cs.CS_DF64, cs.CS_FP32):
+        thr = torch.empty_like(th64)
+        rr = torch.empty_like(th64)
+        it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-8,
+                         max_iter=it64 + 10, precision=filt,
+                         raise_not_converged=(filt == cs.CS_DF64))
+        dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
+        print(f"dense df64, filter {filt}: {it} iterations (FP64: {it64}), max |dtheta| "
+              f"{dev:.3e}, max residual {float(rr.cpu().numpy()[:w.n_want].max()):.3e}")
+        assert dev < 1e-9, (filt, dev)

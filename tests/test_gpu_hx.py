@@ -53,6 +53,24 @@ def test_apply_H_fp64_matches_oracle(case):
     assert torch.all(HXd[:, ctx.d:] == 0)  # padding untouched
 
 
+@pytest.mark.parametrize("case", list(CASES))
+def test_apply_H_df64_matches_oracle(case):
+    """Double-float arithmetic on the FP32 pipe (about 48 significant bits) holds the FP64
+    bar, 1e-11 relative, against the FP64 oracle."""
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, ld=ctx.d + 3)
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_DF64)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    assert fro <= TOL64 and col <= TOL64, (fro, col)
+    assert torch.all(HXd[:, ctx.d:] == 0)
+
+
 @pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "lmax60_thin_radial"])
 def test_apply_H_fp32_error(case):
     torch, cs = need_gpu()
@@ -83,6 +101,11 @@ def test_apply_H_erf32_full_size():
     torch.cuda.synchronize()
     fro, col = rel_errors(to_host(HXd, ctx.d), ref)
     assert fro <= TOL64 and col <= TOL64, (fro, col)
+    HXdf = torch.empty_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXdf, cs.CS_DF64)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXdf, ctx.d), ref)
+    assert fro <= TOL64 and col <= TOL64, ("df64", fro, col)
     X32 = Xd.float()
     HX32 = torch.empty_like(X32)
     cs.cs_apply_H(ctx, X32, HX32, cs.CS_FP32)
