@@ -87,6 +87,11 @@ def dense_flops(d, n):
     return 2 * (2.0 * d * n * n + 2.0 * d * n * n) + (2.0 * d * n * n + 4.0 * d * n * n)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
+# capture of the kernel as it stands, on this workload; a class without a capture reports null
+NCU_TRAFFIC_BYTES = {"angular_f32": 32.402176e6 + 7.424e3}
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -138,7 +143,7 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
     dom = max(classes, key=lambda k: classes[k]["ms"])
     c = classes[dom]
     roofline = {"bound": c["bound"], "kernel": dom, "achieved": c["achieved"], "peak": c["peak"],
-                "unit": "TFLOP/s", "frac": c["frac"], "traffic": None,
+                "unit": "TFLOP/s", "frac": c["frac"], "traffic": NCU_TRAFFIC_BYTES.get(dom),
                 "peak_source": c["peak_source"], "flops_per_launch": c["flops_per_launch"],
                 "avg_launch_ms": c["avg_launch_ms"], "share": c["share"]}
     return roofline, classes

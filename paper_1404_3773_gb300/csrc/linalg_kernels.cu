@@ -278,26 +278,27 @@ template cudaError_t launch_scale_rows<double>(double*, int, int, int, const dou
 template cudaError_t launch_scale_rows<float>(float*, int, int, int, const float*, cudaStream_t);
 
 // ------------------------------------------------------------------ Cholesky-QR factor
-// One CTA. With column scaling D = diag(M)^(-1/2): D M D = L L^T (right-looking Cholesky,
-// one column per step; one thread forms the pivot's reciprocal square root r_j and every
-// division is a multiplication by it), then U = D R^{-1} = D (L^{-1})^T: column c of L^{-1}
-// by forward substitution, one warp per column, the dot product of each row split over the
-// lanes. FP64 division and square root are long-latency on this GPU, so the serial chain
-// per step is one rsqrt and a short reduction. Working matrices in shared memory when they
-// fit (n <= 112), else in `work` (global).
+// From the Gram matrix M: column scaling D = diag(M)^(-1/2), D M D = L L^T, U = D R^{-1} =
+// D (L^{-1})^T. Two launches:
+//  1. one CTA: right-looking Cholesky, one column per step; one thread forms the pivot's
+//     reciprocal square root r_j (FP64 division and square root are long-latency, and a
+//     block-wide evaluation would occupy the narrow FP64 pipe) and every division is a
+//     multiplication by it; L, D and r are written to `work`;
+//  2. one CTA per column c of L^{-1}: forward substitution y_c = r_c, y_i = -r_i
+//     sum_{k=c}^{i-1} L_ik y_k, one warp per column with the dot products split over the
+//     lanes, L staged in shared memory when it fits; the columns run on separate SMs, so the
+//     FP64 work spreads over the GPU instead of one SM's FP64 pipe.
 template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict__ M, int n,
-                                                         double* __restrict__ U,
-                                                         double* __restrict__ work,
-                                                         int* __restrict__ status) {
+__global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ M, int n,
+                                                    double* __restrict__ work,
+                                                    int* __restrict__ status) {
   extern __shared__ double shc[];
   double* Lc = SMEM ? shc : work;                      // n x n, lower
-  double* Yi = SMEM ? shc + (size_t)n * n : U;         // n x n, (L^{-1})^T (upper)
-  double* Dv = SMEM ? shc + 2 * (size_t)n * n : work + (size_t)n * n;
+  double* Dv = SMEM ? shc + (size_t)n * n : work + (size_t)n * n;
   double* rinv = Dv + n;                               // n: 1 / L_jj
   __shared__ int fail;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x, tx = tid & 31, ty = tid >> 5;
+  const int nty = nt >> 5;
   if (tid == 0) fail = 0;
   __syncthreads();
   for (int i = tid; i < n; i += nt) {
@@ -317,12 +318,9 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
   for (int e = tid; e < n * n; e += nt) {
     int i = e % n, j = e / n;
     Lc[e] = (i >= j) ? Dv[i] * M[e] * Dv[j] : 0.0;
-    Yi[e] = 0.0;
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    // one thread forms the pivot's reciprocal square root (the FP64 pipe is narrow: a
-    // block-wide evaluation would cost a thousand times the work), all read it back
     if (tid == 0) {
       const double p = Lc[j + (size_t)j * n];
       if (!(p > 0.0) || !isfinite(p)) {
@@ -342,41 +340,75 @@ __global__ void __launch_bounds__(1024) k_cholqr_factor(const double* __restrict
     const double r = rinv[j];
     for (int i = j + 1 + tid; i < n; i += nt) Lc[i + (size_t)j * n] *= r;
     __syncthreads();
-    const int rem = n - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      int i = j + 1 + e % rem, k = j + 1 + e / rem;
-      if (i >= k) Lc[i + (size_t)k * n] -= Lc[i + (size_t)j * n] * Lc[k + (size_t)j * n];
+    // trailing update of the lower triangle: warps step over columns k, lanes over rows i
+    for (int k = j + 1 + ty; k < n; k += nty) {
+      const double lkj = Lc[k + (size_t)j * n];
+      for (int i = k + tx; i < n; i += 32) Lc[i + (size_t)k * n] -= Lc[i + (size_t)j * n] * lkj;
     }
     __syncthreads();
   }
-  // column c of L^{-1}: y_c = 1/L_cc, y_i = -(sum_{k=c}^{i-1} L_ik y_k) / L_ii, stored as
-  // Yi[c + i n]; one warp per column, columns dealt round-robin
-  for (int c = warp; c < n; c += nwarps) {
-    if (lane == 0) Yi[c + (size_t)c * n] = rinv[c];
-    __syncwarp();
-    for (int i = c + 1; i < n; ++i) {
-      double s = 0.0;
-      for (int k = c + lane; k < i; k += 32) s = fma(Lc[i + (size_t)k * n], Yi[c + (size_t)k * n], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) Yi[c + (size_t)i * n] = -s * rinv[i];
-      __syncwarp();
+  if (SMEM) {
+    for (int e = tid; e < n * n + 2 * n; e += nt) work[e] = shc[e];
+  }
+  if (tid == 0) status[0] = 0;
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(32) k_tri_inv_col(const double* __restrict__ work, int n,
+                                                     double* __restrict__ U,
+                                                     const int* __restrict__ status) {
+  extern __shared__ double shl[];
+  if (status[0] != 0) return;  // the factorisation failed: U is not used
+  const int c = blockIdx.x, lane = threadIdx.x;
+  const double* Lg = work;
+  const double* Dv = work + (size_t)n * n;
+  const double* rinv = Dv + n;
+  const int m = n - c;                       // rows and columns c .. n-1
+  double* y = shl;                           // m
+  double* Ls = shl + m;                      // m x m (SMEM): Ls[(i-c) + (k-c) m] = L[i][k]
+  if (SMEM) {
+    for (int e = lane; e < m * m; e += 32) {
+      const int ii = e % m, kk = e / m;
+      Ls[e] = (ii >= kk) ? Lg[(c + ii) + (size_t)(c + kk) * n] : 0.0;
     }
   }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) U[e] = Dv[e % n] * Yi[e];
-  if (tid == 0) status[0] = 0;
+  if (lane == 0) y[0] = rinv[c];
+  __syncwarp();
+  for (int ii = 1; ii < m; ++ii) {
+    double s = 0.0;
+    for (int kk = lane; kk < ii; kk += 32) {
+      const double l = SMEM ? Ls[ii + (size_t)kk * m] : Lg[(c + ii) + (size_t)(c + kk) * n];
+      s = fma(l, y[kk], s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[ii] = -s * rinv[c + ii];
+    __syncwarp();
+  }
+  // U[c + i n] = D_c (L^{-1})[i][c] for i >= c, zero above
+  const double dc = Dv[c];
+  for (int i = lane; i < n; i += 32) U[c + (size_t)i * n] = (i >= c) ? dc * y[i - c] : 0.0;
 }
 
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream) {
-  size_t smem = (2 * (size_t)n * n + 2 * n) * sizeof(double);
+  size_t smem = ((size_t)n * n + 2 * n) * sizeof(double);
+  cudaError_t e;
   if (smem <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_cholqr_factor<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_cholqr_factor<true><<<1, 1024, smem, stream>>>(M, n, U, work, status);
+    k_cholesky<true><<<1, 1024, smem, stream>>>(M, n, work, status);
   } else {
-    k_cholqr_factor<false><<<1, 1024, 0, stream>>>(M, n, U, work, status);
+    k_cholesky<false><<<1, 1024, 0, stream>>>(M, n, work, status);
+  }
+  const size_t sm2 = ((size_t)n * n + n) * sizeof(double);
+  if (sm2 <= 200 * 1024) {
+    e = cudaFuncSetAttribute(k_tri_inv_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm2);
+    if (e != cudaSuccess) return e;
+    k_tri_inv_col<true><<<n, 32, sm2, stream>>>(work, n, U, status);
+  } else {
+    k_tri_inv_col<false><<<n, 32, (size_t)n * sizeof(double), stream>>>(work, n, U, status);
   }
   return cudaGetLastError();
 }
@@ -403,7 +435,7 @@ struct EigEps<double> {
   static __device__ double v() { return 2.220446049250313e-16; }
 };
 
-template <typename T, bool SMEM>
+template <typename T, bool SMEM, bool BISECT>
 __global__ void __launch_bounds__(1024) k_sym_eig(const double* __restrict__ Ain, int n,
                                                    double* __restrict__ theta,
                                                    double* __restrict__ Vout,
@@ -515,8 +547,125 @@ __global__ void __launch_bounds__(1024) k_sym_eig(const double* __restrict__ Ain
     }
     __syncthreads();
   }
-  // 3. implicit QL on (d, e), e[i] couples i and i+1
   const T eps = EigEps<T>::v();
+  if constexpr (BISECT) {
+    // 3'. eigenvalues of the tridiagonal T = (d, e) by bisection on Sturm counts, one thread
+    //     per eigenvalue (independent), eigenvectors of T by inverse iteration with the
+    //     LDL^T factors of T - lambda I, Gram-Schmidt inside clusters of close eigenvalues,
+    //     then Z <- Z Y. The serial chains are n steps long instead of QL's n sweeps.
+    T* Y = dsort + n;              // n x n, column i: eigenvector of T for lambda_i
+    T* Ls = Y + (size_t)n * n;     // n x n, column i: L factors of thread i
+    T* e2 = rc;                    // e_j^2
+    T* lam = rs;                   // eigenvalues, ascending
+    __shared__ T bnd[2];
+    for (int j = tid; j < n; j += nt) e2[j] = (j < n - 1) ? e[j] * e[j] : T(0);
+    if (tid == 0) {
+      T lo = d[0], hi = d[0];
+      for (int j = 0; j < n; ++j) {
+        const T r = (j > 0 ? fabs(e[j - 1]) : T(0)) + (j < n - 1 ? fabs(e[j]) : T(0));
+        lo = fmin(lo, d[j] - r);
+        hi = fmax(hi, d[j] + r);
+      }
+      bnd[0] = lo;
+      bnd[1] = hi;
+    }
+    __syncthreads();
+    const T glo = bnd[0], ghi = bnd[1];
+    const T tnorm = fmax(fabs(glo), fabs(ghi)) + T(1e-30);
+    const T piv = eps * tnorm;  // pivot guard of the Sturm and LDL^T recurrences
+    for (int i = tid; i < n; i += nt) {
+      T a = glo - piv, b = ghi + piv;  // count(a) <= i < count(b)
+      for (int it = 0; it < 64; ++it) {
+        const T x = T(0.5) * (a + b);
+        if (!(x > a && x < b)) break;
+        int cnt = 0;
+        T q = d[0] - x;
+        if (fabs(q) < piv) q = -piv;
+        cnt += (q < T(0));
+        for (int j = 1; j < n; ++j) {
+          q = d[j] - x - e2[j - 1] / q;
+          if (fabs(q) < piv) q = -piv;
+          cnt += (q < T(0));
+        }
+        if (cnt > i) b = x;
+        else a = x;
+      }
+      const T x = T(0.5) * (a + b);
+      lam[i] = x;
+      T* y = Y + (size_t)i * n;
+      T* L = Ls + (size_t)i * n;
+      // start vector differing per eigenvalue, so that a cluster's members start apart
+      for (int j = 0; j < n; ++j) {
+        const unsigned hsh = (unsigned)(j + 1) * 2654435761u ^ (unsigned)(i + 1) * 40503u;
+        y[j] = T(0.5) + (T)((hsh >> 8) & 0xffffu) * T(1.0 / 65536.0);
+      }
+      for (int rep = 0; rep < 3; ++rep) {
+        T Dp = d[0] - x;
+        if (fabs(Dp) < piv) Dp = piv;
+        T zp = y[0];
+        y[0] = zp / Dp;
+        for (int j = 1; j < n; ++j) {
+          const T l = e[j - 1] / Dp;
+          L[j] = l;
+          const T z = y[j] - l * zp;
+          T Dj = d[j] - x - l * e[j - 1];
+          if (fabs(Dj) < piv) Dj = piv;
+          y[j] = z / Dj;
+          zp = z;
+          Dp = Dj;
+        }
+        for (int j = n - 2; j >= 0; --j) y[j] -= L[j + 1] * y[j + 1];
+        T ss = T(0);
+        for (int j = 0; j < n; ++j) ss += y[j] * y[j];
+        const T sc = rsqrt(ss);
+        for (int j = 0; j < n; ++j) y[j] *= sc;
+      }
+    }
+    __syncthreads();
+    // clusters of eigenvalues closer than 1e-5 |T|: modified Gram-Schmidt, twice
+    int* cst = reinterpret_cast<int*>(Ls);
+    __shared__ int kmax;
+    if (tid == 0) {
+      int start = 0, km = 0;
+      for (int i = 0; i < n; ++i) {
+        if (i > 0 && lam[i] - lam[i - 1] > T(1e-5) * tnorm) start = i;
+        cst[i] = start;
+        km = max(km, i - start);
+      }
+      kmax = km;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 2; ++sweep)
+      for (int pos = 1; pos <= kmax; ++pos) {
+        for (int i = tid; i < n; i += nt) {
+          if (i - cst[i] != pos) continue;
+          T* y = Y + (size_t)i * n;
+          for (int jv = cst[i]; jv < i; ++jv) {
+            const T* u = Y + (size_t)jv * n;
+            T dot = T(0);
+            for (int j = 0; j < n; ++j) dot += u[j] * y[j];
+            for (int j = 0; j < n; ++j) y[j] -= dot * u[j];
+          }
+          T ss = T(0);
+          for (int j = 0; j < n; ++j) ss += y[j] * y[j];
+          const T sc = rsqrt(ss);
+          for (int j = 0; j < n; ++j) y[j] *= sc;
+        }
+        __syncthreads();
+      }
+    // V = Z Y (already ascending)
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, i = idx / n;
+      T acc = T(0);
+      for (int k = 0; k < n; ++k) acc += Z[r + (size_t)k * n] * Y[k + (size_t)i * n];
+      Vout[idx] = (double)acc;
+    }
+    if (theta)
+      for (int i = tid; i < n; i += nt) theta[i] = (double)lam[i];
+    if (tid == 0) status[0] = 1;
+    return;
+  }
+  // 3. implicit QL on (d, e), e[i] couples i and i+1
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
       if (tid == 0) {
@@ -868,14 +1017,23 @@ cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, 
   // 1. FP32 eigendecomposition of sym(A) -> V0 (FP64 copy of the FP32 vectors)
   size_t smem = (2 * n2 + 7 * (size_t)n) * sizeof(float);
   cudaError_t e;
-  if (smem <= 200 * 1024) {
-    e = cudaFuncSetAttribute(k_sym_eig<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+  const size_t smem_b = (4 * n2 + 7 * (size_t)n) * sizeof(float);
+  if (smem_b <= 200 * 1024) {
+    // bisection + inverse iteration on the tridiagonal (parallel over eigenvalues)
+    e = cudaFuncSetAttribute(k_sym_eig<float, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
     if (e != cudaSuccess) return e;
-    k_sym_eig<float, true><<<1, threads, smem, stream>>>(A, n, nullptr, V0, nullptr, status);
+    k_sym_eig<float, true, true><<<1, threads, smem_b, stream>>>(A, n, nullptr, V0, nullptr,
+                                                                 status);
+  } else if (smem <= 200 * 1024) {
+    e = cudaFuncSetAttribute(k_sym_eig<float, true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sym_eig<float, true, false><<<1, threads, smem, stream>>>(A, n, nullptr, V0, nullptr,
+                                                                status);
   } else {
-    k_sym_eig<float, false><<<1, threads, 0, stream>>>(A, n, nullptr, V0,
-                                                       reinterpret_cast<float*>(P), status);
+    k_sym_eig<float, false, false><<<1, threads, 0, stream>>>(A, n, nullptr, V0,
+                                                              reinterpret_cast<float*>(P), status);
   }
   // 2. orthonormalise to FP64 precision (Newton-Schulz), then refine in FP64
   double* Vc = V0;
