@@ -375,6 +375,7 @@ def run_ours(args):
     roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps)
 
     batched = None if args.no_batched else batched_measure(dev)
+    at_scale = None if args.no_at_scale else at_scale_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
@@ -400,6 +401,7 @@ def run_ours(args):
                 "unit": "applies/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches_timed),
         "batched": batched,
+        "at_scale": at_scale,
         "clocks": clocks.summary(),
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
@@ -486,6 +488,74 @@ def batched_measure(dev, reps=2):
             "launches_per_filter": degree + (degree & 1)}
 
 
+def at_scale_measure(dev, chunk=128):
+    """The 400-atom cluster with Kleinman-Bylander s and p projectors (R = 26, lmax 60, 96 radial
+    functions, d = 357216, 192 x 120 x 240 grid, 1600 projectors): one H.X on a chunk of 128
+    states in each precision (CUDA events, after a warm-up call), the split-BF16 and FP32
+    errors against the FP64 product, and the per-class device times of the mixed call."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t, kb_couplings, kb_projector_values_t
+    w = W.erf_cluster_400_kb()
+    idx = torch.device(dev).index or 0
+    t_setup = time.time()
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, idx)
+    xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+    atoms = w.atoms()
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, atoms).contiguous())
+    pcoef = torch.empty((4 * len(atoms), ctx.d), dtype=torch.float64, device=dev)
+    per = 16
+    for a0 in range(0, len(atoms), per):
+        cnt = min(per, len(atoms) - a0)
+        pg = kb_projector_values_t(xyz, atoms, rc=1.0, first=a0, count=cnt)
+        pg = pg.reshape(4 * cnt, ctx.n_r, ctx.n_theta, ctx.n_phi).contiguous()
+        cs.cs_forward_transform(ctx, pg, pcoef[4 * a0:4 * (a0 + cnt)])
+        del pg
+    cs.cs_set_projectors(ctx, pcoef, kb_couplings(len(atoms)))
+    del pcoef, xyz
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    X = torch.tensor(np.ascontiguousarray(W.gaussian_block(w.x_seed, ctx.d, chunk).T), device=dev)
+    out = {}
+    prods = {}
+    stream = torch.cuda.current_stream()
+    for name, prec in (("mixed", cs.CS_MIXED_BF16), ("fp32", cs.CS_FP32), ("fp64", cs.CS_FP64)):
+        Xp = X if prec == cs.CS_FP64 else X.float()
+        Y = torch.empty_like(Xp)
+        work = ctx.workspace(chunk, prec)
+        cs.cs_apply_H(ctx, Xp, Y, prec, work)  # warm
+        torch.cuda.synchronize()
+        if name == "mixed":
+            cs.cs_profile_begin(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_apply_H(ctx, Xp, Y, prec, work)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        entry = {"ms_per_apply_block": round(ms, 3), "applies_per_s": round(chunk / (ms / 1e3), 1)}
+        if name == "mixed":
+            pms, pn = cs.cs_profile_end(ctx)
+            names = cs.profile_class_names()
+            entry["class_ms"] = {names[i]: round(pms[i], 3) for i in range(len(names)) if pn[i]}
+        out[name] = entry
+        prods[name] = Y.double()
+        del work
+        ctx._ws.clear()
+        torch.cuda.empty_cache()
+    ref = prods["fp64"]
+    for name in ("mixed", "fp32"):
+        out[name]["rel_error_vs_fp64"] = float(torch.linalg.norm(prods[name] - ref) /
+                                               torch.linalg.norm(ref))
+    out["workload"] = ("erf400kb_l60_n96: 400 erf atoms + s,p projectors (1600), R=26, lmax=60, "
+                       f"96 radial fns/l, d={ctx.d}, grid 192x120x240, {chunk}-state chunk")
+    out["setup_s"] = round(t_setup, 1)
+    ctx.close()
+    return out
+
+
 def cpu_baseline(w, budget_s=15.0, cols=8):
     """The FP64 oracle as it stands, on the host cores: H.X on `cols` states of the same
     workload, repeated for about `budget_s` seconds. Returns applies/s (state columns per
@@ -562,6 +632,7 @@ def main():
     ap.add_argument("--dense-precision", default="df64", choices=["fp64", "df64"],
                     help="arithmetic of the Gram matrices and block rotations")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-at-scale", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -14,8 +14,9 @@
 //   D: G'[l,m][s]      += sum_p Theta_lm(t_jp) AP[m][p][parity of l+|m|][s]
 // B and C use 4 x 4 register tiles with a warp's lanes laid out 4 (rows) x 8 (columns) and
 // load the next step's operands while the current FMAs run; C groups the modes by parity
-// so one tile needs one cos and one sin input array. D accumulates each (l, m) output for all
-// 8 states in shared memory; its lanes share a mode, so the AP loads are broadcasts. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair]) from a
+// so one tile needs one cos and one sin input array. D accumulates the (l, m) outputs for all
+// 8 states in shared memory; an item is four l of one parity of one mode, its lanes share a
+// mode, so each AP load is a broadcast that feeds 32 FMAs. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair]) from a
 // table built at set-up, so staging them is a contiguous copy.
 #pragma once
 
@@ -29,6 +30,7 @@ namespace cs {
 constexpr int kGmThreads = 256;
 constexpr int kGmST = 8;     // states per CTA
 constexpr int kGmRC = 8;     // mirrored row pairs per chunk
+constexpr int kGmItems = 2;  // Legendre-quadrature items per thread (up to 512 per CTA)
 
 __host__ __device__ inline int gm_round4(int x) { return (x + 3) & ~3; }
 
@@ -136,16 +138,37 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
     Fz[(size_t)(M2 + 1) * NCp + i] = 0.f;
   }
   for (int i = tid; i < 4 * NC; i += kGmThreads) Wq[(size_t)(i / NC) * WS + (size_t)Qp * NC + i % NC] = 0.f;
+  // Legendre-quadrature items: (mode, parity of l - |m|, group of 4 such l); mstart[mi] is the
+  // first item of mode mi, the even-parity groups first
   if (tid == 0) {
     int o = 0;
     for (int mi = 0; mi < M2; ++mi) {
       mstart[mi] = o;
-      const int m = mi - lmax;
-      o += L - (m < 0 ? -m : m);
+      const int m = mi - lmax, cnt = L - (m < 0 ? -m : m);
+      o += ((cnt + 1) / 2 + 3) / 4 + (cnt / 2 + 3) / 4;
     }
     mstart[M2] = o;
   }
   __syncthreads();
+  const int nitems = mstart[M2];
+  int item_code[kGmItems];  // mi | parity << 8 | group << 9, or -1
+#pragma unroll
+  for (int u = 0; u < kGmItems; ++u) {
+    const int t = tid + u * kGmThreads;
+    item_code[u] = -1;
+    if (t < nitems) {
+      int lo = 0, hi = M2 - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mstart[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      const int m = lo - lmax, cnt = L - (m < 0 ? -m : m);
+      const int ge = ((cnt + 1) / 2 + 3) / 4;  // even-parity groups of this mode
+      const int r = t - mstart[lo];
+      item_code[u] = (r < ge) ? (lo | (r << 9)) : (lo | (1 << 8) | ((r - ge) << 9));
+    }
+  }
   const float* wvk = a.wv + (size_t)k * Nt * Np;
 
   for (int c0 = 0, ch = 0; c0 < NP; c0 += RC, ++ch) {
@@ -378,36 +401,52 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
       }
     }
     __syncthreads();
-    // ---- D: Legendre quadrature; item = (mode, l) in mode-major order, so that the lanes of a
-    //      warp share a mode and the AP loads are broadcasts
-    for (int t = tid; t < L2; t += kGmThreads) {
-      int lo = 0, hi = M2 - 1;  // last mode with mstart <= t
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (mstart[mid] <= t) lo = mid;
-        else hi = mid - 1;
+    // ---- D: Legendre quadrature. Item = four l of one parity (l - |m| = par, par + 2, ...) of
+    //      one mode: they read the same half of AP, so each broadcast AP load feeds 32 FMAs.
+#pragma unroll
+    for (int u = 0; u < kGmItems; ++u) {
+      const int code = item_code[u];
+      if (code < 0) continue;
+      const int mi = code & 0xff, par = (code >> 8) & 1, grp = code >> 9;
+      const int m = mi - lmax, am = m < 0 ? -m : m;
+      const int lbase = am + par + 8 * grp;  // l_v = lbase + 2 v
+      float acc[4][ST], pv[4][RC];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int l = lbase + 2 * v;
+        if (l <= lmax) {
+          const float* ga = Ga + (size_t)(l * l + l + m) * ST;
+          unpack4(ld4(ga), acc[v]);
+          unpack4(ld4(ga + 4), acc[v] + 4);
+          const float* pr = PT + (size_t)(theta_off(L, am) + l - am) * RC;
+          unpack4(ld4(pr), pv[v]);
+          unpack4(ld4(pr + 4), pv[v] + 4);
+        } else {
+#pragma unroll
+          for (int q = 0; q < ST; ++q) acc[v][q] = 0.f;
+#pragma unroll
+          for (int q = 0; q < RC; ++q) pv[v][q] = 0.f;
+        }
       }
-      const int mi = lo, m = mi - lmax, am = m < 0 ? -m : m;
-      const int l = am + (t - mstart[mi]);
-      float* ga = Ga + (size_t)(l * l + l + m) * ST;
-      float acc[ST];
-      unpack4(ld4(ga), acc);
-      unpack4(ld4(ga + 4), acc + 4);
-      const float* prow = PT + (size_t)(theta_off(L, am) + l - am) * RC;
-      float pv[8];
-      unpack4(ld4(prow), pv);
-      unpack4(ld4(prow + 4), pv + 4);
-      const float* arow = AP + (size_t)mi * RC * 2 * ST + (((l + am) & 1) ? ST : 0);
+      const float* arow = AP + (size_t)mi * RC * 2 * ST + (par ? ST : 0);
 #pragma unroll
       for (int pp = 0; pp < RC; ++pp) {
-        float av[8];
+        float av[ST];
         unpack4(ld4(arow + (size_t)pp * 2 * ST), av);
         unpack4(ld4(arow + (size_t)pp * 2 * ST + 4), av + 4);
 #pragma unroll
-        for (int s = 0; s < ST; ++s) acc[s] = fmaf(pv[pp], av[s], acc[s]);
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int q = 0; q < ST; ++q) acc[v][q] = fmaf(pv[v][pp], av[q], acc[v][q]);
       }
-      st4(ga, acc[0], acc[1], acc[2], acc[3]);
-      st4(ga + 4, acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int l = lbase + 2 * v;
+        if (l > lmax) break;
+        float* ga = Ga + (size_t)(l * l + l + m) * ST;
+        st4(ga, acc[v][0], acc[v][1], acc[v][2], acc[v][3]);
+        st4(ga + 4, acc[v][4], acc[v][5], acc[v][6], acc[v][7]);
+      }
     }
   }
   __syncthreads();
