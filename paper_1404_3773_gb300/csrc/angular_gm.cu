@@ -15,12 +15,7 @@ __global__ void __launch_bounds__(kGmThreads, 1) k_angular_gm(AngArgs<float> a, 
 
 cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, cudaStream_t stream) {
   const size_t smem = gm_smem_bytes(a.L, a.Q4, a.n_theta);
-  int items = 0;  // Legendre-quadrature items (see angular_gm_block)
-  for (int m = -(a.L - 1); m < a.L; ++m) {
-    const int cnt = a.L - (m < 0 ? -m : m);
-    items += ((cnt + 1) / 2 + 3) / 4 + (cnt / 2 + 3) / 4;
-  }
-  if (!a.theta_pairs || smem > 227 * 1024 || items > kGmItems * kGmThreads)
+  if (!a.theta_pairs || !gm_eligible(a.L, a.Q4, a.n_theta))
     return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_angular_gm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

@@ -70,6 +70,21 @@ __host__ __device__ inline size_t gm_smem_bytes(int L, int Q4, int n_theta) {
   return f * sizeof(float) + (size_t)(g.M2 + 1) * sizeof(int);
 }
 
+// number of Legendre-quadrature items of angular_gm_block (four same-parity l of one mode)
+__host__ __device__ inline int gm_items(int L) {
+  int items = 0;
+  for (int m = -(L - 1); m < L; ++m) {
+    const int cnt = L - (m < 0 ? -m : m);
+    items += ((cnt + 1) / 2 + 3) / 4 + (cnt / 2 + 3) / 4;
+  }
+  return items;
+}
+
+// whether the block fits: shared memory and the per-thread item slots
+__host__ __device__ inline bool gm_eligible(int L, int Q4, int n_theta) {
+  return gm_smem_bytes(L, Q4, n_theta) <= 227 * 1024 && gm_items(L) <= kGmItems * kGmThreads;
+}
+
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);

@@ -11,6 +11,8 @@
 //     the chunk's row pairs into a shared-memory accumulator.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cs_internal.h"
 #include "hx_kernels.cuh"
 #include "angular_rp.cuh"
@@ -37,8 +39,7 @@ static cudaError_t launch_rp(const AngArgs<T>& a, T* G, cudaStream_t stream) {
 }
 
 // Variants: (ST, RC) = 0:(8,8) 1:(8,4) 2:(4,8) 3:(4,4) 4:(2,8) 5:(2,4). With variant < 0 the
-// first of 2, 0, 1, 3, 4, 5 that fits in shared memory runs ((4,8) measured fastest on the
-// 46128-function workload in both precisions).
+// first variant of a measured preference order that fits in shared memory runs.
 template <typename T>
 cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream_t stream) {
   const int L = a.L, Q = a.Q4 + 1, rowlen = L * (L + 1) / 2;
@@ -47,10 +48,14 @@ cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream
     return rp_smem_elems(L, Q, rowlen, st_rc[v][0], st_rc[v][1]) * sizeof(T) <= 227 * 1024;
   };
   if (variant < 0) {
-    const int order[] = {2, 0, 1, 3, 4, 5};
-    for (int v : order)
-      if (fits(v)) {
-        variant = v;
+    // measured on the 46128-function workload: (4,8) fastest in FP32 and FP64, (2,8) in
+    // double-float (1.91 ms against 2.17 ms), whose per-thread state doubles the registers
+    const int order_sp[] = {2, 0, 1, 3, 4, 5};
+    const int order_df[] = {4, 2, 5, 3, 1, 0};
+    const int* order = std::is_same<T, df64>::value ? order_df : order_sp;
+    for (int i = 0; i < 6; ++i)
+      if (fits(order[i])) {
+        variant = order[i];
         break;
       }
     if (variant < 0) return cudaErrorInvalidConfiguration;

@@ -19,10 +19,12 @@
 #include <string>
 #include <vector>
 
+#include "angular_gm.cuh"
 #include "angular_rp.cuh"
 #include "cs_internal.h"
 #include "hx_device.cuh"
 #include "hx_kernels.cuh"
+#include "radial_gemm.cuh"
 
 namespace cs {
 namespace {
@@ -41,6 +43,8 @@ struct BCluster {
   long long ld, ld_alt;
   const float* coef;       // [step][3]: cA, cB, cshift
   int n_items[3];
+  int rm[2];               // rows per thread of the radial tiles (synthesis, analysis)
+  int ang_gm;              // 1: register-blocked angular block (8 states), 0: row-pair block
 };
 
 struct BItem {
@@ -94,17 +98,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_step(const BCluster* __
       const long long ld_in = odd ? c.ld : c.ld_alt;
       const long long ld_out = odd ? c.ld_alt : c.ld;
       if (it.stage == 0) {
-        auto As = reinterpret_cast<float(*)[RBM + 1]>(smem);
-        auto Bs = reinterpret_cast<float(*)[RBN + 1]>(smem + sizeof(float) * RBK * (RBM + 1));
         int l, c0;
-        locate_l_tile(it.x, c.ang.S, l, c0);
-        radial_synth_tile<float>(in, ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S, l, c0,
-                                 it.y * RBM, As, Bs);
+        rg_locate(it.x, c.ang.S, l, c0);
+        radial_gemm_tile_rm<0>(c.rm[0], in, ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r,
+                               c.ang.S, Epilogue<float>(), l, c0, it.y * 16 * c.rm[0],
+                               reinterpret_cast<float*>(smem));
       } else if (it.stage == 1) {
-        angular_rp_block<float, ST, RC>(c.ang, c.G, it.y, it.x * ST, smem);
+        if (c.ang_gm) angular_gm_block(c.ang, c.G, it.y, it.x * kGmST, smem);
+        else angular_rp_block<float, ST, RC>(c.ang, c.G, it.y, it.x * ST, smem);
       } else {
-        auto As = reinterpret_cast<float(*)[RBM + 1]>(smem);
-        auto Bs = reinterpret_cast<float(*)[RBN + 1]>(smem + sizeof(float) * RBK * (RBM + 1));
         Epilogue<float> ep;
         ep.mode = EP_CHEB;
         ep.X = in;
@@ -117,9 +119,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_step(const BCluster* __
         ep.cB = c.coef[3 * (step - 1) + 1];
         ep.cshift = c.coef[3 * (step - 1) + 2];
         int l, c0;
-        locate_l_tile(it.x, c.ang.S, l, c0);
-        radial_anal_tile<float>(c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S, ep, l, c0,
-                                it.y * RBM, As, Bs);
+        rg_locate(it.x, c.ang.S, l, c0);
+        radial_gemm_tile_rm<1>(c.rm[1], nullptr, 0, c.G, c.rad, c.ang.L, c.N, c.ang.n_r,
+                               c.ang.S, ep, l, c0, it.y * 16 * c.rm[1],
+                               reinterpret_cast<float*>(smem));
       }
     }
     __threadfence();  // this thread's results visible device-wide before the count
@@ -153,11 +156,14 @@ constexpr int kNumVariants = 3;
 static_assert(8 * 32 == kBatchThreads, "batch variants assume 8 row pairs per chunk");
 
 size_t variant_smem(const std::vector<cs_ctx*>& ctxs, int v) {
-  size_t m = 2 * sizeof(float) * RBK * (RBM + 1);
+  size_t m = sizeof(float) * rg_smem_floats<8>();
   for (cs_ctx* c : ctxs) {
     const HostTables& H = c->host;
     const int L = H.L, Q = c->Q4 + 1, rowlen = L * (L + 1) / 2;
-    m = std::max(m, rp_smem_elems(L, Q, rowlen, kVariants[v][0], kVariants[v][1]) * sizeof(float));
+    if (gm_eligible(L, c->Q4, H.n_theta))
+      m = std::max(m, gm_smem_bytes(L, c->Q4, H.n_theta));
+    else
+      m = std::max(m, rp_smem_elems(L, Q, rowlen, kVariants[v][0], kVariants[v][1]) * sizeof(float));
   }
   return m;
 }
@@ -236,15 +242,18 @@ cs_status build_items(cs_batch* b, int v) {
       const int S = b->n_s[ci];
       int cnt = 0;
       if (stage == 0 || stage == 2) {
-        const int ct = col_tiles(H.L, S);
-        const int rt = (stage == 0) ? (H.n_r + RBM - 1) / RBM : (H.N + RBM - 1) / RBM;
+        const int ct = rg_col_tiles(H.L, S);
+        const int M = (stage == 0) ? H.n_r : H.N;
+        const int rows = 16 * rg_rm(M);
+        const int rt = (M + rows - 1) / rows;
         for (int y = 0; y < rt; ++y)
           for (int x = 0; x < ct; ++x) {
             items.push_back({ci, stage, x, y});
             ++cnt;
           }
       } else {
-        const int stiles = (S + ST - 1) / ST;
+        const int st = b->h_cl[ci].ang_gm ? kGmST : ST;
+        const int stiles = (S + st - 1) / st;
         for (int k = 0; k < H.n_r; ++k)
           for (int x = 0; x < stiles; ++x) {
             items.push_back({ci, 1, x, k});
@@ -373,8 +382,11 @@ cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree
     const HostTables& H = c->host;
     BCluster bc{};
     bc.ang = AngArgs<float>{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s[i], c->d32.theta,
-                            c->d32.trig, c->d32.wv, c->d32.wkj};
+                            c->d32.trig, c->d32.wv, c->d32.wkj, c->d32.theta_pairs};
+    bc.ang_gm = gm_eligible(H.L, c->Q4, H.n_theta) ? 1 : 0;
     bc.N = H.N;
+    bc.rm[0] = rg_rm(H.n_r);
+    bc.rm[1] = rg_rm(H.N);
     bc.rad = c->d32.rad;
     bc.half_lambda = c->d32.half_lambda;
     bc.ld_alt = H.d;

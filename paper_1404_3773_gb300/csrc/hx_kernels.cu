@@ -14,11 +14,13 @@
 
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 #include "cs_internal.h"
 #include "df64.cuh"
 #include "hx_kernels.cuh"
 #include "hx_device.cuh"
+#include "radial_gemm.cuh"
 
 namespace cs {
 
@@ -44,6 +46,45 @@ __global__ void __launch_bounds__(256) k_radial_anal(const T* __restrict__ G,
   int l, c0;
   locate_l_tile(blockIdx.x, S, l, c0);
   radial_anal_tile<T>(G, rad, L, N, n_r, S, ep, l, c0, blockIdx.y * RBM, As, Bs);
+}
+
+// FP32: register-blocked tiles (radial_gemm.cuh), RM rows per thread chosen from M
+template <int MODE, int RM>
+__global__ void __launch_bounds__(kRgThreads) k_radial_gemm(const float* __restrict__ X,
+                                                             long long ldx, float* __restrict__ G,
+                                                             const float* __restrict__ rad, int L,
+                                                             int N, int n_r, int S,
+                                                             Epilogue<float> ep) {
+  __shared__ __align__(16) float sm[rg_smem_floats<RM>()];
+  int l, c0;
+  rg_locate(blockIdx.x, S, l, c0);
+  radial_gemm_tile<MODE, RM>(X, ldx, G, rad, L, N, n_r, S, ep, l, c0, blockIdx.y * 16 * RM, sm);
+}
+
+template <int MODE>
+static cudaError_t launch_radial_gemm(const float* X, long long ldx, float* G, const float* rad,
+                                      int L, int N, int n_r, int S, const Epilogue<float>& ep,
+                                      cudaStream_t stream) {
+  const int M = (MODE == 0) ? n_r : N;
+  const int rm = rg_rm(M);
+  dim3 grid(rg_col_tiles(L, S), (M + 16 * rm - 1) / (16 * rm));
+#define CS_RG_CASE(R)                                                                       \
+  case R:                                                                                   \
+    k_radial_gemm<MODE, R><<<grid, kRgThreads, 0, stream>>>(X, ldx, G, rad, L, N, n_r, S, ep); \
+    break;
+  switch (rm) {
+    CS_RG_CASE(1)
+    CS_RG_CASE(2)
+    CS_RG_CASE(3)
+    CS_RG_CASE(4)
+    CS_RG_CASE(5)
+    CS_RG_CASE(6)
+    CS_RG_CASE(7)
+    default:
+      k_radial_gemm<MODE, 8><<<grid, kRgThreads, 0, stream>>>(X, ldx, G, rad, L, N, n_r, S, ep);
+  }
+#undef CS_RG_CASE
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ angular kernel
@@ -326,6 +367,8 @@ static int radial_col_tiles(int L, int S) {
 template <typename T>
 cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,
                                 int n_r, int S, cudaStream_t stream) {
+  if constexpr (std::is_same<T, float>::value)
+    return launch_radial_gemm<0>(X, ld, G, rad, L, N, n_r, S, Epilogue<float>(), stream);
   dim3 grid(radial_col_tiles(L, S), (n_r + RBM - 1) / RBM);
   k_radial_synth<T><<<grid, 256, 0, stream>>>(X, ld, G, rad, L, N, n_r, S);
   return cudaGetLastError();
@@ -334,6 +377,8 @@ cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, in
 template <typename T>
 cudaError_t launch_radial_anal(const T* G, const T* rad, int L, int N, int n_r, int S,
                                const Epilogue<T>& ep, cudaStream_t stream) {
+  if constexpr (std::is_same<T, float>::value)
+    return launch_radial_gemm<1>(nullptr, 0, const_cast<float*>(G), rad, L, N, n_r, S, ep, stream);
   dim3 grid(radial_col_tiles(L, S), (N + RBM - 1) / RBM);
   k_radial_anal<T><<<grid, 256, 0, stream>>>(G, rad, L, N, n_r, S, ep);
   return cudaGetLastError();

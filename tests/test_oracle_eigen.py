@@ -134,3 +134,18 @@ def test_planted_wrong_sigma_sign_breaks_filter_closed_form():
     gain = _cheb_T(5, (lam - c) / e) / _cheb_T(5, np.array([(a0 - c) / e]))[0]
     ref = Q @ (gain[:, None] * (Q.T @ X))
     assert np.max(np.abs(Y - ref)) > 1e-3 * np.abs(ref).max()
+
+
+def test_chfsi_free_particle_levels_and_multiplicities():
+    """V = 0: the ChFSI eigenvalues are the free-particle levels 1/2 (z_ln/R)^2, each l level
+    (2l+1)-fold degenerate (Sec. 2.2.1), taken from the Bessel zeros in closed form order."""
+    from oracle.basis import Basis
+    from oracle.hamiltonian import Hamiltonian
+    b = Basis(6.0, 3, 6, n_r=20, n_theta=8, n_phi=16)
+    H = Hamiltonian(b, np.zeros(b.n_grid))
+    levels = sorted(0.5 * (b.z[l, n] / b.R) ** 2 for l in range(b.L) for n in range(b.N)
+                    for _ in range(2 * l + 1))
+    # ten wanted levels: the next level is the sevenfold l = 3 one, wholly inside the block
+    X0 = W.gaussian_block(61, b.d, 17)
+    theta, X, resid, it = eigen.chfsi(H.apply, X0, 10, 10, W.gaussian(62, b.d), tol=1e-10)
+    assert np.max(np.abs(theta[:10] - np.array(levels[:10]))) < 1e-10

@@ -168,3 +168,40 @@ def test_planted_reversed_theta_nodes_break_scipy_harmonics():
     ours = b.theta[m][:, l - m][:, None] * b.phi_fn[:, m + b.lmax][None, :]
     ref = math.sqrt(2.0) * (sp.sph_harm_y(l, m, T, P) * (-1) ** m).real
     assert np.max(np.abs(ours - ref)) > 0.1
+
+
+def test_hydrogen_like_l0_levels_decrease_toward_exact():
+    """V = -1/r in the l = 0 subspace (R = 20, resolved radial rule): the two lowest levels
+    are variational upper bounds that decrease monotonically with the number of radial
+    functions toward the hydrogen levels -1/2 and -1/8 Ha (slow, polynomial convergence: the
+    cusp at the origin)."""
+    from oracle.basis import Basis
+    prev = None
+    for N in (8, 16, 24, 32):
+        b = Basis(20.0, 0, N, n_r=4 * N + 16, n_theta=2, n_phi=2)
+        r = np.linalg.norm(b.points(), axis=1)
+        lam = np.linalg.eigvalsh(Hamiltonian(b, -1.0 / r).dense())[:2]
+        assert lam[0] > -0.5 and lam[1] > -0.125
+        if prev is not None:
+            assert lam[0] < prev[0] and lam[1] < prev[1]
+        prev = lam
+    assert prev[0] < -0.49 and prev[1] < -0.123
+
+
+def test_displaced_atom_converges_to_centred_atom():
+    """Translation: one erf pseudo-atom (Z = 4, rc = 0.8) displaced 1.5 bohr along z in a ball
+    of radius 10. Its lowest level is an upper bound that approaches, monotonically in lmax,
+    the level of the same atom at the centre (converged in N with l = 0 alone), to 1e-4 Ha at
+    lmax 10."""
+    from oracle.basis import Basis
+
+    def lowest(lmax, N, shift):
+        b = Basis(10.0, lmax, N, n_r=2 * N + 24, n_theta=2 * lmax + 2, n_phi=4 * lmax + 4)
+        v = W.erf_cluster_potential(b.points(), np.array([[0.0, 0.0, shift]]), 4.0, 0.8)
+        return np.linalg.eigvalsh(Hamiltonian(b, v).dense())[0]
+
+    centre = lowest(0, 32, 0.0)
+    assert abs(centre - lowest(0, 24, 0.0)) < 1e-6  # converged in N
+    shifted = [lowest(lmax, 16, 1.5) for lmax in (6, 8, 10)]
+    assert shifted[0] > shifted[1] > shifted[2] > centre - 1e-9
+    assert shifted[2] - centre < 1e-4
