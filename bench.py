@@ -445,6 +445,7 @@ def batched_measure(dev, reps=2):
     a, b, a0 = (list(t) for t in zip(*bounds))
     batch = cs.cs_batch_create(ctxs, [w.n_s for w in ws], degree)
     variant, tune_ms = cs.cs_batch_tune(batch, Xs, a, b, a0)
+    variant_ms = cs.cs_batch_tune_times(batch)
     nbytes = max(cs.cs_workspace_bytes(c, w.n_s, cs.CS_FP32) for c, w in zip(ctxs, ws))
     work_seq = torch.empty(nbytes, dtype=torch.uint8, device=dev)  # shared, calls are serial
     stream = torch.cuda.current_stream()
@@ -452,6 +453,10 @@ def batched_measure(dev, reps=2):
     Y = [X.clone() for X in Xs]
     cs.cs_batch_cheb_filter(batch, Y, a, b, a0)  # warm
     torch.cuda.synchronize()
+    n0 = cs.cs_launch_count(ctxs[0])
+    cs.cs_batch_cheb_filter(batch, Y, a, b, a0)
+    torch.cuda.synchronize()
+    launches_per_filter = cs.cs_launch_count(ctxs[0]) - n0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
@@ -484,8 +489,10 @@ def batched_measure(dev, reps=2):
             "sequential_applies_per_s": round(cols / (t_seq / 1e3), 1),
             "speedup_vs_sequential": round(t_seq / t_batch, 3),
             "filter_ms": round(t_batch, 3), "sequential_filter_ms": round(t_seq, 3),
-            "tuned_variant": variant, "bitwise_equal_to_sequential": bool(same),
-            "launches_per_filter": degree + (degree & 1)}
+            "tuned_variant": cs.BATCH_VARIANTS[variant],
+            "tune_filter_ms": {k: round(v, 3) for k, v in variant_ms.items()},
+            "bitwise_equal_to_sequential": bool(same),
+            "launches_per_filter": launches_per_filter}
 
 
 def at_scale_measure(dev, chunk=128):

@@ -265,12 +265,20 @@ cs_status cs_batch_workspace_bytes(const cs_batch* batch, size_t* bytes);
 cs_status cs_batch_cheb_filter(cs_batch* batch, float* const* X, const long long* ld,
                                const double* a, const double* b, const double* a0, void* work,
                                cs_stream stream);
-/* Autotuner: times one filter per angular tile variant (states per CTA x row pairs per
- * chunk) on these blocks and keeps the fastest; X is restored afterwards. Synchronising.
- * *chosen = variant index, *best_ms = its filter time. */
+/* Autotuner: times one filter per variant (launch form x angular tile, see
+ * cs_batch_tune_times) on these blocks and keeps the fastest; X is restored afterwards.
+ * Synchronising. *chosen = variant index, *best_ms = its filter time. */
 cs_status cs_batch_tune(cs_batch* batch, float* const* X, const long long* ld, const double* a,
                         const double* b, const double* a0, void* work, cs_stream stream,
                         int* chosen, float* best_ms);
+
+/* Filter time (ms) of each variant in the last cs_batch_tune (-1 where not timed), for n
+ * variants: 0 .. 2 one persistent launch per Chebyshev step with row-pair angular tiles of 4, 8
+ * and 2 states; 3 one launch per (stage, tile shape) group of items. */
+cs_status cs_batch_tune_times(const cs_batch* batch, float* ms, int n);
+/* Selects a variant (as numbered above) without timing; the next filter call recaptures its
+ * graph. CS_ERR_ARG for an unknown variant or one that does not fit in shared memory. */
+cs_status cs_batch_set_variant(cs_batch* batch, int variant);
 const char* cs_batch_last_error(const cs_batch* batch);
 
 /* Device error word of the context (synchronising): 0 if no kernel reported a problem, else

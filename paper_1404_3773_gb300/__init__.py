@@ -26,7 +26,8 @@ __all__ = [
     "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
     "cs_set_rr_precision", "cs_set_dense_precision",
     "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
-    "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_last_error",
+    "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
+    "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
 ]
 
@@ -90,6 +91,8 @@ _SIGS = {
     "cs_batch_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_batch_cheb_filter": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_ll), _dp, _dp, _dp,
                                   _vp, _vp]),
+    "cs_batch_tune_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
+    "cs_batch_set_variant": (_i, [_vp, _i]),
     "cs_batch_tune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_ll), _dp, _dp, _dp, _vp, _vp,
                            ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
@@ -483,6 +486,22 @@ def cs_batch_tune(batch: Batch, Xs, a, b, a0, work=None, stream=None):
                                    _stream_ptr(stream), ctypes.byref(ch), ctypes.byref(ms)))
     return ch.value, ms.value
 
+
+
+BATCH_VARIANTS = ("persistent_rp4", "persistent_rp8", "persistent_rp2", "staged")
+
+
+def cs_batch_set_variant(batch: Batch, variant):
+    """Select a batch variant by index or by name (BATCH_VARIANTS)."""
+    v = BATCH_VARIANTS.index(variant) if isinstance(variant, str) else int(variant)
+    batch.check(_lib.cs_batch_set_variant(batch.handle, v))
+
+
+def cs_batch_tune_times(batch: Batch):
+    """Filter time (ms) of each variant in the last tune (BATCH_VARIANTS order; -1: not run)."""
+    ms = (ctypes.c_float * len(BATCH_VARIANTS))()
+    batch.check(_lib.cs_batch_tune_times(batch.handle, ms, len(BATCH_VARIANTS)))
+    return dict(zip(BATCH_VARIANTS, list(ms)))
 
 def cs_batch_last_error(batch: Batch) -> str:
     return _lib.cs_batch_last_error(batch.handle).decode()

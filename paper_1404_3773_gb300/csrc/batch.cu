@@ -51,6 +51,32 @@ struct BItem {
   int cluster, stage, x, y;
 };
 
+// buffers of Chebyshev step `step` (1-based): step 1 reads X and writes Yalt, then they alternate
+struct StepBufs {
+  float* in;
+  float* out;
+  long long ld_in, ld_out;
+};
+__device__ __forceinline__ StepBufs step_bufs(const BCluster& c, int step) {
+  const bool odd = (step & 1) != 0;
+  return {odd ? c.X : c.Yalt, odd ? c.Yalt : c.X, odd ? c.ld : c.ld_alt, odd ? c.ld_alt : c.ld};
+}
+__device__ __forceinline__ Epilogue<float> cheb_epilogue(const BCluster& c, int step,
+                                                         const StepBufs& b) {
+  Epilogue<float> ep;
+  ep.mode = EP_CHEB;
+  ep.X = b.in;
+  ep.ld = b.ld_in;
+  ep.out = b.out;
+  ep.ld_out = b.ld_out;
+  ep.Yprev = (step == 1) ? nullptr : b.out;
+  ep.half_lambda = c.half_lambda;
+  ep.cA = c.coef[3 * (step - 1) + 0];
+  ep.cB = c.coef[3 * (step - 1) + 1];
+  ep.cshift = c.coef[3 * (step - 1) + 2];
+  return ep;
+}
+
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
 template <int ST, int RC>
@@ -91,33 +117,18 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_step(const BCluster* __
     }
     __syncthreads();
     if (ok_sh) {
-      // buffers of this step: step 1 reads X, writes Yalt; then they alternate
-      const bool odd = (step & 1) != 0;
-      float* in = odd ? c.X : c.Yalt;
-      float* out = odd ? c.Yalt : c.X;
-      const long long ld_in = odd ? c.ld : c.ld_alt;
-      const long long ld_out = odd ? c.ld_alt : c.ld;
+      const StepBufs sb = step_bufs(c, step);
       if (it.stage == 0) {
         int l, c0;
         rg_locate(it.x, c.ang.S, l, c0);
-        radial_gemm_tile_rm<0>(c.rm[0], in, ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r,
+        radial_gemm_tile_rm<0>(c.rm[0], sb.in, sb.ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r,
                                c.ang.S, Epilogue<float>(), l, c0, it.y * 16 * c.rm[0],
                                reinterpret_cast<float*>(smem));
       } else if (it.stage == 1) {
         if (c.ang_gm) angular_gm_block(c.ang, c.G, it.y, it.x * kGmST, smem);
         else angular_rp_block<float, ST, RC>(c.ang, c.G, it.y, it.x * ST, smem);
       } else {
-        Epilogue<float> ep;
-        ep.mode = EP_CHEB;
-        ep.X = in;
-        ep.ld = ld_in;
-        ep.out = out;
-        ep.ld_out = ld_out;
-        ep.Yprev = (step == 1) ? nullptr : out;
-        ep.half_lambda = c.half_lambda;
-        ep.cA = c.coef[3 * (step - 1) + 0];
-        ep.cB = c.coef[3 * (step - 1) + 1];
-        ep.cshift = c.coef[3 * (step - 1) + 2];
+        const Epilogue<float> ep = cheb_epilogue(c, step, sb);
         int l, c0;
         rg_locate(it.x, c.ang.S, l, c0);
         radial_gemm_tile_rm<1>(c.rm[1], nullptr, 0, c.G, c.rad, c.ang.L, c.N, c.ang.n_r,
@@ -129,6 +140,42 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_step(const BCluster* __
     __syncthreads();
     if (tid == 0) atomicAdd(done + 3 * it.cluster + it.stage, 1);
   }
+}
+
+// ---- staged form: one launch per (stage, tile shape) group of items, no waits inside a launch
+template <int MODE, int RM>
+__global__ void __launch_bounds__(kBatchThreads) k_bstage_radial(const BCluster* __restrict__ cl,
+                                                                  const BItem* __restrict__ items,
+                                                                  int step) {
+  __shared__ __align__(16) float sm[rg_smem_floats<RM>()];
+  const BItem it = items[blockIdx.x];
+  const BCluster& c = cl[it.cluster];
+  const StepBufs sb = step_bufs(c, step);
+  int l, c0;
+  rg_locate(it.x, c.ang.S, l, c0);
+  if (MODE == 0)
+    radial_gemm_tile<0, RM>(sb.in, sb.ld_in, c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S,
+                            Epilogue<float>(), l, c0, it.y * 16 * RM, sm);
+  else
+    radial_gemm_tile<1, RM>(nullptr, 0, c.G, c.rad, c.ang.L, c.N, c.ang.n_r, c.ang.S,
+                            cheb_epilogue(c, step, sb), l, c0, it.y * 16 * RM, sm);
+}
+
+__global__ void __launch_bounds__(kGmThreads, 1) k_bstage_ang_gm(const BCluster* __restrict__ cl,
+                                                                  const BItem* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BItem it = items[blockIdx.x];
+  const BCluster& c = cl[it.cluster];
+  angular_gm_block(c.ang, c.G, it.y, it.x * kGmST, smem);
+}
+
+template <int ST, int RC>
+__global__ void __launch_bounds__(RC * 32) k_bstage_ang_rp(const BCluster* __restrict__ cl,
+                                                            const BItem* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BItem it = items[blockIdx.x];
+  const BCluster& c = cl[it.cluster];
+  angular_rp_block<float, ST, RC>(c.ang, c.G, it.y, it.x * ST, smem);
 }
 
 // copies Yalt -> X for every cluster (after an odd number of steps the result sits in Yalt)
@@ -151,11 +198,21 @@ int col_tiles(int L, int S) {
 
 // angular tile variants (states per CTA, row pairs per chunk); the row-pair block needs
 // exactly RC x 32 threads, so every variant here has RC x 32 == kBatchThreads
-const int kVariants[][2] = {{4, 8}, {8, 8}, {2, 8}};
-constexpr int kNumVariants = 3;
+// variants 0 .. 2: one persistent launch per step, row-pair tiles of ST states; variant 3
+// (kStaged): one launch per (stage, tile shape) group, row-pair tiles of 4 states
+const int kVariants[][2] = {{4, 8}, {8, 8}, {2, 8}, {4, 8}};
+constexpr int kNumVariants = 4;
+constexpr int kStaged = 3;
 static_assert(8 * 32 == kBatchThreads, "batch variants assume 8 row pairs per chunk");
 
+// item groups of the staged form: kind 0 radial synthesis, 1 angular (register-blocked),
+// 2 angular (row-pair), 3 radial analysis; rm = rows per thread of a radial group
+struct BGroup {
+  int kind, rm, begin, count;
+};
+
 size_t variant_smem(const std::vector<cs_ctx*>& ctxs, int v) {
+  if (v == kStaged) return 0;  // each staged launch sizes its own shared memory
   size_t m = sizeof(float) * rg_smem_floats<8>();
   for (cs_ctx* c : ctxs) {
     const HostTables& H = c->host;
@@ -191,6 +248,10 @@ struct cs_batch {
   cudaGraphExec_t graph = nullptr;
   std::vector<void*> graph_key;  // pointers the graph was captured with
   int graph_variant = -1;
+  std::vector<BGroup> groups;     // staged launch groups, in launch order
+  size_t rp_smem = 0;             // shared memory of the staged row-pair launch
+  size_t gm_smem = 0;             // shared memory of the staged register-blocked launch
+  float tune_ms[kNumVariants] = {-1.f, -1.f, -1.f, -1.f};
   std::string err;
 };
 
@@ -231,37 +292,107 @@ cudaError_t launch_variant_step(cs_batch* b, int v, int step, cudaStream_t st) {
   }
 }
 
+template <int MODE>
+cudaError_t launch_stage_radial(const BCluster* cl, const BItem* items, int count, int rm, int step,
+                                cudaStream_t st) {
+  switch (rm) {
+    case 1: k_bstage_radial<MODE, 1><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 2: k_bstage_radial<MODE, 2><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 3: k_bstage_radial<MODE, 3><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 4: k_bstage_radial<MODE, 4><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 5: k_bstage_radial<MODE, 5><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 6: k_bstage_radial<MODE, 6><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    case 7: k_bstage_radial<MODE, 7><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+    default: k_bstage_radial<MODE, 8><<<count, kBatchThreads, 0, st>>>(cl, items, step); break;
+  }
+  return cudaGetLastError();
+}
+
+// one Chebyshev step of the staged form: the groups in order (synthesis, angular, analysis)
+cudaError_t launch_staged_step(cs_batch* b, int step, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (const BGroup& g : b->groups) {
+    const BItem* items = b->d_items + g.begin;
+    switch (g.kind) {
+      case 0: e = launch_stage_radial<0>(b->d_cl, items, g.count, g.rm, step, st); break;
+      case 3: e = launch_stage_radial<1>(b->d_cl, items, g.count, g.rm, step, st); break;
+      case 1:
+        e = cudaFuncSetAttribute(k_bstage_ang_gm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->gm_smem);
+        if (e == cudaSuccess) {
+          k_bstage_ang_gm<<<g.count, kGmThreads, b->gm_smem, st>>>(b->d_cl, items);
+          e = cudaGetLastError();
+        }
+        break;
+      default:
+        e = cudaFuncSetAttribute(k_bstage_ang_rp<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->rp_smem);
+        if (e == cudaSuccess) {
+          k_bstage_ang_rp<4, 8><<<g.count, 8 * 32, b->rp_smem, st>>>(b->d_cl, items);
+          e = cudaGetLastError();
+        }
+        break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return e;
+}
+
 // builds the item list for a variant (the angular item count depends on ST)
 cs_status build_items(cs_batch* b, int v) {
   const int ST = kVariants[v][0];
   std::vector<BItem> items;
   const int nc = (int)b->ctxs.size();
-  for (int stage = 0; stage < 3; ++stage)
-    for (int ci = 0; ci < nc; ++ci) {
-      const HostTables& H = b->ctxs[ci]->host;
-      const int S = b->n_s[ci];
-      int cnt = 0;
-      if (stage == 0 || stage == 2) {
+  b->groups.clear();
+  b->rp_smem = 0;
+  b->gm_smem = 0;
+  for (int ci = 0; ci < nc; ++ci)
+    for (int st = 0; st < 3; ++st) b->h_cl[ci].n_items[st] = 0;
+  // stage-major order (the persistent launch's progress guarantee), grouped by tile shape
+  auto add_group = [&](int kind, int rm, int begin) {
+    const int cnt = (int)items.size() - begin;
+    if (cnt > 0) b->groups.push_back({kind, rm, begin, cnt});
+  };
+  for (int stage = 0; stage < 3; stage += 2) {
+    if (stage == 2) {
+      // angular items between the two radial stages
+      for (int gm = 1; gm >= 0; --gm) {
+        const int begin = (int)items.size();
+        for (int ci = 0; ci < nc; ++ci) {
+          if (b->h_cl[ci].ang_gm != gm) continue;
+          const HostTables& H = b->ctxs[ci]->host;
+          const int S = b->n_s[ci];
+          const int st = gm ? kGmST : ST;
+          const int stiles = (S + st - 1) / st;
+          for (int k = 0; k < H.n_r; ++k)
+            for (int x = 0; x < stiles; ++x) items.push_back({ci, 1, x, k});
+          b->h_cl[ci].n_items[1] += H.n_r * stiles;
+          if (gm) {
+            b->gm_smem = std::max(b->gm_smem, gm_smem_bytes(H.L, b->ctxs[ci]->Q4, H.n_theta));
+          } else {
+            const int L = H.L, Q = b->ctxs[ci]->Q4 + 1, rowlen = L * (L + 1) / 2;
+            b->rp_smem = std::max(b->rp_smem, rp_smem_elems(L, Q, rowlen, ST, 8) * sizeof(float));
+          }
+        }
+        add_group(gm ? 1 : 2, 0, begin);
+      }
+    }
+    for (int rm = 1; rm <= 8; ++rm) {
+      const int begin = (int)items.size();
+      for (int ci = 0; ci < nc; ++ci) {
+        if (b->h_cl[ci].rm[stage == 0 ? 0 : 1] != rm) continue;
+        const HostTables& H = b->ctxs[ci]->host;
+        const int S = b->n_s[ci];
         const int ct = rg_col_tiles(H.L, S);
         const int M = (stage == 0) ? H.n_r : H.N;
-        const int rows = 16 * rg_rm(M);
-        const int rt = (M + rows - 1) / rows;
+        const int rt = (M + 16 * rm - 1) / (16 * rm);
         for (int y = 0; y < rt; ++y)
-          for (int x = 0; x < ct; ++x) {
-            items.push_back({ci, stage, x, y});
-            ++cnt;
-          }
-      } else {
-        const int st = b->h_cl[ci].ang_gm ? kGmST : ST;
-        const int stiles = (S + st - 1) / st;
-        for (int k = 0; k < H.n_r; ++k)
-          for (int x = 0; x < stiles; ++x) {
-            items.push_back({ci, 1, x, k});
-            ++cnt;
-          }
+          for (int x = 0; x < ct; ++x) items.push_back({ci, stage, x, y});
+        b->h_cl[ci].n_items[stage] += rt * ct;
       }
-      b->h_cl[ci].n_items[stage] = cnt;
+      add_group(stage == 0 ? 0 : 3, rm, begin);
     }
+  }
   // a captured graph refers to the old list: drop it before the list is replaced
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
@@ -330,8 +461,12 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     const size_t ctr_bytes = (1 + 3 * (size_t)nc) * sizeof(int);
     for (int step = 1; step <= b->degree && e == cudaSuccess; ++step) {
-      e = cudaMemsetAsync(b->d_ctr, 0, ctr_bytes, cap);
-      if (e == cudaSuccess) e = launch_variant_step(b, b->variant, step, cap);
+      if (b->variant == kStaged) {
+        e = launch_staged_step(b, step, cap);
+      } else {
+        e = cudaMemsetAsync(b->d_ctr, 0, ctr_bytes, cap);
+        if (e == cudaSuccess) e = launch_variant_step(b, b->variant, step, cap);
+      }
     }
     if (e == cudaSuccess && (b->degree & 1)) {
       dim3 grid(64, nc);
@@ -348,7 +483,8 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
     b->graph_variant = b->variant;
   }
   if (cudaGraphLaunch(b->graph, st) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "graph launch failed");
-  for (cs_ctx* c : b->ctxs) c->launches += b->degree + ((b->degree & 1) ? 1 : 0);
+  const int per_step = (b->variant == kStaged) ? (int)b->groups.size() : 1;
+  for (cs_ctx* c : b->ctxs) c->launches += (long long)b->degree * per_step + ((b->degree & 1) ? 1 : 0);
   return CS_OK;
 }
 
@@ -406,8 +542,8 @@ cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree
     return CS_ERR_ALLOC;
   }
   for (int i = 0; i < n; ++i) b->h_cl[i].coef = b->d_coef + (size_t)i * degree * 3;
-  // default variant: the first that fits shared memory
-  for (int v = 0; v < kNumVariants; ++v)
+  // default variant: the first persistent one that fits shared memory
+  for (int v = 0; v < kStaged; ++v)
     if (variant_smem(b->ctxs, v) <= 227 * 1024) {
       b->variant = v;
       break;
@@ -487,6 +623,7 @@ cs_status cs_batch_tune(cs_batch* b, float* const* X, const long long* ld, const
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    b->tune_ms[v] = ms;
     if (ms < best) {
       best = ms;
       best_v = v;
@@ -501,6 +638,21 @@ cs_status cs_batch_tune(cs_batch* b, float* const* X, const long long* ld, const
   if (cudaStreamSynchronize(st) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "sync failed");
   if (chosen) *chosen = best_v;
   if (best_ms) *best_ms = best;
+  return CS_OK;
+}
+
+cs_status cs_batch_set_variant(cs_batch* b, int variant) {
+  if (!b || variant < 0 || variant >= kNumVariants) return bfail(b, CS_ERR_ARG, "bad variant");
+  if (variant_smem(b->ctxs, variant) > 227 * 1024)
+    return bfail(b, CS_ERR_ARG, "variant does not fit in shared memory");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "cudaSetDevice failed");
+  b->variant = variant;
+  return build_items(b, variant);
+}
+
+cs_status cs_batch_tune_times(const cs_batch* b, float* ms, int n) {
+  if (!b || !ms || n < 1) return CS_ERR_ARG;
+  for (int v = 0; v < n; ++v) ms[v] = (v < kNumVariants) ? b->tune_ms[v] : -1.f;
   return CS_OK;
 }
 

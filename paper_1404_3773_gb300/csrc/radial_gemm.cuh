@@ -196,14 +196,17 @@ __device__ __forceinline__ void radial_gemm_tile(const float* __restrict__ X, lo
           ep.out[o] = z;
           continue;
         }
+        // every rounding is spelled out (fmaf, __fmul_rn, __fadd_rn), so the compiler cannot
+        // contract differently from one kernel that embeds this tile to another: the batched
+        // forms stay bitwise equal to the single-cluster launches
         const float x = ep.X[a_ + (size_t)s * ep.ld];
-        float hx = ep.half_lambda[a_] * x + z;
-        if (ep.kb) hx += ep.kb[a_ + (size_t)s * ep.kb_ld];
+        float hx = fmaf(ep.half_lambda[a_], x, z);
+        if (ep.kb) hx = __fadd_rn(hx, ep.kb[a_ + (size_t)s * ep.kb_ld]);
         if (ep.mode == EP_APPLY) {
           ep.out[o] = hx;
         } else {  // EP_CHEB: out = cA (HX - c X) - cB Yprev   (out may alias Yprev)
-          float y = ep.cA * (hx - ep.cshift * x);
-          if (ep.Yprev) y -= ep.cB * ep.Yprev[o];
+          float y = __fmul_rn(ep.cA, fmaf(-ep.cshift, x, hx));
+          if (ep.Yprev) y = fmaf(-ep.cB, ep.Yprev[o], y);
           ep.out[o] = y;
         }
       }

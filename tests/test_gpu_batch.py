@@ -18,6 +18,12 @@ def _clusters():
         W.small_cluster(lmax=4, nmax=6, n_r=12, n_theta=10, n_phi=18, n_s=21, seed=8021),
         W.small_cluster(lmax=12, nmax=10, n_r=20, n_theta=24, n_phi=48, n_s=5, seed=8031,
                         natoms=5),
+        # lmax 32: the register-blocked angular block does not fit, the row-pair block runs
+        W.small_cluster(lmax=32, nmax=4, n_r=8, n_theta=64, n_phi=128, n_s=9, seed=8041,
+                        natoms=3),
+        # 112 radial nodes: seven rows per thread in the synthesis tiles; 130 states
+        W.small_cluster(lmax=5, nmax=56, n_r=112, n_theta=12, n_phi=24, n_s=130, seed=8051,
+                        R=12.0, natoms=4),
     ]
 
 
@@ -27,7 +33,10 @@ def _bounds(ctx, cs, torch):
     return tmin + 0.2 * (b - tmin), b, tmin
 
 
-def test_batched_filter_equals_single_cluster_filters():
+@pytest.mark.parametrize("variant", ["persistent_rp4", "persistent_rp2", "staged"])
+def test_batched_filter_equals_single_cluster_filters(variant):
+    """One persistent launch per step (row-pair tiles of 4 or 2 states) and the staged form
+    (one launch per stage and tile shape): both bitwise equal to the single-cluster filters."""
     torch, cs = need_gpu()
     ws = _clusters()
     ctxs = [make_ctx(w) for w in ws]
@@ -40,6 +49,7 @@ def test_batched_filter_equals_single_cluster_filters():
         cs.cs_cheb_filter(c, Y, degree, a, b, a0, cs.CS_FP32)
         refs.append(Y)
     batch = cs.cs_batch_create(ctxs, [w.n_s for w in ws], degree)
+    cs.cs_batch_set_variant(batch, variant)
     a, b, a0 = zip(*bounds)
     Yb = [X.clone() for X in Xs]
     cs.cs_batch_cheb_filter(batch, Yb, a, b, a0)
@@ -71,6 +81,8 @@ def test_batched_filter_vs_oracle_and_tuner():
     keep = [X.clone() for X in Xs]
     variant, ms = cs.cs_batch_tune(batch, Xs, a, b, a0)
     assert variant >= 0 and ms > 0
+    times = cs.cs_batch_tune_times(batch)
+    assert all(t > 0 for t in times.values()), times
     for X, K in zip(Xs, keep):
         assert torch.equal(X, K)  # restored
     cs.cs_batch_cheb_filter(batch, Xs, a, b, a0)
