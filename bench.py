@@ -89,7 +89,7 @@ def dense_flops(d, n):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of the kernel as it stands, on this workload; a class without a capture reports null
-NCU_TRAFFIC_BYTES = {"angular_f32": 32.402176e6 + 7.424e3}
+NCU_TRAFFIC_BYTES = {"angular_f32": 32.413952e6 + 20.992e3}
 
 
 def measured_peaks():
@@ -100,10 +100,13 @@ def measured_peaks():
         return {}
 
 
-def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
+def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps, dense_prec):
     """Per kernel class: launches, share of device time, algorithmic TFLOP/s and the fraction
-    of the pipe that bounds it; the dominant class becomes the `roofline` object."""
-    from paper_1404_3773_gb300 import CS_MIXED_BF16
+    of the pipe that bounds it; the dominant class becomes the `roofline` object. The dense
+    class (Gram matrices and rotations of CholQR2 and Rayleigh-Ritz, factor, eigensolve) is
+    rated against the pipe its Gram matrices and rotations run on: FP64, or the FP32 pipe in
+    double-float."""
+    from paper_1404_3773_gb300 import CS_DF64, CS_MIXED_BF16
     names = cs.profile_class_names()
     af = algorithmic_flops(w, n_s)
     peaks = measured_peaks()
@@ -127,7 +130,7 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps):
             bound, peak, src = "tensor", bf16, "measured bf16 sustained (MEASURED_PEAKS.json)"
         elif f32:
             bound, peak, src = "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-        elif kind == "df64":
+        elif kind == "df64" or (fam == "dense" and dense_prec == CS_DF64):
             bound, peak, src = "alu", DF64_PEAK_TFLOPS, ("FP32 issue rate / 15 instructions "
                                                          "per double-float multiply-add")
         else:
@@ -372,7 +375,10 @@ def run_ours(args):
         return
 
     # ---- roofline of the dominant kernel class (device time measured live above)
-    roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps)
+    roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps,
+                                       dense_prec)
+
+    step_times = step_breakdown(classes, args.steps, degree, ms_per_step, prec, rr_prec)
 
     batched = None if args.no_batched else batched_measure(dev)
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
@@ -396,6 +402,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (independent state blocks)"},
         "roofline": roofline,
         "kernel_classes": classes,
+        "step_times": step_times,
         "cpu_baseline": cpu,
         "e2e": {"value": round(world * applies_per_step / (e2e_ms / 1e3), 2),
                 "unit": "applies/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -410,6 +417,35 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def step_breakdown(classes, steps, degree, ms_per_step, prec, rr_prec):
+    """Per ChFSI iteration: the filter pass (degree H.X with the recurrence), one Chebyshev
+    step, the Rayleigh-Ritz H.X and the dense part, from the per-class device times; and the
+    step's roofline time, the sum over classes of algorithmic flops / the bounding pipe's peak
+    (every class here is ALU-bound: its bytes / HBM bandwidth is far smaller)."""
+    from paper_1404_3773_gb300 import CS_FP64, CS_FP32, CS_MIXED_BF16, CS_DF64
+    sfx = {CS_FP64: "", CS_FP32: "_f32", CS_MIXED_BF16: "_f32", CS_DF64: "_df64"}
+    fams = ("radial_synth", "angular", "radial_anal", "kb")
+
+    def hx_ms(suffix):
+        return sum(classes[f + suffix]["ms"] for f in fams if f + suffix in classes) / steps
+
+    filt = hx_ms(sfx[prec])
+    if sfx[rr_prec] == sfx[prec]:  # filter and Rayleigh-Ritz applies share the classes
+        rr = filt / (degree + 1)
+        filt -= rr
+    else:
+        rr = hx_ms(sfx[rr_prec])
+    dense = classes["dense"]["ms"] / steps if "dense" in classes else 0.0
+    roof = 0.0
+    for c in classes.values():
+        if c["flops_per_launch"]:
+            roof += c["launches"] / steps * c["flops_per_launch"] / (c["peak"] * 1e12) * 1e3
+    return {"filter_pass_ms": round(filt, 4), "cheb_step_ms": round(filt / degree, 4),
+            "rayleigh_ritz_apply_ms": round(rr, 4), "dense_ms": round(dense, 4),
+            "step_ms": round(ms_per_step, 4),
+            "roofline_ms": round(roof, 4), "roofline_frac": round(roof / ms_per_step, 4)}
 
 
 def batched_measure(dev, reps=2):

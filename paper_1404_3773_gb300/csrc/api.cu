@@ -384,7 +384,7 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   }
   if (r != CS_OK) return r;
   CS_LAUNCH(c, 2, dense_gram(c, X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st));
-  CS_LAUNCH(c, 1, launch_jacobi_eig(Hs, n_s, theta, Q, jw, status_dev, st));
+  CS_LAUNCH(c, 1, launch_sym_eig(Hs, n_s, theta, Q, jw, status_dev, st));
   CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
   CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
@@ -816,7 +816,7 @@ cs_status cs_lanczos_bound(cs_ctx* c, int k, const double* v0, double* b, double
     CS_LAUNCH(c, 1, launch_scale_inv_sqrt(w, V + (size_t)(i + 1) * d, d, beta2 + i, st));
   }
   CS_LAUNCH(c, 1, launch_build_tridiag(alpha, beta2, k, T, st));
-  CS_LAUNCH(c, 1, launch_jacobi_eig(T, k, th, Q, jw, status + 8, st));
+  CS_LAUNCH(c, 1, launch_sym_eig(T, k, th, Q, jw, status + 8, st));
   std::vector<double> hth(k), hb2(k);
   CS_CHECK_CUDA(c, cudaMemcpyAsync(hth.data(), th, k * 8, cudaMemcpyDeviceToHost, st));
   CS_CHECK_CUDA(c, cudaMemcpyAsync(hb2.data(), beta2, k * 8, cudaMemcpyDeviceToHost, st));

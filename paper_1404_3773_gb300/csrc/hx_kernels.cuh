@@ -110,9 +110,12 @@ cudaError_t launch_scale_rows(F* y, int n_p, int S, int ld, const F* h, cudaStre
 // work: n*n + 2n doubles. status[0] = 0 ok, else 1 + index of the failing pivot.
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream);
-// Symmetric eigensolve of sym(A) (n x n, lda = n): theta ascending, V (n x n) columns.
-// work: n*n + 2n doubles. status[0] = sweeps used (negative if not converged).
-cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, double* work,
+// Symmetric eigensolve of sym(A) (n x n, lda = n): theta ascending, V (n x n) columns. An FP32
+// solve (Householder tridiagonalisation, then bisection with inverse iteration, or QL where the
+// bisection tiles do not fit in shared memory), Newton-Schulz re-orthonormalisation and
+// Ogita-Aishima refinement in FP64, exact FP64 Jacobi inside clusters of near-equal values.
+// work: 8n^2 + 3n + 4 doubles. status[0] = 1, or negative if a step did not converge.
+cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, double* work,
                               int* status, cudaStream_t stream);
 // resid[i] = || HX[:, i] - theta[i] X[:, i] ||_2
 cudaError_t launch_residuals(const double* X, long long ldx, const double* HX, long long ldh,

@@ -1001,7 +1001,7 @@ __global__ void __launch_bounds__(1024) k_oa_final(const double* __restrict__ S,
   for (int i = tid; i < n; i += nt) theta[i] = lam[i];
 }
 
-cudaError_t launch_jacobi_eig(const double* A, int n, double* theta, double* V, double* work,
+cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, double* work,
                               int* status, cudaStream_t stream) {
   const size_t n2 = (size_t)n * n;
   double* V0 = work;
