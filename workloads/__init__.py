@@ -162,6 +162,19 @@ def kb_projector_values(xyz: np.ndarray, atoms: np.ndarray, rc: float = 1.0):
     return p, h
 
 
+def gaussian_atom_density(xyz: np.ndarray, atoms: np.ndarray, Z: float = 4.0,
+                          sigma: float = 1.0) -> np.ndarray:
+    """SCF starting density: Z electrons per atom in a normalised Gaussian of width sigma,
+    Z (2 pi sigma^2)^(-3/2) exp(-|x-a|^2 / (2 sigma^2)), summed over atoms (a synthetic
+    superposition of atomic densities)."""
+    rho = np.zeros(xyz.shape[0])
+    c = Z * (2.0 * math.pi * sigma * sigma) ** -1.5
+    for a in atoms:
+        d2 = np.sum((xyz - a[None, :]) ** 2, axis=1)
+        rho += c * np.exp(-d2 / (2.0 * sigma * sigma))
+    return rho
+
+
 # --------------------------------------------------------------------------------------
 # workload descriptions
 # --------------------------------------------------------------------------------------
