@@ -248,11 +248,14 @@ cs_status cs_apply_H_noalloc(cs_ctx* ctx, int n_s, const void* X, void* HX, long
 /* ------------------------------------------------------------------ batched filter */
 
 /* Many independent clusters (contexts of uneven lmax, N, grid and state count) filtered
- * together, FP32 blocks (Sec. 3.2.1 filter, Sec. 2.2.4 H.X per cluster). One persistent
- * launch per Chebyshev step runs the radial, angular and radial-analysis work of every
- * cluster from one ordered work list (bounded waits between the stages of a cluster); the
- * filter is captured once into a CUDA graph and replayed. All contexts must be on one device,
- * have a potential and no projectors. n_s[i] states for cluster i; degree fixed per batch. */
+ * together, FP32 blocks (Sec. 3.2.1 filter, Sec. 2.2.4 H.X per cluster). The radial,
+ * angular and radial-analysis tiles of every cluster form one work list per Chebyshev step,
+ * run either by one persistent launch per step (bounded waits between the stages of a
+ * cluster) or staged, one launch per (stage, tile shape) group (see cs_batch_tune_times);
+ * the filter is captured once into a CUDA graph and replayed. Every cluster's result is
+ * bitwise equal to cs_cheb_filter on that cluster alone (CS_FP32). All contexts must be on one
+ * device, have a potential and no projectors. n_s[i] states for cluster i; degree fixed per
+ * batch. */
 typedef struct cs_batch cs_batch;
 cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree,
                           cs_batch** out);

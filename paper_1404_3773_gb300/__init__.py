@@ -29,6 +29,12 @@ __all__ = [
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
     "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
+    # SCF pieces (include/cs_scf.h)
+    "CS_DENSITY_CHUNK", "CS_MIXER_MAX_HISTORY", "CS_GRID_INTEGRALS_MAX", "ScfParams",
+    "ScfReport", "Mixer", "Scf", "cs_scf_workspace_bytes", "cs_density", "cs_hartree",
+    "cs_lda_xc", "cs_grid_integrals", "cs_fermi_occupations", "cs_mixer_create",
+    "cs_mixer_mix", "cs_mixer_reset", "cs_mixer_free", "cs_scf_create", "cs_scf_work_bytes",
+    "cs_scf_step", "cs_scf_grid", "cs_scf_occupations", "cs_scf_free",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -51,6 +57,27 @@ _lib = ctypes.CDLL(_LIB_PATH)
 class _Quad(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
                 ("radial", ctypes.c_int)]
+
+
+class ScfParams(ctypes.Structure):
+    """cs_scf_params (include/cs_scf.h)."""
+    _fields_ = [("n_s", ctypes.c_int), ("n_want", ctypes.c_int), ("degree", ctypes.c_int),
+                ("filter_prec", ctypes.c_int), ("n_electrons", ctypes.c_double),
+                ("kT", ctypes.c_double), ("beta", ctypes.c_double), ("history", ctypes.c_int),
+                ("first_tol", ctypes.c_double), ("first_max_iter", ctypes.c_int),
+                ("lanczos_k", ctypes.c_int), ("e_ion", ctypes.c_double)]
+
+
+class ScfReport(ctypes.Structure):
+    """cs_scf_report (include/cs_scf.h)."""
+    _fields_ = [("iteration", ctypes.c_int), ("chfsi_iterations", ctypes.c_int),
+                ("energy", ctypes.c_double), ("dE", ctypes.c_double), ("mu", ctypes.c_double),
+                ("entropy", ctypes.c_double), ("band", ctypes.c_double),
+                ("e_hartree", ctypes.c_double), ("e_xc", ctypes.c_double),
+                ("max_resid", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _vp = ctypes.c_void_p
@@ -98,6 +125,23 @@ _SIGS = {
     "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
     "cs_launch_count": (_ll, [_vp]),
+    # SCF pieces
+    "cs_scf_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_density": (_i, [_vp, _i, _vp, _ll, _vp, _vp, _vp, _vp]),
+    "cs_hartree": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "cs_lda_xc": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "cs_grid_integrals": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _dp, _vp, _vp]),
+    "cs_fermi_occupations": (_i, [_i, _dp, _d, _d, _dp, _dp, _dp]),
+    "cs_mixer_create": (_i, [_vp, _d, _i, ctypes.POINTER(_vp)]),
+    "cs_mixer_mix": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "cs_mixer_reset": (_i, [_vp]),
+    "cs_mixer_free": (_i, [_vp]),
+    "cs_scf_create": (_i, [_vp, ctypes.POINTER(ScfParams), _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "cs_scf_work_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_scf_step": (_i, [_vp, _vp, _ll, _vp, _vp, _vp, _vp, ctypes.POINTER(ScfReport)]),
+    "cs_scf_grid": (_i, [_vp, _i, _vp, _vp]),
+    "cs_scf_occupations": (_i, [_vp, _dp]),
+    "cs_scf_free": (_i, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -525,3 +569,207 @@ def grid_points(ctx: Context):
     y = r[:, None, None] * st[None, :, None] * np.sin(ph)[None, None, :]
     z = r[:, None, None] * t[None, :, None] * np.ones_like(ph)[None, None, :]
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+# ---------------------------------------------------------------------- SCF pieces
+CS_DENSITY_CHUNK, CS_MIXER_MAX_HISTORY, CS_GRID_INTEGRALS_MAX = 16, 64, 8
+
+
+def _check_grid(ctx: Context, t: torch.Tensor):
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    assert t.numel() == ctx.n_r * ctx.n_theta * ctx.n_phi
+
+
+def cs_scf_workspace_bytes(ctx: Context) -> int:
+    out = ctypes.c_size_t()
+    ctx.check(_lib.cs_scf_workspace_bytes(ctx.handle, ctypes.byref(out)))
+    return out.value
+
+
+def _scf_ws(ctx: Context, work):
+    if work is not None:
+        return work
+    nbytes = cs_scf_workspace_bytes(ctx)
+    ws = ctx._ws.get("scf")
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        ctx._ws["scf"] = ws
+    return ws
+
+
+def cs_density(ctx: Context, X: torch.Tensor, occ: torch.Tensor, rho: torch.Tensor, work=None,
+               stream=None):
+    """rho = 2 sum_s occ[s] psi_s^2 on the grid (X: (n_s, ld) float64, occ: (n_s,) float64)."""
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    assert occ.is_cuda and occ.dtype == torch.float64 and occ.numel() >= n_s
+    _check_grid(ctx, rho)
+    ctx.check(_lib.cs_density(ctx.handle, n_s, _ptr(X), ld, _ptr(occ), _ptr(rho),
+                              _ptr(_scf_ws(ctx, work)), _stream_ptr(stream)))
+
+
+def cs_hartree(ctx: Context, rho: torch.Tensor, vh: torch.Tensor, work=None, stream=None):
+    _check_grid(ctx, rho)
+    _check_grid(ctx, vh)
+    ctx.check(_lib.cs_hartree(ctx.handle, _ptr(rho), _ptr(vh), _ptr(_scf_ws(ctx, work)),
+                              _stream_ptr(stream)))
+
+
+def cs_lda_xc(ctx: Context, rho: torch.Tensor, exc: torch.Tensor | None,
+              vxc: torch.Tensor | None, stream=None):
+    _check_grid(ctx, rho)
+    for t in (exc, vxc):
+        if t is not None:
+            _check_grid(ctx, t)
+    ctx.check(_lib.cs_lda_xc(ctx.handle, _ptr(rho), _ptr(exc), _ptr(vxc), _stream_ptr(stream)))
+
+
+def cs_grid_integrals(ctx: Context, fs, gs=None, work=None, stream=None) -> list:
+    """[sum_g W_g f_i g_i for i] (g_i None means 1)."""
+    n = len(fs)
+    gs = [None] * n if gs is None else list(gs)
+    for t in list(fs) + [g for g in gs if g is not None]:
+        _check_grid(ctx, t)
+    fa = (_vp * n)(*[t.data_ptr() for t in fs])
+    ga = (_vp * n)(*[None if g is None else g.data_ptr() for g in gs])
+    out = (_d * n)()
+    ctx.check(_lib.cs_grid_integrals(ctx.handle, n, fa, ga, out, _ptr(_scf_ws(ctx, work)),
+                                     _stream_ptr(stream)))
+    return list(out)
+
+
+def cs_fermi_occupations(lam, n_electrons: float, kT: float):
+    """(occ, mu, entropy) on the host (numpy)."""
+    import numpy as np
+    lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+    occ = np.empty_like(lam)
+    mu, ent = _d(), _d()
+    st = _lib.cs_fermi_occupations(lam.size, lam.ctypes.data_as(_dp), float(n_electrons),
+                                   float(kT), occ.ctypes.data_as(_dp), ctypes.byref(mu),
+                                   ctypes.byref(ent))
+    if st != 0:
+        raise CsError(st, "cs_fermi_occupations")
+    return occ, mu.value, ent.value
+
+
+class Mixer:
+    """Owns one cs_mixer."""
+
+    def __init__(self, ctx: Context, handle: int):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.cs_mixer_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_mixer_create(ctx: Context, beta: float, history: int) -> Mixer:
+    h = _vp()
+    ctx.check(_lib.cs_mixer_create(ctx.handle, float(beta), int(history), ctypes.byref(h)))
+    return Mixer(ctx, h.value)
+
+
+def cs_mixer_mix(m: Mixer, x_in: torch.Tensor, x_out: torch.Tensor, x_next: torch.Tensor,
+                 stream=None):
+    for t in (x_in, x_out, x_next):
+        _check_grid(m.ctx, t)
+    m.ctx.check(_lib.cs_mixer_mix(m.handle, _ptr(x_in), _ptr(x_out), _ptr(x_next),
+                                  _stream_ptr(stream)))
+
+
+def cs_mixer_reset(m: Mixer):
+    m.ctx.check(_lib.cs_mixer_reset(m.handle))
+
+
+def cs_mixer_free(m: Mixer):
+    m.close()
+
+
+class Scf:
+    """Owns one cs_scf."""
+
+    def __init__(self, ctx: Context, handle: int, n_s: int):
+        self.ctx = ctx
+        self.n_s = n_s
+        self._h = ctypes.c_void_p(handle)
+        self._work = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def work(self) -> torch.Tensor:
+        if self._work is None:
+            self._work = torch.empty(cs_scf_work_bytes(self), dtype=torch.uint8,
+                                     device=f"cuda:{self.ctx.device}")
+        return self._work
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.cs_scf_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_scf_create(ctx: Context, params: ScfParams, v_ext: torch.Tensor, rho0: torch.Tensor,
+                  v0: torch.Tensor) -> Scf:
+    _check_grid(ctx, v_ext)
+    _check_grid(ctx, rho0)
+    assert v0.is_cuda and v0.dtype == torch.float64 and v0.numel() >= ctx.d
+    h = _vp()
+    ctx.check(_lib.cs_scf_create(ctx.handle, ctypes.byref(params), _ptr(v_ext), _ptr(rho0),
+                                 _ptr(v0), ctypes.byref(h)))
+    return Scf(ctx, h.value, params.n_s)
+
+
+def cs_scf_work_bytes(s: Scf) -> int:
+    out = ctypes.c_size_t()
+    s.ctx.check(_lib.cs_scf_work_bytes(s.handle, ctypes.byref(out)))
+    return out.value
+
+
+def cs_scf_step(s: Scf, X: torch.Tensor, theta: torch.Tensor, resid: torch.Tensor, work=None,
+                stream=None) -> dict:
+    n_s, ld = _check_block(s.ctx, X, torch.float64)
+    assert n_s == s.n_s
+    rep = ScfReport()
+    s.ctx.check(_lib.cs_scf_step(s.handle, _ptr(X), ld, _ptr(theta), _ptr(resid),
+                                 _ptr(s.work() if work is None else work), _stream_ptr(stream),
+                                 ctypes.byref(rep)))
+    return rep.as_dict()
+
+
+def cs_scf_grid(s: Scf, which: int, stream=None) -> torch.Tensor:
+    """A copy (torch float64 (N_g,)) of one of the SCF state's grid functions: 0 v_in, 1 the
+    last output density, 2 its Hartree potential, 3 its eps_xc, 4 v_ext."""
+    ng = s.ctx.n_r * s.ctx.n_theta * s.ctx.n_phi
+    out = torch.empty(ng, dtype=torch.float64, device=f"cuda:{s.ctx.device}")
+    s.ctx.check(_lib.cs_scf_grid(s.handle, int(which), _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def cs_scf_occupations(s: Scf):
+    import numpy as np
+    out = np.empty(s.n_s)
+    s.ctx.check(_lib.cs_scf_occupations(s.handle, out.ctypes.data_as(_dp)))
+    return out
+
+
+def cs_scf_free(s: Scf):
+    s.close()

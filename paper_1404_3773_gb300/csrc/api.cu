@@ -513,6 +513,17 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
                      cudaMemcpyHostToDevice) != cudaSuccess)
         st = CS_ERR_ALLOC;
     }
+    if (st == CS_OK) {
+      // Hartree tables: k_ln = z_ln / R ([l][n]), then r_k / R ([k])
+      const HostTables& H = c->host;
+      std::vector<double> tab((size_t)H.L * H.N + H.n_r);
+      for (size_t i = 0; i < (size_t)H.L * H.N; ++i) tab[i] = H.z[i] / H.R;
+      for (int k = 0; k < H.n_r; ++k) tab[(size_t)H.L * H.N + k] = H.r[k] / H.R;
+      if (cudaMalloc((void**)&c->hartree_tab, tab.size() * sizeof(double)) != cudaSuccess ||
+          cudaMemcpy(c->hartree_tab, tab.data(), tab.size() * sizeof(double),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        st = CS_ERR_ALLOC;
+    }
     if (st != CS_OK) {
       g_init_error = c->err;
       cs_basis_free(c);
@@ -537,6 +548,7 @@ cs_status cs_basis_free(cs_ctx* c) {
     }
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->w_r_dev) cudaFree(c->w_r_dev);
+    if (c->hartree_tab) cudaFree(c->hartree_tab);
     if (c->tc_synth) cudaFree(c->tc_synth);
     if (c->tc_anal) cudaFree(c->tc_anal);
     if (c->kb_tabA) cudaFree(c->kb_tabA);

@@ -70,6 +70,7 @@ struct cs_ctx {
   cs::DevTables<float> d32;
   cs::DevTables<cs::df64> ddf;  // double-float copies (CS_DF64)
   double* w_r_dev = nullptr; // radial weights (for forward transforms of grid data)
+  double* hartree_tab = nullptr;  // k_ln = z_ln / R ([l][n]) then r_k / R ([k]) (scf.cu)
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
   int tc_mt_synth = 0, tc_kpad_synth = 0, tc_mt_anal = 0, tc_kpad_anal = 0;

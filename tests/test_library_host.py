@@ -1,5 +1,5 @@
-"""The C-ABI library without a GPU: it loads, exports every entry point that include/cs.h
-declares, builds its host tables (compared here with the oracle's, which share no code
+"""The C-ABI library without a GPU: it loads, exports every entry point that include/*.h
+declare, builds its host tables (compared here with the oracle's, which share no code
 with them), and rejects bad arguments and device calls on a host-only context."""
 import ctypes
 import os
@@ -17,9 +17,12 @@ def _lib():
 
 
 def _declared_symbols():
-    hdr = open(os.path.join(ROOT, "include", "cs.h")).read()
-    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", hdr)))
+    import glob
+    names = set()
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        hdr = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", hdr))
+    return sorted(names)
 
 
 def test_header_symbols_exported():
@@ -83,3 +86,19 @@ def test_workspace_bytes_grows_with_block():
     assert 0 < a < b < c
     # it covers at least the radial-node intermediate, two blocks and the Lanczos basis
     assert b >= 32 * 121 * 16 * 8 + 4 * ctx.d * 16 * 8
+
+
+def test_fermi_occupations_match_oracle():
+    """cs_fermi_occupations (host Brent root of the electron count) against the oracle's
+    (scipy brentq), including a degenerate level at the Fermi energy."""
+    cs = _lib()
+    from oracle import scf
+    for lam, ne, kT in (([-1.0, -0.5, -0.5, 0.2, 0.9], 4.0, 1e-3),
+                        (np.linspace(-2.0, 1.0, 40), 31.0, 0.05),
+                        ([-0.3, -0.2], 1.0, 1e-6)):
+        occ, mu, S = cs.cs_fermi_occupations(lam, ne, kT)
+        f, m, S2 = scf.fermi_occupations(np.asarray(lam), ne, kT)
+        assert np.max(np.abs(occ - f)) <= 1e-10
+        assert abs(mu - m) <= 1e-9 and abs(S - S2) <= 1e-8
+        # one ulp of mu moves the count by about ulp(mu) / (4 kT)
+        assert abs(occ.sum() - ne / 2) <= 1e-12 + 1e-16 / kT
