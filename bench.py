@@ -382,6 +382,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else batched_measure(dev)
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
+    scf = None if args.no_scf else scf_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
@@ -409,6 +410,7 @@ def run_ours(args):
         "gpu_launches": int(launches_timed),
         "batched": batched,
         "at_scale": at_scale,
+        "scf": scf,
         "clocks": clocks.summary(),
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
@@ -446,6 +448,68 @@ def step_breakdown(classes, steps, degree, ms_per_step, prec, rr_prec):
             "rayleigh_ritz_apply_ms": round(rr, 4), "dense_ms": round(dense, 4),
             "step_ms": round(ms_per_step, 4),
             "roofline_ms": round(roof, 4), "roofline_frac": round(roof / ms_per_step, 4)}
+
+
+def scf_measure(dev, precisions=("fp32", "fp64"), tol=1e-6, max_iter=80):
+    """SCF time to |dE| <= tol Ha on the 32-atom cluster (Z = 4 erf pseudo-atoms, 128
+    electrons, 80 states, degree 16): Gaussian starting density (sigma 1 bohr per atom),
+    Fermi-Dirac kT = 6.3e-4 Ha (200 K), Anderson mixing of the effective potential (beta 0.3,
+    history 8), ChFSI to a 1e-3 residual in the first iteration, then one ChFSI iteration per
+    SCF iteration. Wall clock around the whole loop (every SCF step synchronises)."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t, gaussian_atom_density_t
+    w = W.erf_cluster_32()
+    atoms = w.atoms()
+    Z = w.extra["Z"]
+    e_ion = sum(Z * Z / float(np.linalg.norm(atoms[i] - atoms[j]))
+                for i in range(len(atoms)) for j in range(i))
+    idx = torch.device(dev).index or 0
+    out = {"workload": "erf32_l30_n48 SCF: 32 Z=4 erf pseudo-atoms, 128 electrons, 80 states, "
+                       "degree 16, kT 200 K, Anderson beta 0.3 / history 8, "
+                       f"stop at |dE| <= {tol:g} Ha (total)",
+           "e_ion": e_ion}
+    for name in precisions:
+        prec = {"fp32": cs.CS_FP32, "fp64": cs.CS_FP64, "mixed": cs.CS_MIXED_BF16}[name]
+        ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, idx)
+        if prec != cs.CS_FP64:  # double-float Rayleigh-Ritz apply and dense work
+            cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+            cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+        xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+        v_ext = erf_cluster_potential_t(xyz, atoms, Z, w.extra["rc"]).contiguous()
+        rho0 = gaussian_atom_density_t(xyz, atoms, Z, 1.0).contiguous()
+        v0 = torch.tensor(W.gaussian(17, ctx.d), device=dev)
+        p = cs.ScfParams(n_s=w.n_s, n_want=w.n_want, degree=w.degree, filter_prec=prec,
+                         n_electrons=Z * len(atoms), kT=6.3e-4, beta=0.3, history=8,
+                         first_tol=1e-3, first_max_iter=40, lanczos_k=10, e_ion=e_ion)
+        S = cs.cs_scf_create(ctx, p, v_ext, rho0, v0)
+        X = torch.tensor(W.gaussian_block(w.x_seed, w.d, w.n_s).T.copy(), device=dev)
+        theta = torch.empty(w.n_s, dtype=torch.float64, device=dev)
+        resid = torch.empty_like(theta)
+        S.work()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = []
+        for _ in range(max_iter):
+            reps.append(cs.cs_scf_step(S, X, theta, resid))
+            if len(reps) > 1 and abs(reps[-1]["dE"]) <= tol:
+                break
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        last = reps[-1]
+        out[name] = {"seconds": round(sec, 3), "iterations": len(reps),
+                     "converged": len(reps) > 1 and abs(last["dE"]) <= tol,
+                     "ms_per_iteration": round(1e3 * sec / len(reps), 2),
+                     "first_chfsi_iterations": reps[0]["chfsi_iterations"],
+                     "energy": last["energy"], "energy_per_atom": last["energy"] / len(atoms),
+                     "last_dE": last["dE"], "mu": last["mu"], "max_resid": last["max_resid"],
+                     "dE_history": [r["dE"] for r in reps]}
+        S.close()
+        ctx.close()
+    if "fp32" in out and "fp64" in out:
+        out["fp32_energy_minus_fp64"] = out["fp32"]["energy"] - out["fp64"]["energy"]
+    return out
 
 
 def batched_measure(dev, reps=2):
@@ -676,6 +740,7 @@ def main():
                     help="arithmetic of the Gram matrices and block rotations")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-at-scale", action="store_true")
+    ap.add_argument("--no-scf", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

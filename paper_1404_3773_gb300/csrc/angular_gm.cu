@@ -25,17 +25,36 @@ cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, cudaStream_t st
   return cudaGetLastError();
 }
 
-size_t build_theta_pairs(const std::vector<double>& theta, int L, int n_theta,
-                         std::vector<double>& out) {
-  const GmShape g = gm_shape(L, 0, n_theta);
+size_t build_theta_pairs(const std::vector<double>& theta, const std::vector<double>& trig,
+                         int L, int Q4, int n_theta, std::vector<double>& out) {
+  const GmShape g = gm_shape(L, Q4, n_theta);
   const int NP = (n_theta + 1) / 2;
-  out.assign(gm_theta_pairs_elems(L, n_theta), 0.0);
+  const size_t nth = gm_theta_pairs_elems(L, n_theta);
+  out.assign(nth + gm_trig_elems(L, Q4), 0.0);
   for (int ch = 0; ch < g.nchunks; ++ch)
     for (int o = 0; o < g.RL; ++o)
       for (int p = 0; p < kGmRC; ++p) {
         const int jp = ch * kGmRC + p;
         if (jp < NP)
           out[((size_t)ch * (g.RL + 4) + o) * kGmRC + p] = theta[(size_t)jp * g.RL + o];
+      }
+  // phi tables in the kernel's shared-memory layouts. Tb[cos|sin][m < Lb][q < Qp] and
+  // Tc[cos|sin][q < Qp + 1][mp < Lq], where mp lists the even m (padded to ne4), then the odd
+  // m. Zero outside m < L, q < Q.
+  const int Q = g.Q;
+  double* Tb = out.data() + nth;
+  double* Tc = Tb + 2 * (size_t)g.Lb * g.Qp;
+  for (int c = 0; c < 2; ++c)
+    for (int m = 0; m < g.Lb; ++m)
+      for (int q = 0; q < g.Qp; ++q)
+        Tb[((size_t)c * g.Lb + m) * g.Qp + q] =
+            (m < L && q < Q) ? trig[((size_t)c * L + m) * Q + q] : 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int q = 0; q <= g.Qp; ++q)
+      for (int mp = 0; mp < g.Lq; ++mp) {
+        const int m = (mp < g.ne4) ? 2 * mp : 2 * (mp - g.ne4) + 1;
+        Tc[((size_t)c * (g.Qp + 1) + q) * g.Lq + mp] =
+            (m < L && q < Q) ? trig[((size_t)c * L + m) * Q + q] : 0.0;
       }
   return out.size();
 }

@@ -15,9 +15,12 @@
 // B and C use 4 x 4 register tiles with a warp's lanes laid out 4 (rows) x 8 (columns) and
 // load the next step's operands while the current FMAs run; C groups the modes by parity
 // so one tile needs one cos and one sin input array. D accumulates the (l, m) outputs for all
-// 8 states in shared memory; an item is four l of one parity of one mode, its lanes share a
-// mode, so each AP load is a broadcast that feeds 32 FMAs. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair]) from a
-// table built at set-up, so staging them is a contiguous copy.
+// 8 states in shared memory; an item is five l of one parity of one mode, its lanes share a
+// mode, so each AP load is a broadcast that feeds 40 FMAs, and up to lmax 31 every thread has
+// at most one item. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair])
+// from a table built at set-up, followed by the phi tables in their shared-memory layouts, so
+// staging either is a contiguous copy. The W V rows of a chunk are staged in the AP region
+// (free until stage C) before stage A.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +34,7 @@ constexpr int kGmThreads = 256;
 constexpr int kGmST = 8;     // states per CTA
 constexpr int kGmRC = 8;     // mirrored row pairs per chunk
 constexpr int kGmItems = 2;  // Legendre-quadrature items per thread (up to 512 per CTA)
+constexpr int kGmLq = 5;     // l per Legendre-quadrature item
 
 __host__ __device__ inline int gm_round4(int x) { return (x + 3) & ~3; }
 
@@ -59,6 +63,12 @@ __host__ __device__ inline size_t gm_theta_pairs_elems(int L, int n_theta) {
   const GmShape g = gm_shape(L, 0, n_theta);
   return (size_t)g.nchunks * (g.RL + 4) * kGmRC;
 }
+// floats of the phi tables in their shared-memory layouts (Tb then Tc), stored after the
+// Legendre table
+__host__ __device__ inline size_t gm_trig_elems(int L, int Q4) {
+  const GmShape g = gm_shape(L, Q4, 1);
+  return 2 * (size_t)g.Lb * g.Qp + 2 * (size_t)(g.Qp + 1) * g.Lq;
+}
 
 // shared-memory footprint in bytes
 __host__ __device__ inline size_t gm_smem_bytes(int L, int Q4, int n_theta) {
@@ -75,14 +85,17 @@ __host__ __device__ inline int gm_items(int L) {
   int items = 0;
   for (int m = -(L - 1); m < L; ++m) {
     const int cnt = L - (m < 0 ? -m : m);
-    items += ((cnt + 1) / 2 + 3) / 4 + (cnt / 2 + 3) / 4;
+    items += ((cnt + 1) / 2 + kGmLq - 1) / kGmLq + (cnt / 2 + kGmLq - 1) / kGmLq;
   }
   return items;
 }
 
-// whether the block fits: shared memory and the per-thread item slots
+// whether the block fits: shared memory, the per-thread item slots, and the W V rows of a
+// chunk (2 kGmRC rows of n_phi <= 4 Q4 + 3 values) inside the AP region
 __host__ __device__ inline bool gm_eligible(int L, int Q4, int n_theta) {
-  return gm_smem_bytes(L, Q4, n_theta) <= 227 * 1024 && gm_items(L) <= kGmItems * kGmThreads;
+  const GmShape g = gm_shape(L, Q4, n_theta);
+  return gm_smem_bytes(L, Q4, n_theta) <= 227 * 1024 && gm_items(L) <= kGmItems * kGmThreads &&
+         (size_t)2 * kGmRC * (4 * Q4 + 4) <= (size_t)g.M2 * g.NC;
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -119,17 +132,14 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = min(ST, S - s0);
 
-  // ---- set-up: phi tables in two layouts, the state tile of G, zero rows, mode starts
-  for (int i = tid; i < 2 * Lb * Qp; i += kGmThreads) {
-    const int cs_ = i / (Lb * Qp), r = i - cs_ * Lb * Qp;
-    const int m = r / Qp, q = r - m * Qp;
-    Tb[i] = (m < L && q < Q) ? a.trig[(size_t)(cs_ * L + m) * Q + q] : 0.f;
-  }
-  for (int i = tid; i < 2 * (Qp + 1) * Lq; i += kGmThreads) {
-    const int cs_ = i / ((Qp + 1) * Lq), r = i - cs_ * (Qp + 1) * Lq;
-    const int q = r / Lq, mp = r - q * Lq;
-    const int m = (mp < ne4) ? 2 * mp : 2 * (mp - ne4) + 1;
-    Tc[i] = (m < L && q < Q) ? a.trig[(size_t)(cs_ * L + m) * Q + q] : 0.f;
+  // ---- set-up: phi tables (both layouts, from the set-up table), the state tile of G, zero
+  //      rows, mode starts
+  {
+    const float4* src =
+        reinterpret_cast<const float4*>(a.theta_pairs + gm_theta_pairs_elems(L, Nt));
+    float4* dst = reinterpret_cast<float4*>(Tb);  // Tc follows Tb
+    const int n4 = (int)(gm_trig_elems(L, Q4) / 4);
+    for (int i = tid; i < n4; i += kGmThreads) dst[i] = src[i];
   }
   for (int b0 = 0; b0 < L2 * ST; b0 += NB * kGmThreads) {
     float v[NB];
@@ -153,14 +163,14 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
     Fz[(size_t)(M2 + 1) * NCp + i] = 0.f;
   }
   for (int i = tid; i < 4 * NC; i += kGmThreads) Wq[(size_t)(i / NC) * WS + (size_t)Qp * NC + i % NC] = 0.f;
-  // Legendre-quadrature items: (mode, parity of l - |m|, group of 4 such l); mstart[mi] is the
+  // Legendre-quadrature items: (mode, parity of l - |m|, group of kGmLq such l); mstart[mi] is the
   // first item of mode mi, the even-parity groups first
   if (tid == 0) {
     int o = 0;
     for (int mi = 0; mi < M2; ++mi) {
       mstart[mi] = o;
       const int m = mi - lmax, cnt = L - (m < 0 ? -m : m);
-      o += ((cnt + 1) / 2 + 3) / 4 + (cnt / 2 + 3) / 4;
+      o += ((cnt + 1) / 2 + kGmLq - 1) / kGmLq + (cnt / 2 + kGmLq - 1) / kGmLq;
     }
     mstart[M2] = o;
   }
@@ -179,7 +189,7 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
         else hi = mid - 1;
       }
       const int m = lo - lmax, cnt = L - (m < 0 ? -m : m);
-      const int ge = ((cnt + 1) / 2 + 3) / 4;  // even-parity groups of this mode
+      const int ge = ((cnt + 1) / 2 + kGmLq - 1) / kGmLq;  // even-parity groups of this mode
       const int r = t - mstart[lo];
       item_code[u] = (r < ge) ? (lo | (r << 9)) : (lo | (1 << 8) | ((r - ge) << 9));
     }
@@ -205,6 +215,20 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
           const int i = b0 + u * kGmThreads + tid;
           if (i < n4) dst[i] = v[u];
         }
+      }
+    }
+    // ---- W V rows of the chunk's pairs into the AP region (unused until stage C):
+    //      WVs[p][r][q], r = 0 row j = c0 + p, r = 1 its mirror; zero where absent
+    {
+      float* WVs = AP;
+      const int n = RC * 2 * Np;
+      for (int i = tid; i < n; i += kGmThreads) {
+        const int pr = i / Np, q = i - pr * Np;
+        const int p = pr >> 1, r = pr & 1;
+        const int jp = c0 + p;
+        const int row = r ? Nt - 1 - jp : jp;
+        const bool ok = jp < NP && (r == 0 || row != jp);
+        WVs[i] = ok ? wvk[(size_t)row * Np + q] : 0.f;
       }
     }
     __syncthreads();
@@ -311,26 +335,25 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
               }
           }
         }
-        // W V of the pair's two rows at the 16 angles of the tile
+        // W V of the pair's two rows at the 16 angles of the tile (staged rows; zero rows
+        // stand for absent mirrors and pairs past the last)
         const int p = cb >> 2;  // 4 column blocks per pair
-        const int jp = c0 + p;
-        const bool v0 = jp < NP, v1 = v0 && (Nt - 1 - jp) != jp;
-        const float* wr0 = wvk + (size_t)(v0 ? jp : 0) * Np;
-        const float* wr1 = wvk + (size_t)(v1 ? Nt - 1 - jp : 0) * Np;
+        const float* wr0 = AP + (size_t)(2 * p) * Np;
+        const float* wr1 = wr0 + Np;
         float wang[2][4][4];  // [row][q][angle q, N-q, h-q, h+q]
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int q = q0 + i;
           const bool ok = q <= Q4;
           const int i0 = q, i1 = (Np - q) % Np, i2 = h - q, i3 = h + q;
-          wang[0][i][0] = (ok && v0) ? wr0[i0] : 0.f;
-          wang[0][i][1] = (ok && v0) ? wr0[i1] : 0.f;
-          wang[0][i][2] = (ok && v0) ? wr0[i2] : 0.f;
-          wang[0][i][3] = (ok && v0) ? wr0[i3] : 0.f;
-          wang[1][i][0] = (ok && v1) ? wr1[i0] : 0.f;
-          wang[1][i][1] = (ok && v1) ? wr1[i1] : 0.f;
-          wang[1][i][2] = (ok && v1) ? wr1[i2] : 0.f;
-          wang[1][i][3] = (ok && v1) ? wr1[i3] : 0.f;
+          wang[0][i][0] = ok ? wr0[i0] : 0.f;
+          wang[0][i][1] = ok ? wr0[i1] : 0.f;
+          wang[0][i][2] = ok ? wr0[i2] : 0.f;
+          wang[0][i][3] = ok ? wr0[i3] : 0.f;
+          wang[1][i][0] = ok ? wr1[i0] : 0.f;
+          wang[1][i][1] = ok ? wr1[i1] : 0.f;
+          wang[1][i][2] = ok ? wr1[i2] : 0.f;
+          wang[1][i][3] = ok ? wr1[i3] : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -416,18 +439,19 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
       }
     }
     __syncthreads();
-    // ---- D: Legendre quadrature. Item = four l of one parity (l - |m| = par, par + 2, ...) of
-    //      one mode: they read the same half of AP, so each broadcast AP load feeds 32 FMAs.
+    // ---- D: Legendre quadrature. Item = kGmLq l of one parity (l - |m| = par, par + 2, ...)
+    //      of one mode: they read the same half of AP, so each broadcast AP load feeds
+    //      8 kGmLq FMAs.
 #pragma unroll
     for (int u = 0; u < kGmItems; ++u) {
       const int code = item_code[u];
       if (code < 0) continue;
       const int mi = code & 0xff, par = (code >> 8) & 1, grp = code >> 9;
       const int m = mi - lmax, am = m < 0 ? -m : m;
-      const int lbase = am + par + 8 * grp;  // l_v = lbase + 2 v
-      float acc[4][ST], pv[4][RC];
+      const int lbase = am + par + 2 * kGmLq * grp;  // l_v = lbase + 2 v
+      float acc[kGmLq][ST], pv[kGmLq][RC];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < kGmLq; ++v) {
         const int l = lbase + 2 * v;
         if (l <= lmax) {
           const float* ga = Ga + (size_t)(l * l + l + m) * ST;
@@ -450,12 +474,12 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
         unpack4(ld4(arow + (size_t)pp * 2 * ST), av);
         unpack4(ld4(arow + (size_t)pp * 2 * ST + 4), av + 4);
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
+        for (int v = 0; v < kGmLq; ++v)
 #pragma unroll
           for (int q = 0; q < ST; ++q) acc[v][q] = fmaf(pv[v][pp], av[q], acc[v][q]);
       }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < kGmLq; ++v) {
         const int l = lbase + 2 * v;
         if (l > lmax) break;
         float* ga = Ga + (size_t)(l * l + l + m) * ST;

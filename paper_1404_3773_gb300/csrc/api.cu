@@ -172,11 +172,6 @@ cs_status upload_tables(cs_ctx* c) {
   const int rows = (H.n_theta + 1) / 2;
   std::vector<double> th(H.theta.begin(), H.theta.begin() + (size_t)rows * rowlen);
   if ((st = upload<T>(c, &D.theta, th)) != CS_OK) return st;
-  if (sizeof(T) == 4) {
-    std::vector<double> tp;
-    build_theta_pairs(th, H.L, H.n_theta, tp);
-    if ((st = upload<T>(c, &D.theta_pairs, tp)) != CS_OK) return st;
-  }
   const int Q = c->Q4 + 1;
   std::vector<double> trig((size_t)2 * H.L * Q);
   for (int m = 0; m < H.L; ++m)
@@ -188,6 +183,11 @@ cs_status upload_tables(cs_ctx* c) {
       trig[(size_t)(H.L + m) * Q + q] = std::fabs(sv) < 1e-12 ? 0.0 : sv;
     }
   if ((st = upload<T>(c, &D.trig, trig)) != CS_OK) return st;
+  if (sizeof(T) == 4) {
+    std::vector<double> tp;
+    build_theta_pairs(th, trig, H.L, c->Q4, H.n_theta, tp);
+    if ((st = upload<T>(c, &D.theta_pairs, tp)) != CS_OK) return st;
+  }
   std::vector<double> wkj((size_t)H.n_r * H.n_theta);
   for (int k = 0; k < H.n_r; ++k)
     for (int j = 0; j < H.n_theta; ++j)

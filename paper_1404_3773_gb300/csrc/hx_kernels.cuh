@@ -56,10 +56,11 @@ cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream
 // register-blocked FP32 angular kernel (angular_gm.cu); cudaErrorInvalidConfiguration when
 // its tile does not fit in shared memory or the transposed Legendre table is missing
 cudaError_t launch_angular_gm(const AngArgs<float>& a, float* G, cudaStream_t stream);
-// builds the transposed Legendre table of the register-blocked kernel from the packed rows
-// [ceil(n_theta/2)][L(L+1)/2] (host; returns the element count)
-size_t build_theta_pairs(const std::vector<double>& theta, int L, int n_theta,
-                         std::vector<double>& out);
+// builds the set-up table of the register-blocked kernel (host; returns the element count):
+// the transposed Legendre table from the packed rows [ceil(n_theta/2)][L(L+1)/2], followed by
+// the phi tables of trig ([cos|sin][m < L][q <= Q4]) in the kernel's shared-memory layouts
+size_t build_theta_pairs(const std::vector<double>& theta, const std::vector<double>& trig,
+                         int L, int Q4, int n_theta, std::vector<double>& out);
 
 template <typename T>
 cudaError_t launch_radial_synth(const T* X, long long ld, T* G, const T* rad, int L, int N,

@@ -60,7 +60,8 @@ def test_torch_generators_equal_numpy_ones():
     """The torch evaluations used for large grids reproduce the numpy input functions."""
     import torch
 
-    from workloads.device import erf_cluster_potential_t, kb_couplings, kb_projector_values_t
+    from workloads.device import (erf_cluster_potential_t, gaussian_atom_density_t, kb_couplings,
+                                  kb_projector_values_t)
     u = W.uniform(99, 3 * 500).reshape(500, 3) * 12.0 - 6.0
     u[0] = [0.0, 0.0, 0.0]          # on an atom: series branch
     atoms = W.place_atoms(98, 5, 4.0, 2.0)
@@ -72,3 +73,6 @@ def test_torch_generators_equal_numpy_ones():
     p_t = kb_projector_values_t(torch.tensor(u), atoms, rc=1.0, first=1, count=3).numpy()
     assert np.max(np.abs(p_np[4:16] - p_t)) <= 1e-14
     assert np.array_equal(h_np, kb_couplings(5))
+    r_np = W.gaussian_atom_density(u, atoms, 4.0, 1.0)
+    r_t = gaussian_atom_density_t(torch.tensor(u), atoms, 4.0, 1.0).numpy()
+    assert np.max(np.abs(r_np - r_t)) <= 1e-14 * np.max(r_np)

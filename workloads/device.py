@@ -51,3 +51,15 @@ def kb_projector_values_t(xyz, atoms: np.ndarray, rc: float = 1.0, first: int = 
 def kb_couplings(natoms: int) -> np.ndarray:
     """Couplings of the projectors above (s: +1.0 Ha, p: +0.5 Ha; synthetic values)."""
     return np.tile(np.array([1.0, 0.5, 0.5, 0.5]), natoms)
+
+
+def gaussian_atom_density_t(xyz, atoms: np.ndarray, Z: float = 4.0, sigma: float = 1.0):
+    """SCF starting density of `gaussian_atom_density` (Z electrons per atom in a normalised
+    Gaussian of width sigma) at the points xyz (torch, (n, 3), float64)."""
+    import torch
+    rho = torch.zeros(xyz.shape[0], dtype=torch.float64, device=xyz.device)
+    c = Z * (2.0 * math.pi * sigma * sigma) ** -1.5
+    for a in torch.tensor(np.asarray(atoms, dtype=np.float64), device=xyz.device):
+        d2 = torch.sum((xyz - a) ** 2, dim=1)
+        rho += c * torch.exp(-d2 / (2.0 * sigma * sigma))
+    return rho
