@@ -20,7 +20,9 @@
 // at most one item. The Legendre rows of a chunk come pre-transposed ([packed (m,l)][pair])
 // from a table built at set-up, followed by the phi tables in their shared-memory layouts, so
 // staging either is a contiguous copy. The W V rows of a chunk are staged in the AP region
-// (free until stage C) before stage A.
+// (free until stage C) before stage A. Both come from registers loaded during the previous
+// chunk's stages C and D, so their global-memory latency overlaps that work; the state
+// tile of G is fetched in a single round of loads.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,6 +37,9 @@ constexpr int kGmST = 8;     // states per CTA
 constexpr int kGmRC = 8;     // mirrored row pairs per chunk
 constexpr int kGmItems = 2;  // Legendre-quadrature items per thread (up to 512 per CTA)
 constexpr int kGmLq = 5;     // l per Legendre-quadrature item
+constexpr int kGmPtRegs = 5;  // float4 of a chunk's Legendre rows per thread ((528+4) 8 / 4 / 256)
+constexpr int kGmWvRegs = 8;  // W V values of a chunk per thread (16 (4 Q4 + 3) / 256, Q4 <= 31)
+constexpr int kGmGRegs = 32;  // G-tile values per thread (32^2 8 / 256)
 
 __host__ __device__ inline int gm_round4(int x) { return (x + 3) & ~3; }
 
@@ -95,7 +100,10 @@ __host__ __device__ inline int gm_items(int L) {
 __host__ __device__ inline bool gm_eligible(int L, int Q4, int n_theta) {
   const GmShape g = gm_shape(L, Q4, n_theta);
   return gm_smem_bytes(L, Q4, n_theta) <= 227 * 1024 && gm_items(L) <= kGmItems * kGmThreads &&
-         (size_t)2 * kGmRC * (4 * Q4 + 4) <= (size_t)g.M2 * g.NC;
+         (size_t)2 * kGmRC * (4 * Q4 + 4) <= (size_t)g.M2 * g.NC &&
+         (g.RL + 4) * kGmRC / 4 <= kGmPtRegs * kGmThreads &&
+         2 * kGmRC * (4 * Q4 + 3) <= kGmWvRegs * kGmThreads &&
+         L * L * kGmST <= kGmGRegs * kGmThreads;
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -111,7 +119,7 @@ __device__ __forceinline__ void unpack4(const float4 v, float* o) {
 
 __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float* __restrict__ G,
                                                  int k, int s0, unsigned char* smem_raw) {
-  constexpr int ST = kGmST, RC = kGmRC, NC = 2 * RC * ST, NB = 8;
+  constexpr int ST = kGmST, RC = kGmRC, NC = 2 * RC * ST;
   const int L = a.L, lmax = L - 1, L2 = L * L, M2 = 2 * L - 1;
   const int Np = a.n_phi, h = Np / 2, Q4 = a.Q4;
   const int Nt = a.n_theta, S = a.S, NP = (Nt + 1) / 2;
@@ -141,17 +149,46 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
     const int n4 = (int)(gm_trig_elems(L, Q4) / 4);
     for (int i = tid; i < n4; i += kGmThreads) dst[i] = src[i];
   }
-  for (int b0 = 0; b0 < L2 * ST; b0 += NB * kGmThreads) {
-    float v[NB];
+  const float* wvk = a.wv + (size_t)k * Nt * Np;
+  // the next chunk's Legendre rows and W V rows, held in registers until they are stored
+  float4 pt_reg[kGmPtRegs];
+  float wv_reg[kGmWvRegs];
+  auto fetch_chunk = [&](int c, int chn) {
+    const float4* src = reinterpret_cast<const float4*>(a.theta_pairs + (size_t)chn * (RL + 4) * RC);
+    const int n4 = (RL + 4) * RC / 4;
 #pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      const int i = b0 + u * kGmThreads + tid;
+    for (int u = 0; u < kGmPtRegs; ++u) {
+      const int i = u * kGmThreads + tid;
+      if (i < n4) pt_reg[u] = src[i];
+    }
+    const int n = RC * 2 * Np;
+#pragma unroll
+    for (int u = 0; u < kGmWvRegs; ++u) {
+      const int i = u * kGmThreads + tid;
+      float v = 0.f;
+      if (i < n) {
+        const int pr = i / Np, q = i - pr * Np;
+        const int p = pr >> 1, r = pr & 1;
+        const int jp = c + p;
+        const int row = r ? Nt - 1 - jp : jp;
+        if (jp < NP && (r == 0 || row != jp)) v = wvk[(size_t)row * Np + q];
+      }
+      wv_reg[u] = v;
+    }
+  };
+  // the state tile of G in one round of loads, together with the first chunk's rows
+  {
+    float v[kGmGRegs];
+#pragma unroll
+    for (int u = 0; u < kGmGRegs; ++u) {
+      const int i = u * kGmThreads + tid;
       const int lm = i / ST, s = i - lm * ST;
       v[u] = (i < L2 * ST && s < ns) ? G[((size_t)k * L2 + lm) * S + s0 + s] : 0.f;
     }
+    fetch_chunk(0, 0);
 #pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      const int i = b0 + u * kGmThreads + tid;
+    for (int u = 0; u < kGmGRegs; ++u) {
+      const int i = u * kGmThreads + tid;
       if (i < L2 * ST) {
         Gs[i] = v[u];
         Ga[i] = 0.f;
@@ -194,41 +231,25 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
       item_code[u] = (r < ge) ? (lo | (r << 9)) : (lo | (1 << 8) | ((r - ge) << 9));
     }
   }
-  const float* wvk = a.wv + (size_t)k * Nt * Np;
 
   for (int c0 = 0, ch = 0; c0 < NP; c0 += RC, ++ch) {
     __syncthreads();  // previous chunk's stage D done with PT and AP
-    // ---- Legendre rows of the chunk (pre-transposed table): contiguous float4 copy
+    // ---- the chunk's Legendre rows (pre-transposed table) and its pairs' W V rows into the
+    //      AP region (unused until stage C): WVs[p][r][q], r = 0 row j = c0 + p, r = 1 its
+    //      mirror; zero where absent. Both were fetched into registers earlier.
     {
-      const float4* src = reinterpret_cast<const float4*>(a.theta_pairs + (size_t)ch * (RL + 4) * RC);
       float4* dst = reinterpret_cast<float4*>(PT);
       const int n4 = (RL + 4) * RC / 4;
-      for (int b0 = 0; b0 < n4; b0 += 4 * kGmThreads) {
-        float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = b0 + u * kGmThreads + tid;
-          if (i < n4) v[u] = src[i];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = b0 + u * kGmThreads + tid;
-          if (i < n4) dst[i] = v[u];
-        }
+      for (int u = 0; u < kGmPtRegs; ++u) {
+        const int i = u * kGmThreads + tid;
+        if (i < n4) dst[i] = pt_reg[u];
       }
-    }
-    // ---- W V rows of the chunk's pairs into the AP region (unused until stage C):
-    //      WVs[p][r][q], r = 0 row j = c0 + p, r = 1 its mirror; zero where absent
-    {
-      float* WVs = AP;
       const int n = RC * 2 * Np;
-      for (int i = tid; i < n; i += kGmThreads) {
-        const int pr = i / Np, q = i - pr * Np;
-        const int p = pr >> 1, r = pr & 1;
-        const int jp = c0 + p;
-        const int row = r ? Nt - 1 - jp : jp;
-        const bool ok = jp < NP && (r == 0 || row != jp);
-        WVs[i] = ok ? wvk[(size_t)row * Np + q] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kGmWvRegs; ++u) {
+        const int i = u * kGmThreads + tid;
+        if (i < n) AP[i] = wv_reg[u];
       }
     }
     __syncthreads();
@@ -383,6 +404,8 @@ __device__ __forceinline__ void angular_gm_block(const AngArgs<float>& a, float*
       }
     }
     __syncthreads();
+    // the next chunk's rows: their loads run while stages C and D compute
+    if (c0 + RC < NP) fetch_chunk(c0 + RC, ch + 1);
     // ---- C: phi quadrature of one parity class of modes per tile, combined over the mirror
     //      rows: AP[m][p][0] = A_j + A_jb, AP[m][p][1] = A_j - A_jb. Warp tile = 4 mode
     //      blocks x 8 column blocks.
