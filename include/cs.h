@@ -217,6 +217,28 @@ cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degre
                         double b, double a0, cs_precision prec, double* theta, double* resid,
                         void* work, cs_stream stream);
 
+/* LOBPCG (Sec. 3.1) with the diagonal Teter-Payne-Allan preconditioner (Sec. 3.1.2), FP64:
+ * the lowest n_s eigenpairs of H from the block X (DEVICE FP64 d x n_s, ld; Ritz vectors on
+ * exit). Each iteration runs Rayleigh-Ritz on [X, W, P]:
+ *   - W: the preconditioned residuals of the columns whose residual is above tol (soft
+ *     locking), made orthogonal to X and orthonormalised (Cholesky-QR twice, column scaling);
+ *   - P: the previous search directions, orthonormalised.
+ * Convergence: the largest residual norm of the n_want lowest pairs <= tol.
+ * A Cholesky breakdown discards the iteration and restarts from the current Ritz vectors (W
+ * and P dropped).
+ * precondition = 0 switches the preconditioner off. The preconditioner scales coefficient
+ * alpha of a residual column y by
+ *   (27 + 18g + 12g^2 + 8g^3) / (27 + 18g + 12g^2 + 8g^3 + 16g^4),
+ *   g = Lambda_alpha / (1/2 sum Lambda y^2 / sum y^2).
+ * theta, resid: DEVICE n_s doubles. *iters receives the iteration count and *restarts the
+ * restarts (either may be NULL). work: DEVICE, cs_lobpcg_workspace_bytes(ctx, n_s) bytes.
+ * Synchronising. CS_ERR_NOT_CONVERGED after max_iter iterations (results written);
+ * CS_ERR_CHOLESKY if the starting block is rank deficient. */
+cs_status cs_lobpcg_workspace_bytes(const cs_ctx* ctx, int n_s, size_t* bytes);
+cs_status cs_lobpcg(cs_ctx* ctx, int n_s, int n_want, double* X, long long ld, double tol,
+                    int max_iter, int precondition, double* theta, double* resid, int* iters,
+                    int* restarts, void* work, cs_stream stream);
+
 /* Measurement hooks: between cs_profile_begin and cs_profile_end the library records a
  * CUDA event pair on the launching stream around every kernel it launches on ctx.
  * cs_profile_end synchronises, and writes per kernel class the summed device time

@@ -115,6 +115,8 @@ typedef struct {
   int first_max_iter;        /* ChFSI iterations allowed in the first solve */
   int lanczos_k;             /* Lanczos steps of the filter's upper bound, 1 .. 64 */
   double e_ion;              /* constant added to the energy (ion-ion interaction) */
+  int first_solver;          /* eigensolver of the first iteration: 0 ChFSI, 1 LOBPCG with the
+                                Teter-Payne-Allan preconditioner (Sec. 3.1) */
 } cs_scf_params;
 
 typedef struct {
@@ -142,9 +144,10 @@ cs_status cs_scf_work_bytes(const cs_scf* s, size_t* bytes);
 
 /* One SCF iteration on the block X (DEVICE FP64 d x n_s, ld).
  * 1. Set the potential v_in (cs_set_potential).
- * 2. Eigensolve. The first iteration runs cs_chfsi to first_tol from the block as given.
- *    Later ones run one cs_chfsi_step with a = the previous largest Ritz value,
- *    a0 = the previous smallest, and b from lanczos_k Lanczos steps.
+ * 2. Eigensolve. The first iteration runs cs_chfsi (first_solver 0) or cs_lobpcg
+ *    (first_solver 1) to first_tol from the block as given. Later ones run one
+ *    cs_chfsi_step with a = the previous largest Ritz value, a0 = the previous smallest, and
+ *    b from lanczos_k Lanczos steps.
  * 3. Fermi-Dirac occupations, then the output density rho, V_H[rho] and the LDA.
  * 4. The free energy
  *      E = 2 sum f lambda - int rho (v_in - v_ext) + 1/2 int rho V_H + int rho eps_xc

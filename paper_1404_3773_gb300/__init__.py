@@ -29,6 +29,7 @@ __all__ = [
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
     "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
+    "cs_lobpcg_workspace_bytes", "cs_lobpcg",
     # SCF pieces (include/cs_scf.h)
     "CS_DENSITY_CHUNK", "CS_MIXER_MAX_HISTORY", "CS_GRID_INTEGRALS_MAX", "ScfParams",
     "ScfReport", "Mixer", "Scf", "cs_scf_workspace_bytes", "cs_density", "cs_hartree",
@@ -65,7 +66,8 @@ class ScfParams(ctypes.Structure):
                 ("filter_prec", ctypes.c_int), ("n_electrons", ctypes.c_double),
                 ("kT", ctypes.c_double), ("beta", ctypes.c_double), ("history", ctypes.c_int),
                 ("first_tol", ctypes.c_double), ("first_max_iter", ctypes.c_int),
-                ("lanczos_k", ctypes.c_int), ("e_ion", ctypes.c_double)]
+                ("lanczos_k", ctypes.c_int), ("e_ion", ctypes.c_double),
+                ("first_solver", ctypes.c_int)]
 
 
 class ScfReport(ctypes.Structure):
@@ -125,6 +127,9 @@ _SIGS = {
     "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
     "cs_launch_count": (_ll, [_vp]),
+    "cs_lobpcg_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_lobpcg": (_i, [_vp, _i, _i, _vp, _ll, _d, _i, _i, _vp, _vp, ctypes.POINTER(_i),
+                       ctypes.POINTER(_i), _vp, _vp]),
     # SCF pieces
     "cs_scf_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_density": (_i, [_vp, _i, _vp, _ll, _vp, _vp, _vp, _vp]),
@@ -569,6 +574,30 @@ def grid_points(ctx: Context):
     y = r[:, None, None] * st[None, :, None] * np.sin(ph)[None, None, :]
     z = r[:, None, None] * t[None, :, None] * np.ones_like(ph)[None, None, :]
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def cs_lobpcg_workspace_bytes(ctx: Context, n_s: int) -> int:
+    out = ctypes.c_size_t()
+    ctx.check(_lib.cs_lobpcg_workspace_bytes(ctx.handle, int(n_s), ctypes.byref(out)))
+    return out.value
+
+
+def cs_lobpcg(ctx: Context, X: torch.Tensor, n_want: int, theta: torch.Tensor,
+              resid: torch.Tensor, tol: float = 1e-8, max_iter: int = 200,
+              precondition: bool = True, work=None, stream=None,
+              raise_not_converged: bool = True):
+    """LOBPCG with the Teter-Payne-Allan preconditioner; returns (iterations, restarts)."""
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    if work is None:
+        work = torch.empty(cs_lobpcg_workspace_bytes(ctx, n_s), dtype=torch.uint8,
+                           device=f"cuda:{ctx.device}")
+    it, rs = _i(), _i()
+    st = _lib.cs_lobpcg(ctx.handle, n_s, int(n_want), _ptr(X), ld, float(tol), int(max_iter),
+                        1 if precondition else 0, _ptr(theta), _ptr(resid), ctypes.byref(it),
+                        ctypes.byref(rs), _ptr(work), _stream_ptr(stream))
+    if st != 0 and not (st == 6 and not raise_not_converged):
+        ctx.check(st)
+    return it.value, rs.value
 
 
 # ---------------------------------------------------------------------- SCF pieces

@@ -654,7 +654,7 @@ cs_status cs_scf_create(cs_ctx* c, const cs_scf_params* p, const double* v_ext,
   if (!p || !v_ext || !rho0 || !v0 || !out) return sfail(c, CS_ERR_ARG, "cs_scf_create: NULL argument");
   if (p->n_s < 1 || p->n_want < 1 || p->n_want > p->n_s || p->degree < 1 || !(p->kT > 0) ||
       !(0.5 * p->n_electrons > 0 && 0.5 * p->n_electrons < p->n_s) || p->lanczos_k < 1 ||
-      p->lanczos_k > 64 || p->first_max_iter < 1)
+      p->lanczos_k > 64 || p->first_max_iter < 1 || p->first_solver < 0 || p->first_solver > 1)
     return sfail(c, CS_ERR_ARG, "cs_scf_create: bad parameters");
   cs_scf* S = new cs_scf;
   S->ctx = c;
@@ -694,6 +694,11 @@ cs_status cs_scf_work_bytes(const cs_scf* S, size_t* bytes) {
   cs_workspace_bytes(S->ctx, S->p.n_s, S->p.filter_prec, &a);
   cs_workspace_bytes(S->ctx, S->p.n_s, CS_FP64, &b);
   *bytes = std::max(std::max(a, b), scf_layout(S->ctx).total);
+  if (S->p.first_solver == 1) {
+    size_t l = 0;
+    cs_lobpcg_workspace_bytes(S->ctx, S->p.n_s, &l);
+    *bytes = std::max(*bytes, l);
+  }
   return CS_OK;
 }
 
@@ -718,8 +723,12 @@ cs_status cs_scf_step(cs_scf* S, double* X, long long ld, double* theta, double*
   if ((s = cs_set_potential(c, S->v_in, stream)) != CS_OK) return s;
   int iters = 1;
   if (S->iteration == 0) {
-    s = cs_chfsi(c, p.n_s, p.n_want, X, ld, p.degree, p.first_tol, p.first_max_iter,
-                 p.filter_prec, S->v0, theta, resid, &iters, work, stream);
+    if (p.first_solver == 1)
+      s = cs_lobpcg(c, p.n_s, p.n_want, X, ld, p.first_tol, p.first_max_iter, 1, theta, resid,
+                    &iters, nullptr, work, stream);
+    else
+      s = cs_chfsi(c, p.n_s, p.n_want, X, ld, p.degree, p.first_tol, p.first_max_iter,
+                   p.filter_prec, S->v0, theta, resid, &iters, work, stream);
     if (s != CS_OK && s != CS_ERR_NOT_CONVERGED) return s;
   } else {
     double b = 0.0, tmin = 0.0;
