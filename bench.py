@@ -383,6 +383,7 @@ def run_ours(args):
     batched = None if args.no_batched else batched_measure(dev)
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
     scf = None if args.no_scf else scf_measure(dev)
+    first_solve = None if args.no_scf else first_solve_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
@@ -411,6 +412,7 @@ def run_ours(args):
         "batched": batched,
         "at_scale": at_scale,
         "scf": scf,
+        "first_solve": first_solve,
         "clocks": clocks.summary(),
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
@@ -509,6 +511,57 @@ def scf_measure(dev, precisions=("fp32", "fp64"), tol=1e-6, max_iter=80):
         ctx.close()
     if "fp32" in out and "fp64" in out:
         out["fp32_energy_minus_fp64"] = out["fp32"]["energy"] - out["fp64"]["energy"]
+    return out
+
+
+def first_solve_measure(dev, tol=1e-4, n_want=64):
+    """The first eigensolve of an SCF on the 32-atom cluster (fixed potential, the seeded random
+    block of 80 states): time and iterations until the 64 lowest residuals are <= tol, for
+    LOBPCG with and without the Teter-Payne-Allan preconditioner (FP64) and for ChFSI with the
+    FP64 and the FP32 filter (double-float Rayleigh-Ritz)."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t
+    w = W.erf_cluster_32()
+    idx = torch.device(dev).index or 0
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, idx)
+    xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, w.atoms(), w.extra["Z"],
+                                                     w.extra["rc"]).contiguous())
+    X0 = torch.tensor(W.gaussian_block(w.x_seed, w.d, w.n_s).T.copy(), device=dev)
+    v0 = torch.tensor(W.gaussian(17, ctx.d), device=dev)
+    theta = torch.empty(w.n_s, dtype=torch.float64, device=dev)
+    resid = torch.empty_like(theta)
+    out = {"workload": f"erf32_l30_n48, fixed potential, 80 random states, stop when the "
+                       f"{n_want} lowest residuals are <= {tol:g}"}
+    for name, pre in (("lobpcg_tpa", True), ("lobpcg_none", False)):
+        X = X0.clone()
+        work = torch.empty(cs.cs_lobpcg_workspace_bytes(ctx, w.n_s), dtype=torch.uint8,
+                           device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rs = cs.cs_lobpcg(ctx, X, n_want, theta, resid, tol=tol, max_iter=150,
+                              precondition=pre, work=work, raise_not_converged=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out[name] = {"seconds": round(sec, 3), "iterations": it, "restarts": rs,
+                     "max_resid": float(resid[:n_want].max())}
+        del work
+    for name, prec, rr in (("chfsi_fp64", cs.CS_FP64, cs.CS_FP64),
+                           ("chfsi_fp32_rr_df64", cs.CS_FP32, cs.CS_DF64)):
+        cs.cs_set_rr_precision(ctx, rr)
+        cs.cs_set_dense_precision(ctx, rr)
+        X = X0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = cs.cs_chfsi(ctx, X, n_want, w.degree, v0, theta, resid, tol=tol, max_iter=60,
+                         precision=prec, raise_not_converged=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out[name] = {"seconds": round(sec, 3), "iterations": it,
+                     "max_resid": float(resid[:n_want].max())}
+    ctx.close()
     return out
 
 

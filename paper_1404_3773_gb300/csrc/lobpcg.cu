@@ -151,7 +151,13 @@ LbLayout lb_layout(const cs_ctx* c, int m) {
   o.U2 = take(n3 * n3 * 8);
   o.eigw = take((8 * n3 * n3 + 3 * n3 + 4) * 8);
   o.cholw = take((n3 * n3 + 2 * n3) * 8);
-  o.part = take(gram_partial_elems((long long)d, (int)n3, (int)n3) * 8);
+  // the partial buffer of a Gram grows with the number of row chunks, which is larger for
+  // narrow products: size it for every shape up to 3m x 3m
+  size_t pe = 0;
+  for (int na = 1; na <= (int)n3; ++na)
+    for (int nb = 1; nb <= (int)n3; ++nb)
+      pe = std::max(pe, gram_partial_elems((long long)d, na, nb));
+  o.part = take(pe * 8);
   o.norms = take((size_t)m * 8);
   o.theta = take(n3 * 8);
   o.th2 = take((size_t)m * 8);

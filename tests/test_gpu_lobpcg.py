@@ -55,3 +55,25 @@ def test_lobpcg_large_block():
     it, rs = cs.cs_lobpcg(ctx, X, 40, theta, resid, tol=1e-8, max_iter=400)
     assert np.max(np.abs(theta.cpu().numpy()[:40] - lam[:40])) <= 1e-9
     assert np.max(resid.cpu().numpy()[:40]) <= 1e-8
+
+
+def test_lobpcg_on_a_larger_basis_matches_chfsi():
+    """d = 4056, 40 states: the narrow Gram products of an iteration split d into more row
+    chunks than the widest one, so their partial sums need more room (the workspace is sized
+    for every shape); eigenvalues equal those of a tightly converged FP64 ChFSI."""
+    torch, cs = need_gpu()
+    w = W.small_cluster(lmax=12, nmax=24, n_r=48, n_theta=26, n_phi=50, n_s=40, seed=7321,
+                        R=10.0, natoms=4)
+    ctx = make_ctx(w)
+    d = ctx.d
+    X0 = torch.tensor(W.gaussian_block(7322, d, 40).T.copy(), device="cuda")
+    theta = torch.empty(40, dtype=torch.float64, device="cuda")
+    resid = torch.empty_like(theta)
+    X = X0.clone()
+    it, rs = cs.cs_lobpcg(ctx, X, 32, theta, resid, tol=1e-8, max_iter=300)
+    assert rs == 0
+    th_lb = theta.cpu().numpy()[:32].copy()
+    v0 = torch.tensor(W.gaussian(7323, d), device="cuda")
+    X = X0.clone()
+    cs.cs_chfsi(ctx, X, 32, 16, v0, theta, resid, tol=1e-9, max_iter=200)
+    assert np.max(np.abs(th_lb - theta.cpu().numpy()[:32])) <= 1e-9
