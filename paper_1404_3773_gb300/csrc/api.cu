@@ -240,13 +240,15 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   TcTables tt;
   tt.synth = c->tc_synth;
   tt.anal = c->tc_anal;
-  tt.m_tiles_synth = c->tc_mt_synth;
+  tt.rows_synth = c->tc_rows_synth;
   tt.kpad_synth = c->tc_kpad_synth;
-  tt.m_tiles_anal = c->tc_mt_anal;
+  tt.rows_anal = c->tc_rows_anal;
   tt.kpad_anal = c->tc_kpad_anal;
   if (tc && !std::is_same<T, float>::value)
     return fail(c, CS_ERR_ARG, "tensor-core path needs float blocks");
-  if (tc) {
+  // radial dimensions above the MMA's N limit take the FP32 tiles
+  const bool tc_rad = tc && tc_radial_fits(H);
+  if (tc_rad) {
     CS_LAUNCH_CLS(c, prof_cls<T>(0), 1, launch_tc_radial_synth(tt, H, reinterpret_cast<const float*>(X), ldx,
                                                   reinterpret_cast<float*>(G), n_s, c->dev_err,
                                                   st));
@@ -269,7 +271,7 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   ep.cA = (T)cA;
   ep.cB = (T)cB;
   ep.cshift = (T)csh;
-  if (tc) {
+  if (tc_rad) {
     CS_LAUNCH_CLS(c, prof_cls<T>(2), 1, launch_tc_radial_anal(tt, H, reinterpret_cast<const float*>(G), n_s,
                                                  *reinterpret_cast<const Epilogue<float>*>(&ep),
                                                  c->dev_err, st));
@@ -495,10 +497,10 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
             cudaMemcpy(*dst, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
           st = CS_ERR_ALLOC;
         if (mode == 0) {
-          c->tc_mt_synth = mt;
+          c->tc_rows_synth = mt;
           c->tc_kpad_synth = kp;
         } else {
-          c->tc_mt_anal = mt;
+          c->tc_rows_anal = mt;
           c->tc_kpad_anal = kp;
         }
       }

@@ -34,7 +34,7 @@ std::string build_host_tables(double R, int lmax, int nmax, const cs_quadrature&
                               HostTables& out);
 
 // split-BF16 radial tables for the tensor-core path (tc_radial.cu); mode 0 synthesis, 1 analysis
-void build_tc_tables(const HostTables& H, int mode, std::vector<uint16_t>& out, int& m_tiles,
+void build_tc_tables(const HostTables& H, int mode, std::vector<uint16_t>& out, int& rows,
                      int& kpad);
 
 // packed offset of (m, l) inside one theta row: sum_{m'<m} (L - m') + (l - m)
@@ -73,7 +73,7 @@ struct cs_ctx {
   double* hartree_tab = nullptr;  // k_ln = z_ln / R ([l][n]) then r_k / R ([k]) (scf.cu)
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
-  int tc_mt_synth = 0, tc_kpad_synth = 0, tc_mt_anal = 0, tc_kpad_anal = 0;
+  int tc_rows_synth = 0, tc_kpad_synth = 0, tc_rows_anal = 0, tc_kpad_anal = 0;
   void* kb_tabA = nullptr;   // split-BF16 projector operands (kb_tc.cu), set with the projectors
   void* kb_tabB = nullptr;
   int* dev_err = nullptr;    // device error word (bounded waits); 0 = ok

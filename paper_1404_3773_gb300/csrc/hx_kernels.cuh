@@ -73,10 +73,12 @@ cudaError_t launch_radial_anal(const T* G, const T* rad, int L, int N, int n_r, 
 struct HostTables;
 // split-BF16 radial tables in the canonical tcgen05 operand layout (tc_radial.cu)
 struct TcTables {
-  const void* synth = nullptr;  // __nv_bfloat16, [l][m tile][k chunk][hi|lo][128 x 64]
+  const void* synth = nullptr;  // __nv_bfloat16, [l][k chunk][hi|lo][rows x 64]
   const void* anal = nullptr;
-  int m_tiles_synth = 0, kpad_synth = 0, m_tiles_anal = 0, kpad_anal = 0;
+  int rows_synth = 0, kpad_synth = 0, rows_anal = 0, kpad_anal = 0;
 };
+// whether both radial tables fit the tensor-core kernels (radial dimensions <= 256)
+bool tc_radial_fits(const HostTables& H);
 cudaError_t launch_tc_radial_synth(const TcTables& tt, const HostTables& H, const float* X,
                                    long long ldx, float* G, int S, int* err,
                                    cudaStream_t stream);
