@@ -123,31 +123,42 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
                bar_tma);
     }
     // stage A (TC rows = state columns, KC K-elements) as split BF16
+    // every load of the chunk is issued before any value is converted, so that a thread
+    // has all of them in flight at once (the epilogue's stores may alias the inputs, which
+    // keeps the compiler from reordering loads past stores by itself)
+    constexpr int NT = TC * (KC / 8) / kThreads;  // tasks (8 values each) per thread
+    static_assert(NT == 8, "one column (analysis) or one octet of 8 columns (synthesis)");
+    float v[NT][8];
     if (MODE == 0) {
-      // A[c][n] = X[(l^2 + mi) N + n + s ldx]; task = (column, octet of n)
-      for (int t = tid; t < TC * (KC / 8); t += kThreads) {
-        const int oc = t % (KC / 8), cc = t / (KC / 8);
-        const int c = c0 + cc, n0 = kb + oc * 8;
-        float v[8];
+      // A[c][n] = X[(l^2 + mi) N + n + s ldx]; task = (column cc, octet oc of n)
+      const int oc = tid % (KC / 8), n0 = kb + oc * 8;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      for (int u = 0; u < NT; ++u) {
+        const int cc = tid / (KC / 8) + u * (kThreads / (KC / 8));
+        const int c = c0 + cc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[u][i] = 0.f;
         if (c < ncol) {
           const int mi = c / sh.S, s = c - mi * sh.S;
           const float* src = X + (size_t)(l * l + mi) * sh.N + (size_t)s * ldx + n0;
           if (vec_ok && n0 + 8 <= Kdim) {  // two 16-byte loads (aligned: N, ldx, n0 multiples of 4)
             const float4 a = *reinterpret_cast<const float4*>(src);
             const float4 b = *reinterpret_cast<const float4*>(src + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+            v[u][4] = b.x; v[u][5] = b.y; v[u][6] = b.z; v[u][7] = b.w;
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-              if (n0 + i < Kdim) v[i] = src[i];
+              if (n0 + i < Kdim) v[u][i] = src[i];
           }
         }
+      }
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        const int cc = tid / (KC / 8) + u * (kThreads / (KC / 8));
         __align__(16) __nv_bfloat16 h[8], lo[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) split_bf16(v[i], h[i], lo[i]);
+        for (int i = 0; i < 8; ++i) split_bf16(v[u][i], h[i], lo[i]);
         const int off = canon_off(cc, oc * 8, TC);
         *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Ahi) + off) =
             *reinterpret_cast<uint4*>(h);
@@ -155,18 +166,21 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
             *reinterpret_cast<uint4*>(lo);
       }
     } else {
-      // A[c][k] = G[(k L^2 + l^2) S + c]; lanes over columns, loop over the k octet
-      for (int t = tid; t < TC * (KC / 8); t += kThreads) {
-        const int cc = t % TC, oc = t / TC;
-        const int c = c0 + cc, k0 = kb + oc * 8;
-        __align__(16) __nv_bfloat16 h[8], lo[8];
+      // A[c][k] = G[(k L^2 + l^2) S + c]; thread = column cc = tid, all eight k octets
+      const int cc = tid, c = c0 + cc;
+#pragma unroll
+      for (int u = 0; u < NT; ++u)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          float x = 0.f;
-          if (c < ncol && k0 + i < Kdim) x = G[((size_t)(k0 + i) * L2 + l * l) * sh.S + c];
-          split_bf16(x, h[i], lo[i]);
+          const int k = kb + u * 8 + i;
+          v[u][i] = (c < ncol && k < Kdim) ? G[((size_t)k * L2 + l * l) * sh.S + c] : 0.f;
         }
-        const int off = canon_off(cc, oc * 8, TC);
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        __align__(16) __nv_bfloat16 h[8], lo[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) split_bf16(v[u][i], h[i], lo[i]);
+        const int off = canon_off(cc, u * 8, TC);
         *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Ahi) + off) =
             *reinterpret_cast<uint4*>(h);
         *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Alo) + off) =
@@ -246,20 +260,21 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
             ep.kb ? reinterpret_cast<const float4*>(ep.kb + a + (size_t)s * ep.kb_ld) : nullptr;
         const float4* y4 =
             ep.Yprev ? reinterpret_cast<const float4*>(ep.Yprev + o) : nullptr;
+        // all loads of the run first (out may alias Yprev: no store before the last load)
+        float4 xv[4], hv[4], kv[4], yv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          float xs[4], hs[4], ks[4] = {0.f, 0.f, 0.f, 0.f}, ys[4] = {0.f, 0.f, 0.f, 0.f};
-          const float4 xv = x4[q], hv = h4[q];
-          xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
-          hs[0] = hv.x; hs[1] = hv.y; hs[2] = hv.z; hs[3] = hv.w;
-          if (k4) {
-            const float4 kv = k4[q];
-            ks[0] = kv.x; ks[1] = kv.y; ks[2] = kv.z; ks[3] = kv.w;
-          }
-          if (y4 && ep.mode != EP_APPLY) {
-            const float4 yv = y4[q];
-            ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
-          }
+          xv[q] = x4[q];
+          hv[q] = h4[q];
+          kv[q] = k4 ? k4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          yv[q] = (y4 && ep.mode != EP_APPLY) ? y4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float xs[4] = {xv[q].x, xv[q].y, xv[q].z, xv[q].w};
+          const float hs[4] = {hv[q].x, hv[q].y, hv[q].z, hv[q].w};
+          const float ks[4] = {kv[q].x, kv[q].y, kv[q].z, kv[q].w};
+          const float ys[4] = {yv[q].x, yv[q].y, yv[q].z, yv[q].w};
           float r[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
