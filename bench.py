@@ -1,14 +1,18 @@
 """Benchmark: ChFSI H.X applies/s on the 32-atom erf cluster (lmax 30, 48 radial functions,
 d = 46128, 96 x 60 x 120 grid, 80 states, Chebyshev degree 16) on one GB300.
 
-A step is one ChFSI iteration (Sec. 3.2.1): the degree-16 Chebyshev filter (16 H.X block
-products in the chosen precision, three-term recurrence fused into the H.X epilogue),
-Cholesky-QR (two passes, FP64) and Rayleigh-Ritz (one FP64 H.X, Gram, Jacobi eigensolve,
-rotations, residual norms). value = state-columns multiplied by H per second
-= (degree + 1) * n_s / step time, summed over ranks (each rank runs its own block:
-weak scaling, no collective on the data path).
+A step is one ChFSI iteration (Sec. 3.2.1):
+  - the degree-16 Chebyshev filter: 16 H.X block products in the chosen precision, with the
+    three-term recurrence fused into the H.X epilogue. The default is the mixed form:
+    split-BF16 tensor-core radial contractions and FP32 transforms;
+  - Cholesky-QR (two passes);
+  - Rayleigh-Ritz: one H.X, Gram, eigensolve, rotations and residual norms. By default the H.X
+    and the Gram matrices and rotations run in double-float (FP64-class); the factorisation,
+    eigensolve and residual norms run in FP64.
+value = state-columns multiplied by H per second = (degree + 1) * n_s / step time, summed over
+ranks (each rank runs its own block: weak scaling, no collective on the data path).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64|df64]
     python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 """
 from __future__ import annotations
@@ -89,7 +93,7 @@ def dense_flops(d, n):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of the kernel as it stands, on this workload; a class without a capture reports null
-NCU_TRAFFIC_BYTES = {"angular_f32": 32.413952e6 + 20.992e3}
+NCU_TRAFFIC_BYTES = {"angular_f32": 32.435712e6 + 26.624e3}
 
 
 def measured_peaks():
@@ -384,6 +388,7 @@ def run_ours(args):
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
     scf = None if args.no_scf else scf_measure(dev)
     first_solve = None if args.no_scf else first_solve_measure(dev)
+    eigen_gate = None if args.no_scf else eigen_gate_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
@@ -413,6 +418,7 @@ def run_ours(args):
         "at_scale": at_scale,
         "scf": scf,
         "first_solve": first_solve,
+        "eigen_gate": eigen_gate,
         "clocks": clocks.summary(),
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
@@ -452,7 +458,7 @@ def step_breakdown(classes, steps, degree, ms_per_step, prec, rr_prec):
             "roofline_ms": round(roof, 4), "roofline_frac": round(roof / ms_per_step, 4)}
 
 
-def scf_measure(dev, precisions=("fp32", "fp64"), tol=1e-6, max_iter=80):
+def scf_measure(dev, precisions=("mixed", "fp32", "fp64"), tol=1e-6, max_iter=80):
     """SCF time to |dE| <= tol Ha on the 32-atom cluster (Z = 4 erf pseudo-atoms, 128
     electrons, 80 states, degree 16): Gaussian starting density (sigma 1 bohr per atom),
     Fermi-Dirac kT = 6.3e-4 Ha (200 K), Anderson mixing of the effective potential (beta 0.3,
@@ -509,8 +515,9 @@ def scf_measure(dev, precisions=("fp32", "fp64"), tol=1e-6, max_iter=80):
                      "dE_history": [r["dE"] for r in reps]}
         S.close()
         ctx.close()
-    if "fp32" in out and "fp64" in out:
-        out["fp32_energy_minus_fp64"] = out["fp32"]["energy"] - out["fp64"]["energy"]
+    for name in precisions:
+        if name != "fp64" and "fp64" in out:
+            out[f"{name}_energy_minus_fp64"] = out[name]["energy"] - out["fp64"]["energy"]
     return out
 
 
@@ -561,6 +568,43 @@ def first_solve_measure(dev, tol=1e-4, n_want=64):
         sec = time.perf_counter() - t0
         out[name] = {"seconds": round(sec, 3), "iterations": it,
                      "max_resid": float(resid[:n_want].max())}
+    ctx.close()
+    return out
+
+
+def eigen_gate_measure(dev):
+    """The mixed form's acceptance gate on the 32-atom cluster: ChFSI from the seeded block
+    with the all-FP64 path to residuals of 1e-8, then with the bench's filter precisions
+    (double-float Rayleigh-Ritz and Gram/rotations) for as many iterations as FP64 took plus
+    ten; the largest deviation of the 64 lowest Ritz values from FP64 (gate: 1e-6 Ha)."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t
+    w = W.erf_cluster_32()
+    idx = torch.device(dev).index or 0
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, idx)
+    xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, w.atoms(), w.extra["Z"],
+                                                     w.extra["rc"]).contiguous())
+    X0 = torch.tensor(W.gaussian_block(w.x_seed, w.d, w.n_s).T.copy(), device=dev)
+    v0 = torch.tensor(W.gaussian(2003, ctx.d), device=dev)
+    th64 = torch.empty(w.n_s, dtype=torch.float64, device=dev)
+    r64 = torch.empty_like(th64)
+    it64 = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, th64, r64, tol=1e-8,
+                       max_iter=80, precision=cs.CS_FP64)
+    out = {"workload": "erf32_l30_n48 ChFSI from the seeded block, 64 lowest Ritz values",
+           "fp64_iterations": it64, "gate_ha": 1e-6}
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+    for name, prec in (("mixed", cs.CS_MIXED_BF16), ("fp32", cs.CS_FP32)):
+        th = torch.empty_like(th64)
+        rr = torch.empty_like(th64)
+        it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, th, rr, tol=1e-8,
+                         max_iter=it64 + 10, precision=prec, raise_not_converged=False)
+        dmax = float(np.max(np.abs(th.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want])))
+        out[name] = {"iterations": it, "max_dev_vs_fp64_ha": dmax,
+                     "max_resid": float(rr[:w.n_want].max()), "within_gate": dmax < 1e-6}
     ctx.close()
     return out
 
@@ -782,7 +826,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "mixed", "df64"],
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed", "df64"],
                     help="filter precision")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
