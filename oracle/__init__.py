@@ -19,6 +19,9 @@ primitives:
                     H for tiny bases (eq. Hij_def)
   eigen.py        - scaled Chebyshev filter, Cholesky-QR with column scaling, Rayleigh-
                     Ritz, Lanczos bound and the ChFSI loop (Sec. 3.1.1, 3.2, 3.2.1)
+  lobpcg.py       - LOBPCG with the Teter-Payne-Allan preconditioner (Sec. 3.1)
+  learned_density.py - per-atom radial descriptors, fitted atom-centred density
+                    corrections, a small MLP with Adam, and the predicted starting density
   scf.py          - electron density, Hartree potential (eqs. hartree_calc1,
                     zeta_definition), LDA exchange-correlation, Fermi-Dirac occupations,
                     Anderson mixing and the SCF loop (Sec. 2.1, 2.2.5, 2.3.1, 3.4.1)
