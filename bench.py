@@ -389,6 +389,7 @@ def run_ours(args):
     scf = None if args.no_scf else scf_measure(dev)
     first_solve = None if args.no_scf else first_solve_measure(dev)
     eigen_gate = None if args.no_scf else eigen_gate_measure(dev)
+    learned_init = None if args.no_scf else learned_init_measure(dev)
     cpu = cpu_baseline(w, budget_s=args.cpu_seconds) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "applies/s", "n_gpus": world,
@@ -419,6 +420,7 @@ def run_ours(args):
         "scf": scf,
         "first_solve": first_solve,
         "eigen_gate": eigen_gate,
+        "learned_init": learned_init,
         "clocks": clocks.summary(),
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
@@ -607,6 +609,124 @@ def eigen_gate_measure(dev):
                      "max_resid": float(rr[:w.n_want].max()), "within_gate": dmax < 1e-6}
     ctx.close()
     return out
+
+
+def learned_init_measure(dev, n_train=48, n_test=16, tol=1e-6, hidden=128, steps=2000,
+                         ceiling=True):
+    """The learned initial density: small clusters of 4-12 Z=4 erf pseudo-atoms (R = 9, lmax 10,
+    16 radial functions, 32 x 22 x 42 grid), SCF (mixed filter) from the Gaussian start to
+    |dE| <= tol. On the training clusters, the converged density minus the start is fitted by
+    atom-centred Gaussians; a 16-128-128-128-5 tanh network learns the fitted coefficients
+    from the radial descriptors (Adam). On the held-out clusters, the SCF runs from the
+    Gaussian start, from the learned start, and (ceiling) from the cluster's own best-fit
+    correction; iterations and times are compared."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t, gaussian_atom_density_t
+    idx = torch.device(dev).index or 0
+    ctx = cs.cs_basis_init(9.0, 10, 16, 32, 22, 42, 0, idx)
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+    xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+    mu = np.linspace(2.0, 10.0, 16)
+    width = 0.5
+    sig = np.array([0.6, 0.9, 1.3, 1.9, 2.8])
+
+    def cluster(i):
+        natoms = 4 + int(9 * W.uniform(5000 + i, 1)[0])
+        return W.place_atoms(5100 + i, natoms, 3.5, 2.2)
+
+    def scf(atoms, rho0):
+        ne = 4.0 * len(atoms)
+        n_s = int(ne // 2) + 8
+        v_ext = erf_cluster_potential_t(xyz, atoms, 4.0, 0.8).contiguous()
+        p = cs.ScfParams(n_s=n_s, n_want=int(ne // 2), degree=12, filter_prec=cs.CS_MIXED_BF16,
+                         n_electrons=ne, kT=6.3e-4, beta=0.3, history=8, first_tol=1e-3,
+                         first_max_iter=40, lanczos_k=10, e_ion=0.0, first_solver=0)
+        S = cs.cs_scf_create(ctx, p, v_ext, rho0.contiguous(),
+                             torch.tensor(W.gaussian(17, ctx.d), device=dev))
+        X = torch.tensor(W.gaussian_block(18, ctx.d, n_s).T.copy(), device=dev)
+        th = torch.empty(n_s, dtype=torch.float64, device=dev)
+        rs = torch.empty_like(th)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = 0
+        for it in range(1, 101):
+            rep = cs.cs_scf_step(S, X, th, rs)
+            if it > 1 and abs(rep["dE"]) <= tol:
+                break
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        rho = cs.cs_scf_grid(S, 1)
+        S.close()
+        return it, sec, rho, rep["energy"]
+
+    # training data
+    D, C = [], []
+    for i in range(n_train):
+        atoms = cluster(i)
+        start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
+        _, _, rho, _ = scf(atoms, start)
+        C.append(cs.cs_fit_atom_density(ctx, atoms, sig, (rho - start).contiguous(), ridge=1e-8))
+        D.append(cs.cs_atom_descriptors(atoms, mu, width))
+    D, C = np.concatenate(D), np.concatenate(C)
+    d_mean, d_std = D.mean(axis=0), D.std(axis=0) + 1e-6
+    c_scale = float(np.abs(C).max()) or 1.0
+    dims = [16, hidden, hidden, hidden, len(sig)]
+    params = []
+    for k in range(len(dims) - 1):
+        params.append((W.gaussian_block(5200 + k, dims[k], dims[k + 1])
+                       / math.sqrt(dims[k])).ravel(order="F"))
+        params.append(np.zeros(dims[k + 1]))
+    net = cs.cs_mlp_create(dims, np.concatenate(params).astype(np.float32), max_rows=D.shape[0],
+                           cuda_device=idx)
+    Xd = torch.tensor(((D - d_mean) / d_std).T.copy(), dtype=torch.float32, device=dev)
+    Td = torch.tensor((C / c_scale).T.copy(), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    loss0 = cs.cs_mlp_train_step(net, Xd, Td, 1e-3)
+    for _ in range(steps):
+        cs.cs_mlp_train_step(net, Xd, Td, 1e-3, want_loss=False)
+    loss = cs.cs_mlp_loss_grad(net, Xd, Td)[0]
+    train_s = time.perf_counter() - t0
+    # held-out comparison
+    it_g, it_l, s_g, s_l, de, it_c = [], [], [], [], [], []
+    for i in range(n_train, n_train + n_test):
+        atoms = cluster(i)
+        start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
+        a, sa, rho_c, ea = scf(atoms, start)
+        if ceiling:  # start from this cluster's own best-fit correction
+            cfit = cs.cs_fit_atom_density(ctx, atoms, sig, (rho_c - start).contiguous(), ridge=1e-8)
+            fitted = start.clone()
+            cs.cs_atom_density(ctx, atoms, sig, cfit, fitted)
+            fitted *= 4.0 * len(atoms) / cs.cs_grid_integrals(ctx, [fitted])[0]
+            it_c.append(scf(atoms, fitted)[0])
+        desc = (cs.cs_atom_descriptors(atoms, mu, width) - d_mean) / d_std
+        coef = cs.cs_mlp_forward(net, torch.tensor(desc.T.copy(), dtype=torch.float32,
+                                                   device=dev)).cpu().numpy().T * c_scale
+        learned = start.clone()
+        cs.cs_atom_density(ctx, atoms, sig, coef.astype(np.float64), learned)
+        ne = 4.0 * len(atoms)
+        learned *= ne / cs.cs_grid_integrals(ctx, [learned])[0]
+        b, sb, _, eb = scf(atoms, learned)
+        it_g.append(a)
+        it_l.append(b)
+        s_g.append(sa)
+        s_l.append(sb)
+        de.append(abs(ea - eb))
+    net.close()
+    ctx.close()
+    return {"workload": f"{n_train} training + {n_test} held-out clusters of 4-12 Z=4 erf atoms "
+                        "(R 9, lmax 10, N 16, grid 32x22x42), mixed-filter SCF to "
+                        f"|dE| <= {tol:g} Ha",
+            "train_atoms": int(D.shape[0]), "train_loss_first": loss0, "train_loss_final": loss,
+            "train_seconds": round(train_s, 3),
+            "held_out_mean_iterations_gaussian_start": float(np.mean(it_g)),
+            "held_out_mean_iterations_learned_start": float(np.mean(it_l)),
+            "held_out_mean_seconds_gaussian_start": round(float(np.mean(s_g)), 4),
+            "held_out_mean_seconds_learned_start": round(float(np.mean(s_l)), 4),
+            "held_out_max_energy_difference_ha": float(np.max(de)),
+            "held_out_mean_iterations_own_fit_start": float(np.mean(it_c)) if it_c else None}
 
 
 def batched_measure(dev, reps=2):

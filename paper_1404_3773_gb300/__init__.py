@@ -36,6 +36,10 @@ __all__ = [
     "cs_lda_xc", "cs_grid_integrals", "cs_fermi_occupations", "cs_mixer_create",
     "cs_mixer_mix", "cs_mixer_reset", "cs_mixer_free", "cs_scf_create", "cs_scf_work_bytes",
     "cs_scf_step", "cs_scf_grid", "cs_scf_occupations", "cs_scf_free",
+    # learned initial density (include/cs_learned.h)
+    "Mlp", "cs_atom_descriptors", "cs_atom_density", "cs_fit_workspace_bytes",
+    "cs_fit_atom_density", "cs_mlp_create", "cs_mlp_free", "cs_mlp_param_count", "cs_mlp_params",
+    "cs_mlp_forward", "cs_mlp_loss_grad", "cs_mlp_train_step", "cs_mlp_last_error",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -145,6 +149,22 @@ _SIGS = {
     "cs_scf_work_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_scf_step": (_i, [_vp, _vp, _ll, _vp, _vp, _vp, _vp, ctypes.POINTER(ScfReport)]),
     "cs_scf_grid": (_i, [_vp, _i, _vp, _vp]),
+    # learned initial density
+    "cs_atom_descriptors": (_i, [_i, _dp, _i, _dp, _d, _dp]),
+    "cs_atom_density": (_i, [_vp, _i, _dp, _i, _dp, _dp, _vp, _vp]),
+    "cs_fit_workspace_bytes": (_i, [_vp, _i, _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_fit_atom_density": (_i, [_vp, _i, _dp, _i, _dp, _vp, _d, _dp, _vp, _vp]),
+    "cs_mlp_create": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float), _i, _i,
+                           ctypes.POINTER(_vp)]),
+    "cs_mlp_free": (_i, [_vp]),
+    "cs_mlp_param_count": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "cs_mlp_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "cs_mlp_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "cs_mlp_loss_grad": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float),
+                              ctypes.POINTER(ctypes.c_float), _vp]),
+    "cs_mlp_train_step": (_i, [_vp, _i, _vp, _vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                               _vp]),
+    "cs_mlp_last_error": (ctypes.c_char_p, [_vp]),
     "cs_scf_occupations": (_i, [_vp, _dp]),
     "cs_scf_free": (_i, [_vp]),
 }
@@ -802,3 +822,148 @@ def cs_scf_occupations(s: Scf):
 
 def cs_scf_free(s: Scf):
     s.close()
+
+
+# ---------------------------------------------------------------------- learned density
+def cs_atom_descriptors(atoms, mu, width: float):
+    """(n_atoms, len(mu)) numpy descriptors of the atoms (n_atoms, 3)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    out = np.empty((a.shape[0], m.size))
+    st = _lib.cs_atom_descriptors(a.shape[0], a.ctypes.data_as(_dp), m.size,
+                                  m.ctypes.data_as(_dp), float(width), out.ctypes.data_as(_dp))
+    if st != 0:
+        raise CsError(st, "cs_atom_descriptors")
+    return out
+
+
+def cs_atom_density(ctx: Context, atoms, sigmas, coef, rho: torch.Tensor, stream=None):
+    """rho += sum_a sum_j coef[a, j] phi_j(|x - a|) (rho: device float64 grid)."""
+    import numpy as np
+    _check_grid(ctx, rho)
+    a = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64))
+    sg = np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
+    ctx.check(_lib.cs_atom_density(ctx.handle, a.shape[0], a.ctypes.data_as(_dp), sg.size,
+                                   sg.ctypes.data_as(_dp), c.ctypes.data_as(_dp), _ptr(rho),
+                                   _stream_ptr(stream)))
+
+
+def cs_fit_workspace_bytes(ctx: Context, n_atoms: int, n_basis: int) -> int:
+    out = ctypes.c_size_t()
+    ctx.check(_lib.cs_fit_workspace_bytes(ctx.handle, int(n_atoms), int(n_basis), ctypes.byref(out)))
+    return out.value
+
+
+def cs_fit_atom_density(ctx: Context, atoms, sigmas, target: torch.Tensor, ridge: float = 1e-10,
+                        work=None, stream=None):
+    """Least-squares coefficients (n_atoms, n_basis) of the atom-centred expansion of target."""
+    import numpy as np
+    _check_grid(ctx, target)
+    a = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64))
+    sg = np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64))
+    out = np.empty((a.shape[0], sg.size))
+    if work is None:
+        work = torch.empty(cs_fit_workspace_bytes(ctx, a.shape[0], sg.size), dtype=torch.uint8,
+                           device=f"cuda:{ctx.device}")
+    ctx.check(_lib.cs_fit_atom_density(ctx.handle, a.shape[0], a.ctypes.data_as(_dp), sg.size,
+                                       sg.ctypes.data_as(_dp), _ptr(target), float(ridge),
+                                       out.ctypes.data_as(_dp), _ptr(work), _stream_ptr(stream)))
+    return out
+
+
+class Mlp:
+    """Owns one cs_mlp. Activations are float32 column-major (n rows = atoms): pass torch
+    tensors of shape (features, n) (C order), i.e. row f holds feature f of every atom."""
+
+    def __init__(self, handle: int, dims):
+        self._h = ctypes.c_void_p(handle)
+        self.dims = list(dims)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, status: int):
+        if status != 0:
+            raise CsError(status, _lib.cs_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.cs_mlp_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_mlp_create(dims, params, max_rows: int, cuda_device: int = 0) -> Mlp:
+    """params: flat float32 (W_1 column-major n_in x n_out, b_1, W_2, b_2, ...)."""
+    import numpy as np
+    d = (_i * len(dims))(*[int(x) for x in dims])
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    h = _vp()
+    st = _lib.cs_mlp_create(len(dims) - 1, d, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                            int(max_rows), int(cuda_device), ctypes.byref(h))
+    if st != 0:
+        raise CsError(st, "cs_mlp_create")
+    return Mlp(h.value, dims)
+
+
+def cs_mlp_free(m: Mlp):
+    m.close()
+
+
+def cs_mlp_param_count(m: Mlp) -> int:
+    c = _ll()
+    m.check(_lib.cs_mlp_param_count(m.handle, ctypes.byref(c)))
+    return c.value
+
+
+def cs_mlp_params(m: Mlp):
+    import numpy as np
+    out = np.empty(cs_mlp_param_count(m), dtype=np.float32)
+    m.check(_lib.cs_mlp_params(m.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def _check_act(t: torch.Tensor, rows: int):
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.shape[0] == rows
+
+
+def cs_mlp_forward(m: Mlp, X: torch.Tensor, stream=None) -> torch.Tensor:
+    _check_act(X, m.dims[0])
+    n = X.shape[1]
+    Y = torch.empty((m.dims[-1], n), dtype=torch.float32, device=X.device)
+    m.check(_lib.cs_mlp_forward(m.handle, n, _ptr(X), _ptr(Y), _stream_ptr(stream)))
+    return Y
+
+
+def cs_mlp_loss_grad(m: Mlp, X: torch.Tensor, T: torch.Tensor, stream=None):
+    import numpy as np
+    _check_act(X, m.dims[0])
+    _check_act(T, m.dims[-1])
+    loss = ctypes.c_float()
+    g = np.empty(cs_mlp_param_count(m), dtype=np.float32)
+    m.check(_lib.cs_mlp_loss_grad(m.handle, X.shape[1], _ptr(X), _ptr(T), ctypes.byref(loss),
+                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                  _stream_ptr(stream)))
+    return loss.value, g
+
+
+def cs_mlp_train_step(m: Mlp, X: torch.Tensor, T: torch.Tensor, lr: float, want_loss=True,
+                      stream=None):
+    _check_act(X, m.dims[0])
+    _check_act(T, m.dims[-1])
+    loss = ctypes.c_float()
+    m.check(_lib.cs_mlp_train_step(m.handle, X.shape[1], _ptr(X), _ptr(T), float(lr),
+                                   ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)))
+    return loss.value if want_loss else None
+
+
+def cs_mlp_last_error(m: Mlp) -> str:
+    return _lib.cs_mlp_last_error(m.handle).decode()

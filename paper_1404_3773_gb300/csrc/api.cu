@@ -526,6 +526,18 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
                      cudaMemcpyHostToDevice) != cudaSuccess)
         st = CS_ERR_ALLOC;
     }
+    if (st == CS_OK) {
+      // grid coordinates: r_k, cos(theta_j), phi_q
+      const HostTables& H = c->host;
+      std::vector<double> g;
+      g.insert(g.end(), H.r.begin(), H.r.end());
+      g.insert(g.end(), H.t.begin(), H.t.end());
+      g.insert(g.end(), H.phi.begin(), H.phi.end());
+      if (cudaMalloc((void**)&c->grid_tab, g.size() * sizeof(double)) != cudaSuccess ||
+          cudaMemcpy(c->grid_tab, g.data(), g.size() * sizeof(double),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        st = CS_ERR_ALLOC;
+    }
     if (st != CS_OK) {
       g_init_error = c->err;
       cs_basis_free(c);
@@ -551,6 +563,7 @@ cs_status cs_basis_free(cs_ctx* c) {
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->w_r_dev) cudaFree(c->w_r_dev);
     if (c->hartree_tab) cudaFree(c->hartree_tab);
+    if (c->grid_tab) cudaFree(c->grid_tab);
     if (c->tc_synth) cudaFree(c->tc_synth);
     if (c->tc_anal) cudaFree(c->tc_anal);
     if (c->kb_tabA) cudaFree(c->kb_tabA);

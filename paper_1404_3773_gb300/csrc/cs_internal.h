@@ -71,6 +71,7 @@ struct cs_ctx {
   cs::DevTables<cs::df64> ddf;  // double-float copies (CS_DF64)
   double* w_r_dev = nullptr; // radial weights (for forward transforms of grid data)
   double* hartree_tab = nullptr;  // k_ln = z_ln / R ([l][n]) then r_k / R ([k]) (scf.cu)
+  double* grid_tab = nullptr;     // r_k, cos(theta_j), phi_q (learned.cu)
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
   int tc_rows_synth = 0, tc_kpad_synth = 0, tc_rows_anal = 0, tc_kpad_anal = 0;

@@ -102,3 +102,14 @@ def test_fermi_occupations_match_oracle():
         assert abs(mu - m) <= 1e-9 and abs(S - S2) <= 1e-8
         # one ulp of mu moves the count by about ulp(mu) / (4 kT)
         assert abs(occ.sum() - ne / 2) <= 1e-12 + 1e-16 / kT
+
+
+def test_atom_descriptors_match_oracle():
+    cs = _lib()
+    import workloads as W
+    from oracle import learned_density as LD
+    atoms = W.place_atoms(8850, 9, 5.0, 2.0)
+    mu = np.linspace(2.0, 10.0, 16)
+    got = cs.cs_atom_descriptors(atoms, mu, 0.5)
+    ref = LD.descriptors(atoms, mu, 0.5)
+    assert np.max(np.abs(got - ref)) <= 1e-13
