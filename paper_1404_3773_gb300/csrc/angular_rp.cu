@@ -49,8 +49,10 @@ cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream
   };
   if (variant < 0) {
     // measured on the 46128-function workload: (4,8) fastest in FP32 and FP64, (2,8) in
-    // double-float (1.91 ms against 2.17 ms), whose per-thread state doubles the registers
-    const int order_sp[] = {2, 0, 1, 3, 4, 5};
+    // double-float (1.91 ms against 2.17 ms), whose per-thread state doubles the registers.
+    // Where (4,8) does not fit (lmax 60 in FP32), (2,8) beats (4,4): 14.9 ms against 16.2 ms
+    // on a 128-state chunk of the 357216-function workload.
+    const int order_sp[] = {2, 0, 1, 4, 3, 5};
     const int order_df[] = {4, 2, 5, 3, 1, 0};
     const int* order = std::is_same<T, df64>::value ? order_df : order_sp;
     for (int i = 0; i < 6; ++i)
