@@ -257,7 +257,15 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   }
   AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj,
                D.theta_pairs};
-  CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
+  bool ang_done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc && c->tc_phi && angular_tc_enabled()) {
+      CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular_tc(a, c->tc_phi, G, c->dev_err, st));
+      ang_done = true;
+    }
+  }
+  if (!ang_done)
+    CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular<T>(a, ANG_FULL, G, nullptr, nullptr, st));
   Epilogue<T> ep;
   ep.mode = mode;
   ep.out = out;
@@ -504,6 +512,14 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
           c->tc_kpad_anal = kp;
         }
       }
+      if (st == CS_OK && angular_tc_eligible(c->host.L, c->host.n_theta, c->host.n_phi)) {
+        std::vector<uint16_t> tab;
+        build_tc_phi_table(c->host.L, c->host.n_phi, tab);
+        if (cudaMalloc(&c->tc_phi, tab.size() * 2) != cudaSuccess ||
+            cudaMemcpy(c->tc_phi, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+          st = CS_ERR_ALLOC;
+      }
       if (st == CS_OK && (cudaMalloc((void**)&c->dev_err, sizeof(int)) != cudaSuccess ||
                           cudaMemset(c->dev_err, 0, sizeof(int)) != cudaSuccess))
         st = CS_ERR_ALLOC;
@@ -566,6 +582,7 @@ cs_status cs_basis_free(cs_ctx* c) {
     if (c->grid_tab) cudaFree(c->grid_tab);
     if (c->tc_synth) cudaFree(c->tc_synth);
     if (c->tc_anal) cudaFree(c->tc_anal);
+    if (c->tc_phi) cudaFree(c->tc_phi);
     if (c->kb_tabA) cudaFree(c->kb_tabA);
     if (c->kb_tabB) cudaFree(c->kb_tabB);
     if (c->dev_err) cudaFree(c->dev_err);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdint>
 #include <vector>
 
 namespace cs {
@@ -84,6 +85,16 @@ cudaError_t launch_tc_radial_synth(const TcTables& tt, const HostTables& H, cons
                                    cudaStream_t stream);
 cudaError_t launch_tc_radial_anal(const TcTables& tt, const HostTables& H, const float* G, int S,
                                   const Epilogue<float>& ep, int* err, cudaStream_t stream);
+
+// angular block with the phi transforms on the tensor cores (angular_tc.cu, mixed precision):
+// whether its tile fits, whether CS_ANGULAR_KERNEL leaves it enabled (unset or "tc"), the
+// split-BF16 phi operands it copies to shared memory (uint16 BF16 bits), and the launch
+// (cudaErrorInvalidConfiguration when the tile does not fit or a table is missing)
+bool angular_tc_eligible(int L, int n_theta, int n_phi);
+bool angular_tc_enabled();
+void build_tc_phi_table(int L, int n_phi, std::vector<uint16_t>& out);
+cudaError_t launch_angular_tc(const AngArgs<float>& a, const void* tphi, float* G, int* err,
+                              cudaStream_t stream);
 
 // ---------------------------------------------------------------- dense FP64 pieces
 // C (na x nb, column-major, ldc) = A^T B, A: d x na (lda), B: d x nb (ldb), split over d
