@@ -50,6 +50,11 @@ constexpr int kRC = kGmRC;            // mirrored row pairs per chunk
 constexpr int kNC = 2 * kRC * kST;    // columns per chunk = MMA M
 static_assert(kNC == 128, "the chunk's columns are the MMA's 128 rows");
 constexpr int kNCp = kNC + 4;         // FP32 F row stride (rows start on different banks)
+// The next chunk's Legendre rows and W V rows are fetched into registers by warps 1..7 only, so
+// that warp 0 issues the MMAs without waiting on that work.
+constexpr int kFetchThreads = kTaThreads - 32;
+constexpr int kTaPtRegs = 5;   // float4 of Legendre rows per fetching thread ((528+4) 8 / 4 / 224)
+constexpr int kTaWvRegs = 10;  // W V values per fetching thread (2 8 n_phi / 224, n_phi <= 140)
 
 __host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 __host__ __device__ inline int round64(int x) { return (x + 63) & ~63; }
@@ -155,28 +160,39 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   }
 
   const float* wvk = a.wv + (size_t)k * Nt * Np;
-  float4 pt_reg[kGmPtRegs];
-  float wv_reg[kGmWvRegs];
+  const int ft = tid - 32;  // fetching thread, warps 1..7
+  float4 pt_reg[kTaPtRegs];
+  float wv_reg[kTaWvRegs];
+  // W V element u of this thread: staged index ft + u kFetchThreads = pr Np + q, packed as
+  // pr << 16 | q once per CTA (-1 past the end)
+  int wv_pq[kTaWvRegs];
+#pragma unroll
+  for (int u = 0; u < kTaWvRegs; ++u) {
+    const int i = u * kFetchThreads + ft;
+    wv_pq[u] = -1;
+    if (ft >= 0 && i < RC * 2 * Np) {
+      const int pr = i / Np;
+      wv_pq[u] = (pr << 16) | (i - pr * Np);
+    }
+  }
   auto fetch_chunk = [&](int c, int chn) {
+    if (ft < 0) return;
     const float4* src =
         reinterpret_cast<const float4*>(a.theta_pairs + (size_t)chn * (RL + 4) * RC);
     const int n4 = (RL + 4) * RC / 4;
 #pragma unroll
-    for (int u = 0; u < kGmPtRegs; ++u) {
-      const int i = u * kTaThreads + tid;
+    for (int u = 0; u < kTaPtRegs; ++u) {
+      const int i = u * kFetchThreads + ft;
       if (i < n4) pt_reg[u] = src[i];
     }
-    const int n = RC * 2 * Np;
 #pragma unroll
-    for (int u = 0; u < kGmWvRegs; ++u) {
-      const int i = u * kTaThreads + tid;
+    for (int u = 0; u < kTaWvRegs; ++u) {
       float v = 0.f;
-      if (i < n) {
-        const int pr = i / Np, q = i - pr * Np;
-        const int p = pr >> 1, r = pr & 1;
-        const int jp = c + p;
-        const int row = r ? Nt - 1 - jp : jp;
-        if (jp < NP && (r == 0 || row != jp)) v = wvk[(size_t)row * Np + q];
+      if (wv_pq[u] >= 0) {
+        const int pr = wv_pq[u] >> 16, q = wv_pq[u] & 0xffff;
+        const int jp = c + (pr >> 1);
+        const int row = (pr & 1) ? Nt - 1 - jp : jp;
+        if (jp < NP && ((pr & 1) == 0 || row != jp)) v = wvk[(size_t)row * Np + q];
       }
       wv_reg[u] = v;
     }
@@ -239,19 +255,18 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   uint32_t phase = 0;
   for (int c0 = 0, ch = 0; ok && c0 < NP; c0 += RC, ++ch) {
     __syncthreads();  // the previous chunk's stage D is done with PT and AP
-    {
+    if (ft >= 0) {
       float4* dst = reinterpret_cast<float4*>(PT);
       const int n4 = (RL + 4) * RC / 4;
 #pragma unroll
-      for (int u = 0; u < kGmPtRegs; ++u) {
-        const int i = u * kTaThreads + tid;
+      for (int u = 0; u < kTaPtRegs; ++u) {
+        const int i = u * kFetchThreads + ft;
         if (i < n4) dst[i] = pt_reg[u];
       }
-      const int n = RC * 2 * Np;
 #pragma unroll
-      for (int u = 0; u < kGmWvRegs; ++u) {
-        const int i = u * kTaThreads + tid;
-        if (i < n) WV[i] = wv_reg[u];
+      for (int u = 0; u < kTaWvRegs; ++u) {
+        const int i = u * kFetchThreads + ft;
+        if (wv_pq[u] >= 0) WV[i] = wv_reg[u];
       }
     }
     __syncthreads();
@@ -494,8 +509,8 @@ bool angular_tc_eligible(int L, int n_theta, int n_phi) {
   const TaShape s = ta_shape(L, n_theta, n_phi);
   return s.NB <= 256 && s.Kb <= 256 && s.NB + s.Kb <= 512 && s.total <= 227 * 1024 &&
          L * L * kST <= kGmGRegs * kTaThreads && gm_items(L) <= kGmItems * kTaThreads &&
-         (s.RL + 4) * kRC / 4 <= kGmPtRegs * kTaThreads &&
-         2 * kRC * n_phi <= kGmWvRegs * kTaThreads && s.M2 <= 255;
+         (s.RL + 4) * kRC / 4 <= kTaPtRegs * kFetchThreads &&
+         2 * kRC * n_phi <= kTaWvRegs * kFetchThreads && s.M2 <= 255;
 }
 
 bool angular_tc_enabled() {
