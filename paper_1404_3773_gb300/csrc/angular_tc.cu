@@ -109,6 +109,17 @@ __host__ __device__ inline TaShape ta_shape(int L, int n_theta, int n_phi) {
   return s;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// src_bytes = 0 fills the destination word with zero and reads nothing
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __host__ __device__ inline uint32_t ta_tmem_cols(int NB, int Kb) {
   uint32_t c = 32;
   while ((int)c < NB + Kb) c <<= 1;
@@ -138,8 +149,8 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   float* WV = reinterpret_cast<float*>(smem + sh.off_wv);  // [RC][2][Np]
   int* mstart = reinterpret_cast<int*>(smem + sh.off_ms);  // [M2 + 1]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k = blockIdx.y, s0 = blockIdx.x * ST;
-  const int ns = min(ST, S - s0);
+  // tiles t = (radial node t / nst, states (t % nst) ST ..), taken in steps of the grid size
+  const int nst = (S + ST - 1) / ST, ntiles = nst * a.n_r;
   const uint32_t bar_tma = smem_u32(&bars[0]);
   const uint32_t bar_mma = smem_u32(&bars[1]);
   const uint32_t tcols = ta_tmem_cols(NB, Kb);
@@ -159,7 +170,6 @@ __global__ void __launch_bounds__(kTaThreads, 1)
     bulk_g2s(smem_u32(smem + sh.off_tb), tphi, (uint32_t)sh.off_x, bar_tma);
   }
 
-  const float* wvk = a.wv + (size_t)k * Nt * Np;
   const int ft = tid - 32;  // fetching thread, warps 1..7
   float4 pt_reg[kTaPtRegs];
   float wv_reg[kTaWvRegs];
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       wv_pq[u] = (pr << 16) | (i - pr * Np);
     }
   }
-  auto fetch_chunk = [&](int c, int chn) {
+  auto fetch_chunk = [&](const float* wvk, int c, int chn) {
     if (ft < 0) return;
     const float4* src =
         reinterpret_cast<const float4*>(a.theta_pairs + (size_t)chn * (RL + 4) * RC);
@@ -197,7 +207,25 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       wv_reg[u] = v;
     }
   };
+  // the next tile's state tile of G, streamed into Gs by cp.async (zero fill past the states)
+  auto prefetch_g = [&](int kn, int s0n) {
+    const int nsn = min(ST, S - s0n);
+    if ((S & 3) == 0 && nsn == ST && (reinterpret_cast<uintptr_t>(G) & 15) == 0) {
+      for (int i = tid; i < L2 * 2; i += kTaThreads) {
+        const int lm = i >> 1, h = i & 1;
+        cp_async16(smem_u32(Gs + lm * ST + 4 * h), G + ((size_t)kn * L2 + lm) * S + s0n + 4 * h);
+      }
+    } else {
+      for (int i = tid; i < L2 * ST; i += kTaThreads) {
+        const int lm = i / ST, sl = i - lm * ST;
+        const bool in = sl < nsn;
+        cp_async4(smem_u32(Gs + i), in ? G + ((size_t)kn * L2 + lm) * S + s0n + sl : G, in ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
   {
+    const int k = blockIdx.x / nst, s0 = (blockIdx.x % nst) * ST, ns = min(ST, S - s0);
     float v[kGmGRegs];
 #pragma unroll
     for (int u = 0; u < kGmGRegs; ++u) {
@@ -205,7 +233,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       const int lm = i / ST, s = i - lm * ST;
       v[u] = (i < L2 * ST && s < ns) ? G[((size_t)k * L2 + lm) * S + s0 + s] : 0.f;
     }
-    fetch_chunk(0, 0);
+    fetch_chunk(a.wv + (size_t)k * Nt * Np, 0, 0);
 #pragma unroll
     for (int u = 0; u < kGmGRegs; ++u) {
       const int i = u * kTaThreads + tid;
@@ -253,7 +281,14 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   const int lq = warp & 3, hb = warp >> 2;  // lane quarter of tensor memory, column half
   const int my_col = 32 * lq + lane;
   uint32_t phase = 0;
+  for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+  const int k = tile / nst, s0 = (tile % nst) * ST, ns = min(ST, S - s0);
+  const float* wvk = a.wv + (size_t)k * Nt * Np;
+  const int tnext = tile + gridDim.x;
+  const bool has_next = tnext < ntiles;
+  const int kn = tnext / nst, s0n = (tnext % nst) * ST;
   for (int c0 = 0, ch = 0; ok && c0 < NP; c0 += RC, ++ch) {
+    const bool last = c0 + RC >= NP;
     __syncthreads();  // the previous chunk's stage D is done with PT and AP
     if (ft >= 0) {
       float4* dst = reinterpret_cast<float4*>(PT);
@@ -335,6 +370,8 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       *reinterpret_cast<uint4*>(Fhi + off) = h;
       *reinterpret_cast<uint4*>(Flo + off) = lo;
     }
+    // the tile's last stage A has read Gs: stream the next tile's G into it
+    if (last && has_next) prefetch_g(kn, s0n);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -355,7 +392,8 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       mma_commit(bar_mma);
     }
     // the next chunk's rows: their loads run while the MMAs and the later stages compute
-    if (c0 + RC < NP) fetch_chunk(c0 + RC, ch + 1);
+    if (!last) fetch_chunk(wvk, c0 + RC, ch + 1);
+    else if (has_next) fetch_chunk(a.wv + (size_t)kn * Nt * Np, 0, 0);
     bool w_ok = mbar_wait(bar_mma, phase);
     phase ^= 1u;
     if (!w_ok) atomicCAS(err, 0, 2);
@@ -492,14 +530,19 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       }
     }
   }
+  if (!ok) break;
+  __syncthreads();  // stage D of the tile's last chunk is done with Ga
+  for (int i = tid; i < L2 * ST; i += kTaThreads) {
+    const int lm = i / ST, sl = i - lm * ST;
+    if (sl < ns) G[((size_t)k * L2 + lm) * S + s0 + sl] = Ga[i];
+    Ga[i] = 0.f;
+  }
+  cp_async_wait_all();
+  __syncthreads();  // the next tile's Gs is complete
+  }
+  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
-  if (ok) {
-    for (int i = tid; i < L2 * ST; i += kTaThreads) {
-      const int lm = i / ST, sl = i - lm * ST;
-      if (sl < ns) G[((size_t)k * L2 + lm) * S + s0 + sl] = Ga[i];
-    }
-  }
   if (warp == 0) tmem_dealloc(tmem, tcols);
 }
 
@@ -553,7 +596,15 @@ cudaError_t launch_angular_tc(const AngArgs<float>& a, const void* tphi, float* 
   cudaError_t e = cudaFuncSetAttribute(k_angular_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)s.total);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.S + kST - 1) / kST, a.n_r);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+  }
+  const int ntiles = ((a.S + kST - 1) / kST) * a.n_r;
+  const int grid = ntiles < nsm ? ntiles : nsm;  // persistent: one CTA per SM
   k_angular_tc<<<grid, kTaThreads, s.total, stream>>>(
       a, static_cast<const __nv_bfloat16*>(tphi), G, err);
   return cudaGetLastError();
