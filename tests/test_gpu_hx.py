@@ -189,6 +189,32 @@ def test_apply_H_mixed_bf16_error(case):
     assert cs.cs_device_error(ctx) == 0
 
 
+@pytest.mark.parametrize("case", ["small_ragged", "ho_l10", "odd_theta_phi_not_mult4",
+                                  "gauss_jacobi"])
+def test_mixed_angular_tensor_core_matches_fp32_kernel(case, monkeypatch):
+    """The mixed path's angular block runs its phi transforms on tcgen05 (split BF16); with
+    CS_ANGULAR_KERNEL=gm the same call takes the FP32 register-blocked kernel. Both stay within
+    the mixed bar of the FP64 oracle, and they agree with each other to the split-BF16 level."""
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, dtype=torch.float32)
+    out = {}
+    for kern in ("tc", "gm"):
+        monkeypatch.setenv("CS_ANGULAR_KERNEL", kern)
+        HXd = torch.zeros_like(Xd)
+        cs.cs_apply_H(ctx, Xd, HXd, cs.CS_MIXED_BF16)
+        torch.cuda.synchronize()
+        out[kern] = to_host(HXd, ctx.d)
+        fro, col = rel_errors(out[kern], ref)
+        assert fro <= 1e-4 and col <= 1e-3, (kern, fro, col)
+    fro, _ = rel_errors(out["tc"], out["gm"])
+    assert 0 < fro <= 1e-4, fro  # nonzero: the two kernels really differ in arithmetic
+    assert cs.cs_device_error(ctx) == 0
+
+
 def test_apply_H_mixed_bf16_full_size():
     torch, cs = need_gpu()
     w = W.erf_cluster_32()
