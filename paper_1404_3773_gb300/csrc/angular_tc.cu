@@ -20,9 +20,10 @@
 // The MMA operands are BF16 in the canonical K-major no-swizzle layout; each product is
 // accumulated in FP32 tensor memory as hi*hi + hi*lo + lo*hi (split BF16, about 16
 // significant bits). The FP32 F rows with the F operand, the g operand, and AP share one
-// shared-memory region: each is dead once the pass or the MMA that reads it has completed. The two trig operands (T as B of
-// the first MMA, T transposed as B of the second) are pre-split and pre-laid-out at set-up
-// and copied once per CTA by the TMA engine (cp.async.bulk).
+// shared-memory region: each is dead once the pass or the MMA that reads it has completed.
+// The two trig operands (T as B of the first MMA, T transposed as B of the second) are
+// pre-split and pre-laid-out at set-up and copied once per CTA by the TMA engine
+// (cp.async.bulk). CTAs are persistent (one per SM) and loop over the tiles.
 // Every mbarrier wait is bounded: on expiry the kernel records an error code in a device word,
 // releases its tensor memory and returns without writing G.
 #include <cuda_bf16.h>
