@@ -95,7 +95,7 @@ def dense_flops(d, n):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
 # capture of the kernel as it stands, on this workload; a class without a capture reports null
-NCU_TRAFFIC_BYTES = {"angular_f32": 32.498176e6 + 768.0}  # k_angular_tc (mixed default)
+NCU_TRAFFIC_BYTES = {"angular_f32": 32.497664e6 + 0.0}  # k_angular_tc (mixed default)
 
 
 def measured_peaks():

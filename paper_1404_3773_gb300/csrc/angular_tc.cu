@@ -21,9 +21,9 @@
 // accumulated in FP32 tensor memory as hi*hi + hi*lo + lo*hi (split BF16, about 16
 // significant bits). The FP32 F rows with the F operand, the g operand, and AP share one
 // shared-memory region: each is dead once the pass or the MMA that reads it has completed.
-// The two trig operands (T as B of the first MMA, T transposed as B of the second) are
-// pre-split and pre-laid-out at set-up and copied once per CTA by the TMA engine
-// (cp.async.bulk). CTAs are persistent (one per SM) and loop over the tiles.
+// The two trig operands (T as B of the first MMA; T transposed, hi rows stacked over lo rows,
+// as B of the second) are pre-split and pre-laid-out at set-up and copied once per CTA by the
+// TMA engine (cp.async.bulk). CTAs are persistent (one per SM) and loop over the tiles.
 // Every mbarrier wait is bounded: on expiry the kernel records an error code in a device word,
 // releases its tensor memory and returns without writing G.
 #include <cuda_bf16.h>
@@ -51,6 +51,8 @@ constexpr int kRC = kGmRC;            // mirrored row pairs per chunk
 constexpr int kNC = 2 * kRC * kST;    // columns per chunk = MMA M
 static_assert(kNC == 128, "the chunk's columns are the MMA's 128 rows");
 constexpr int kNCp = kNC + 4;         // FP32 F row stride (rows start on different banks)
+constexpr int kAPS = kNC + 4;         // AP stride per mode (stage D's lanes on different modes
+                                      // then read different banks)
 // The next chunk's Legendre rows and W V rows are fetched into registers by warps 1..7 only, so
 // that warp 0 issues the MMAs without waiting on that work.
 constexpr int kFetchThreads = kTaThreads - 32;
@@ -88,12 +90,12 @@ __host__ __device__ inline TaShape ta_shape(int L, int n_theta, int n_phi) {
   s.off_tb = o;
   o += (size_t)2 * s.NB * s.Kb * 2;  // T (rows p, K = kap), hi then lo
   s.off_tc = o;
-  o += (size_t)2 * s.Kb * s.NB * 2;  // T^T (rows kap, K = p), hi then lo
+  o += (size_t)2 * s.Kb * s.NB * 2;  // T^T: rows kap (hi) then Kb + kap (lo), K = p
   s.off_x = o;
   // F operand followed by the FP32 F rows it is converted from ([M2][kNCp])
   size_t xb = (size_t)2 * kNC * s.Kb * 2 + (size_t)s.M2 * kNCp * 4;
   if ((size_t)2 * kNC * s.NB * 2 > xb) xb = (size_t)2 * kNC * s.NB * 2;  // g operand
-  if ((size_t)s.M2 * kNC * 4 > xb) xb = (size_t)s.M2 * kNC * 4;            // AP
+  if ((size_t)s.M2 * kAPS * 4 > xb) xb = (size_t)s.M2 * kAPS * 4;          // AP
   o += xb;
   s.off_gs = o;
   o += (size_t)L * L * kST * 4;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   unsigned char* Ghi = smem + sh.off_x;                 // g operand: NC x NB, hi then lo
   unsigned char* Glo = Ghi + (size_t)NC * NB * 2;
   float* F32 = reinterpret_cast<float*>(Flo + (size_t)NC * Kb * 2);  // [M2][kNCp]
-  float* AP = reinterpret_cast<float*>(smem + sh.off_x);  // [M2][RC][2][ST]
+  float* AP = reinterpret_cast<float*>(smem + sh.off_x);  // [M2][kAPS]: [RC][2][ST] + pad
   float* Gs = reinterpret_cast<float*>(smem + sh.off_gs);  // [L2][ST]
   float* Ga = reinterpret_cast<float*>(smem + sh.off_ga);  // [L2][ST]
   float* PT = reinterpret_cast<float*>(smem + sh.off_pt);  // [RL + 4][RC]
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   const int nst = (S + ST - 1) / ST, ntiles = nst * a.n_r;
   const uint32_t bar_tma = smem_u32(&bars[0]);
   const uint32_t bar_mma = smem_u32(&bars[1]);
-  const uint32_t tcols = ta_tmem_cols(NB, Kb);
+  const uint32_t tcols = ta_tmem_cols(NB, 2 * Kb);
   if (tid == 0) {
     mbar_init(bar_tma, 1);
     mbar_init(bar_mma, 1);
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
 
   const uint32_t idesc_b = make_idesc(NC, NB);
   const uint32_t idesc_c = make_idesc(NC, Kb);
+  const uint32_t idesc_c2 = make_idesc(NC, 2 * Kb);
   const int lq = warp & 3, hb = warp >> 2;  // lane quarter of tensor memory, column half
   const int my_col = 32 * lq + lane;
   uint32_t phase = 0;
@@ -441,19 +444,19 @@ __global__ void __launch_bounds__(kTaThreads, 1)
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    // ---- C: phi quadrature, D_C[col][kap] (tensor memory columns NB .. NB+Kb-1)
+    // ---- C: phi quadrature. The B operand stacks the hi rows of T^T over its lo rows, so one
+    //      MMA of N = 2 Kb gives hi*hi (columns NB ..) and hi*lo (columns NB + Kb ..), and one of
+    //      N = Kb adds lo*hi to the first block: D_C = sum of the two blocks.
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a_hi = smem_u32(Ghi), a_lo = smem_u32(Glo);
-      const uint32_t b_hi = smem_u32(smem + sh.off_tc);
-      const uint32_t b_lo = b_hi + (uint32_t)Kb * NB * 2;
+      const uint32_t b = smem_u32(smem + sh.off_tc);
       for (int ks = 0; ks < NB / 16; ++ks) {
-        const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (Kb / 8) * 256;
+        const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (2 * Kb / 8) * 256;
         const uint64_t dah = make_desc(a_hi + ao, 128, 256), dal = make_desc(a_lo + ao, 128, 256);
-        const uint64_t dbh = make_desc(b_hi + bo, 128, 256), dbl = make_desc(b_lo + bo, 128, 256);
-        mma_bf16(tmem + (uint32_t)NB, dah, dbh, idesc_c, ks > 0 ? 1u : 0u);
-        mma_bf16(tmem + (uint32_t)NB, dah, dbl, idesc_c, 1u);
-        mma_bf16(tmem + (uint32_t)NB, dal, dbh, idesc_c, 1u);
+        const uint64_t db = make_desc(b + bo, 128, 256);
+        mma_bf16(tmem + (uint32_t)NB, dah, db, idesc_c2, ks > 0 ? 1u : 0u);
+        mma_bf16(tmem + (uint32_t)NB, dal, db, idesc_c, 1u);
       }
       mma_commit(bar_mma);
     }
@@ -470,15 +473,19 @@ __global__ void __launch_bounds__(kTaThreads, 1)
       const int pp = col >> 4, r = (col >> 1) & 1, s = 2 * ((col >> 2) & 3) + (col & 1);
       const int half = Kb / 2;
       for (int kb0 = hb * half; kb0 < (hb + 1) * half; kb0 += 16) {
-        float v[16];
-        tmem_ld16_issue(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(NB + kb0), v);
+        float v[16], w[16];
+        const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(NB + kb0);
+        tmem_ld16_issue(ta, v);
+        tmem_ld16_issue(ta + (uint32_t)Kb, w);
         tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += w[i];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const float other = __shfl_xor_sync(0xffffffffu, v[i], 2);
           const int kap = kb0 + i;
           if (kap < M2)
-            AP[((size_t)(kap * RC + pp) * 2 + r) * ST + s] = r ? other - v[i] : v[i] + other;
+            AP[(size_t)kap * kAPS + (pp * 2 + r) * ST + s] = r ? other - v[i] : v[i] + other;
         }
       }
     }
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
           for (int q = 0; q < RC; ++q) pv[v][q] = 0.f;
         }
       }
-      const float* arow = AP + (size_t)mi * RC * 2 * ST + (par ? ST : 0);
+      const float* arow = AP + (size_t)mi * kAPS + (par ? ST : 0);
 #pragma unroll
       for (int pp = 0; pp < RC; ++pp) {
         float av[ST];
@@ -551,7 +558,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
 
 bool angular_tc_eligible(int L, int n_theta, int n_phi) {
   const TaShape s = ta_shape(L, n_theta, n_phi);
-  return s.NB <= 256 && s.Kb <= 256 && s.NB + s.Kb <= 512 && s.total <= 227 * 1024 &&
+  return s.NB <= 256 && 2 * s.Kb <= 256 && s.NB + 2 * s.Kb <= 512 && s.total <= 227 * 1024 &&
          L * L * kST <= kGmGRegs * kTaThreads && gm_items(L) <= kGmItems * kTaThreads &&
          (s.RL + 4) * kRC / 4 <= kTaPtRegs * kFetchThreads &&
          2 * kRC * n_phi <= kTaWvRegs * kFetchThreads && s.M2 <= 255;
@@ -569,8 +576,7 @@ void build_tc_phi_table(int L, int n_phi, std::vector<uint16_t>& out) {
   out.assign(4 * nb, 0);
   uint16_t* tbh = out.data();
   uint16_t* tbl = tbh + nb;
-  uint16_t* tch = tbl + nb;
-  uint16_t* tcl = tch + nb;
+  uint16_t* tc2 = tbl + nb;  // 2 Kb rows: hi, then lo
   auto bits = [](__nv_bfloat16 b) -> uint16_t { return *reinterpret_cast<uint16_t*>(&b); };
   for (int p = 0; p < n_phi; ++p)
     for (int kap = 0; kap < s.M2; ++kap) {
@@ -581,11 +587,11 @@ void build_tc_phi_table(int L, int n_phi, std::vector<uint16_t>& out) {
       const float f = (float)v;
       const __nv_bfloat16 hb = __float2bfloat16_rn(f);
       const __nv_bfloat16 lb = __float2bfloat16_rn(f - __bfloat162float(hb));
-      const int ob = canon_off(p, kap, s.NB) / 2, oc = canon_off(kap, p, s.Kb) / 2;
+      const int ob = canon_off(p, kap, s.NB) / 2;
       tbh[ob] = bits(hb);
       tbl[ob] = bits(lb);
-      tch[oc] = bits(hb);
-      tcl[oc] = bits(lb);
+      tc2[canon_off(kap, p, 2 * s.Kb) / 2] = bits(hb);
+      tc2[canon_off(s.Kb + kap, p, 2 * s.Kb) / 2] = bits(lb);
     }
 }
 
