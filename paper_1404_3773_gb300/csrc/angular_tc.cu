@@ -14,7 +14,9 @@
 //   epi         g[col][p]    = W V(k, row, p) D_B[col][p], split BF16, into the next A operand
 //   C   (MMA)   D_C[col][kap] = sum_p g[col][p] T[p][kap]: the phi quadrature
 //   epi         AP[kap][p][+-][s] = D_C of row j +- D_C of row jb (a lane shuffle)
-//   D   (FP32)  G'[l,m][s]  += sum_pairs Theta_lm(t_j) AP[...]  (as the FP32 kernel)
+//   D   (FP32)  G'[l,m][s]  += sum_pairs Theta_lm(t_j) AP[...]: a thread owns one item of 5
+//               same-parity l of one mode, keeps its sums in registers for the whole tile and
+//               writes them to G at the tile's end
 // The phi sums are plain dense products over all n_phi angles (no folding of the four mirror
 // angles), which costs the tensor cores nothing and keeps the epilogues elementwise.
 // The MMA operands are BF16 in the canonical K-major no-swizzle layout; each product is
@@ -74,7 +76,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 struct TaShape {
   int M2, Kb, NB, RL, NP;
   // byte offsets in dynamic shared memory
-  size_t off_tb, off_tc, off_x, off_gs, off_ga, off_pt, off_wv, off_ms, total;
+  size_t off_tb, off_tc, off_x, off_gs, off_pt, off_wv, off_ms, total;
 };
 
 // Kb = modes rounded up to 32 (split into 16-column tensor-memory loads between the two warps
@@ -98,8 +100,6 @@ __host__ __device__ inline TaShape ta_shape(int L, int n_theta, int n_phi) {
   if ((size_t)s.M2 * kAPS * 4 > xb) xb = (size_t)s.M2 * kAPS * 4;          // AP
   o += xb;
   s.off_gs = o;
-  o += (size_t)L * L * kST * 4;
-  s.off_ga = o;
   o += (size_t)L * L * kST * 4;
   s.off_pt = o;
   o += (size_t)(s.RL + 4) * kRC * 4;
@@ -147,7 +147,6 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   float* F32 = reinterpret_cast<float*>(Flo + (size_t)NC * Kb * 2);  // [M2][kNCp]
   float* AP = reinterpret_cast<float*>(smem + sh.off_x);  // [M2][kAPS]: [RC][2][ST] + pad
   float* Gs = reinterpret_cast<float*>(smem + sh.off_gs);  // [L2][ST]
-  float* Ga = reinterpret_cast<float*>(smem + sh.off_ga);  // [L2][ST]
   float* PT = reinterpret_cast<float*>(smem + sh.off_pt);  // [RL + 4][RC]
   float* WV = reinterpret_cast<float*>(smem + sh.off_wv);  // [RC][2][Np]
   int* mstart = reinterpret_cast<int*>(smem + sh.off_ms);  // [M2 + 1]
@@ -240,10 +239,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
 #pragma unroll
     for (int u = 0; u < kGmGRegs; ++u) {
       const int i = u * kTaThreads + tid;
-      if (i < L2 * ST) {
-        Gs[i] = v[u];
-        Ga[i] = 0.f;
-      }
+      if (i < L2 * ST) Gs[i] = v[u];
     }
   }
   if (tid == 0) {
@@ -257,24 +253,32 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   }
   __syncthreads();
   const int nitems = mstart[M2];
-  int item_code[kGmItems];  // mi | parity << 8 | group << 9, or -1
-#pragma unroll
-  for (int u = 0; u < kGmItems; ++u) {
-    const int t = tid + u * kTaThreads;
-    item_code[u] = -1;
-    if (t < nitems) {
-      int lo = 0, hi = M2 - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (mstart[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      const int m = lo - lmax, cnt = L - (m < 0 ? -m : m);
-      const int ge = ((cnt + 1) / 2 + kGmLq - 1) / kGmLq;
-      const int r = t - mstart[lo];
-      item_code[u] = (r < ge) ? (lo | (r << 9)) : (lo | (1 << 8) | ((r - ge) << 9));
+  // this thread's Legendre-quadrature item (at most one per thread): mode mi, parity of
+  // l - |m|, group of kGmLq such l; its sums stay in registers for the whole tile
+  int d_mi = 0, d_m = 0, d_am = 0, d_lbase = 0, d_par = 0;
+  bool d_live = false;
+  if (tid < nitems) {
+    int lo = 0, hi = M2 - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mstart[mid] <= tid) lo = mid;
+      else hi = mid - 1;
     }
+    const int m = lo - lmax, cnt = L - (m < 0 ? -m : m);
+    const int ge = ((cnt + 1) / 2 + kGmLq - 1) / kGmLq;
+    const int r = tid - mstart[lo];
+    d_mi = lo;
+    d_m = m;
+    d_am = m < 0 ? -m : m;
+    d_par = (r < ge) ? 0 : 1;
+    d_lbase = d_am + d_par + 2 * kGmLq * ((r < ge) ? r : r - ge);  // l_v = d_lbase + 2 v
+    d_live = true;
   }
+  float dacc[kGmLq][ST];
+#pragma unroll
+  for (int v = 0; v < kGmLq; ++v)
+#pragma unroll
+    for (int q = 0; q < ST; ++q) dacc[v][q] = 0.f;
   bool ok = mbar_wait(bar_tma, 0);
   if (!ok) atomicCAS(err, 0, 1);
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
@@ -491,33 +495,22 @@ __global__ void __launch_bounds__(kTaThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    // ---- D: Legendre quadrature (items of kGmLq same-parity l of one mode)
-#pragma unroll
-    for (int u = 0; u < kGmItems; ++u) {
-      const int code = item_code[u];
-      if (code < 0) continue;
-      const int mi = code & 0xff, par = (code >> 8) & 1, grp = code >> 9;
-      const int m = mi - lmax, am = m < 0 ? -m : m;
-      const int lbase = am + par + 2 * kGmLq * grp;  // l_v = lbase + 2 v
-      float acc[kGmLq][ST], pv[kGmLq][RC];
+    // ---- D: Legendre quadrature into the item's register sums (rows past lmax read as zero)
+    if (d_live) {
+      float pv[kGmLq][RC];
 #pragma unroll
       for (int v = 0; v < kGmLq; ++v) {
-        const int l = lbase + 2 * v;
+        const int l = d_lbase + 2 * v;
         if (l <= lmax) {
-          const float* ga = Ga + (size_t)(l * l + l + m) * ST;
-          unpack4(ld4(ga), acc[v]);
-          unpack4(ld4(ga + 4), acc[v] + 4);
-          const float* prw = PT + (size_t)(theta_off(L, am) + l - am) * RC;
+          const float* prw = PT + (size_t)(theta_off(L, d_am) + l - d_am) * RC;
           unpack4(ld4(prw), pv[v]);
           unpack4(ld4(prw + 4), pv[v] + 4);
         } else {
 #pragma unroll
-          for (int q = 0; q < ST; ++q) acc[v][q] = 0.f;
-#pragma unroll
           for (int q = 0; q < RC; ++q) pv[v][q] = 0.f;
         }
       }
-      const float* arow = AP + (size_t)mi * kAPS + (par ? ST : 0);
+      const float* arow = AP + (size_t)d_mi * kAPS + (d_par ? ST : 0);
 #pragma unroll
       for (int pp = 0; pp < RC; ++pp) {
         float av[ST];
@@ -526,24 +519,31 @@ __global__ void __launch_bounds__(kTaThreads, 1)
 #pragma unroll
         for (int v = 0; v < kGmLq; ++v)
 #pragma unroll
-          for (int q = 0; q < ST; ++q) acc[v][q] = fmaf(pv[v][pp], av[q], acc[v][q]);
-      }
-#pragma unroll
-      for (int v = 0; v < kGmLq; ++v) {
-        const int l = lbase + 2 * v;
-        if (l > lmax) break;
-        float* ga = Ga + (size_t)(l * l + l + m) * ST;
-        st4(ga, acc[v][0], acc[v][1], acc[v][2], acc[v][3]);
-        st4(ga + 4, acc[v][4], acc[v][5], acc[v][6], acc[v][7]);
+          for (int q = 0; q < ST; ++q) dacc[v][q] = fmaf(pv[v][pp], av[q], dacc[v][q]);
       }
     }
   }
   if (!ok) break;
-  __syncthreads();  // stage D of the tile's last chunk is done with Ga
-  for (int i = tid; i < L2 * ST; i += kTaThreads) {
-    const int lm = i / ST, sl = i - lm * ST;
-    if (sl < ns) G[((size_t)k * L2 + lm) * S + s0 + sl] = Ga[i];
-    Ga[i] = 0.f;
+  // the item's sums go straight to G (8 consecutive states of one (l, m) row), then reset
+  if (d_live) {
+    const bool vec = (S & 3) == 0 && ns == ST && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+#pragma unroll
+    for (int v = 0; v < kGmLq; ++v) {
+      const int l = d_lbase + 2 * v;
+      if (l <= lmax) {
+        float* gr = G + ((size_t)k * L2 + l * l + l + d_m) * S + s0;
+        if (vec) {
+          st4(gr, dacc[v][0], dacc[v][1], dacc[v][2], dacc[v][3]);
+          st4(gr + 4, dacc[v][4], dacc[v][5], dacc[v][6], dacc[v][7]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < ST; ++q)
+            if (q < ns) gr[q] = dacc[v][q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < ST; ++q) dacc[v][q] = 0.f;
+    }
   }
   cp_async_wait_all();
   __syncthreads();  // the next tile's Gs is complete
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kTaThreads, 1)
 bool angular_tc_eligible(int L, int n_theta, int n_phi) {
   const TaShape s = ta_shape(L, n_theta, n_phi);
   return s.NB <= 256 && 2 * s.Kb <= 256 && s.NB + 2 * s.Kb <= 512 && s.total <= 227 * 1024 &&
-         L * L * kST <= kGmGRegs * kTaThreads && gm_items(L) <= kGmItems * kTaThreads &&
+         L * L * kST <= kGmGRegs * kTaThreads && gm_items(L) <= kTaThreads &&
          (s.RL + 4) * kRC / 4 <= kTaPtRegs * kFetchThreads &&
          2 * kRC * n_phi <= kTaWvRegs * kFetchThreads && s.M2 <= 255;
 }
