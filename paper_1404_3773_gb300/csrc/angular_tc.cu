@@ -120,8 +120,12 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, int sr
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 __host__ __device__ inline uint32_t ta_tmem_cols(int NB, int Kb) {
   uint32_t c = 32;
@@ -290,263 +294,263 @@ __global__ void __launch_bounds__(kTaThreads, 1)
   const int my_col = 32 * lq + lane;
   uint32_t phase = 0;
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-  const int k = tile / nst, s0 = (tile % nst) * ST, ns = min(ST, S - s0);
-  const float* wvk = a.wv + (size_t)k * Nt * Np;
-  const int tnext = tile + gridDim.x;
-  const bool has_next = tnext < ntiles;
-  const int kn = tnext / nst, s0n = (tnext % nst) * ST;
-  for (int c0 = 0, ch = 0; ok && c0 < NP; c0 += RC, ++ch) {
-    const bool last = c0 + RC >= NP;
-    __syncthreads();  // the previous chunk's stage D is done with PT and AP
-    if (ft >= 0) {
-      float4* dst = reinterpret_cast<float4*>(PT);
-      const int n4 = (RL + 4) * RC / 4;
-#pragma unroll
-      for (int u = 0; u < kTaPtRegs; ++u) {
-        const int i = u * kFetchThreads + ft;
-        if (i < n4) dst[i] = pt_reg[u];
-      }
-#pragma unroll
-      for (int u = 0; u < kTaWvRegs; ++u) {
-        const int i = u * kFetchThreads + ft;
-        if (wv_pq[u] >= 0) WV[i] = wv_reg[u];
-      }
-    }
-    __syncthreads();
-    // ---- A: Legendre sums (4 pairs x 4 states per item), stored as split BF16 at
-    //      (col, kap = m + lmax) of the F operand
-    {
-      constexpr int NPB = RC / 4, NSB = ST / 4, NCMB = NPB * NSB;
-      for (int it = tid; it < M2 * NCMB; it += kTaThreads) {
-        const int mo = it / NCMB, cmb = it - mo * NCMB;
-        const int pb = cmb / NSB, sb = cmb - pb * NSB;
-        const int am = (mo + 1) >> 1, m = (mo & 1) ? am : -am;
-        const int p0 = 4 * pb, s0l = 4 * sb;
-        float E[4][4], O[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) E[u][v] = O[u][v] = 0.f;
-        const float* prow = PT + (size_t)theta_off(L, am) * RC + p0;
-        for (int l0 = am; l0 <= lmax; l0 += 4) {
-          float4 P4[4], g4[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int l = l0 + i;
-            P4[i] = ld4(prow + (size_t)(l - am) * RC);  // finite past lmax; times 0 below
-            g4[i] = (l <= lmax) ? ld4(Gs + (size_t)(l * l + l + m) * ST + s0l)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float pv[4], gv[4];
-            unpack4(P4[i], pv);
-            unpack4(g4[i], gv);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) {
-                if (i & 1) O[u][v] = fmaf(pv[u], gv[v], O[u][v]);
-                else       E[u][v] = fmaf(pv[u], gv[v], E[u][v]);
-              }
-          }
+    const int k = tile / nst, s0 = (tile % nst) * ST, ns = min(ST, S - s0);
+    const float* wvk = a.wv + (size_t)k * Nt * Np;
+    const int tnext = tile + gridDim.x;
+    const bool has_next = tnext < ntiles;
+    const int kn = tnext / nst, s0n = (tnext % nst) * ST;
+    for (int c0 = 0, ch = 0; ok && c0 < NP; c0 += RC, ++ch) {
+      const bool last = c0 + RC >= NP;
+      __syncthreads();  // the previous chunk's stage D is done with PT and AP
+      if (ft >= 0) {
+        float4* dst = reinterpret_cast<float4*>(PT);
+        const int n4 = (RL + 4) * RC / 4;
+  #pragma unroll
+        for (int u = 0; u < kTaPtRegs; ++u) {
+          const int i = u * kFetchThreads + ft;
+          if (i < n4) dst[i] = pt_reg[u];
         }
-        // columns 16 p + 4 sp + 2 r + e: r = 0 row j (E + O), r = 1 mirror row jb (E - O)
-        float* frow = F32 + (size_t)(m + lmax) * kNCp + 2 * s0l;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float* f = frow + (size_t)(p0 + u) * 16;
-          st4(f, E[u][0] + O[u][0], E[u][1] + O[u][1], E[u][0] - O[u][0], E[u][1] - O[u][1]);
-          st4(f + 4, E[u][2] + O[u][2], E[u][3] + O[u][3], E[u][2] - O[u][2], E[u][3] - O[u][3]);
+  #pragma unroll
+        for (int u = 0; u < kTaWvRegs; ++u) {
+          const int i = u * kFetchThreads + ft;
+          if (wv_pq[u] >= 0) WV[i] = wv_reg[u];
         }
       }
-    }
-    __syncthreads();
-    // F rows -> split BF16 F operand (row = column col, K = kap; kap >= M2 zero). Task = one
-    // column and 8 consecutive kap: 8 lanes fill 128 contiguous bytes of each plane.
-    for (int t = tid; t < NC * (Kb / 8); t += kTaThreads) {
-      const int col = t & (NC - 1), k0 = (t >> 7) * 8;
-      float x[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = (k0 + i < M2) ? F32[(size_t)(k0 + i) * kNCp + col] : 0.f;
-      uint4 h, lo;
-      split2(x[0], x[1], h.x, lo.x);
-      split2(x[2], x[3], h.y, lo.y);
-      split2(x[4], x[5], h.z, lo.z);
-      split2(x[6], x[7], h.w, lo.w);
-      const int off = canon_off(col, k0, NC);
-      *reinterpret_cast<uint4*>(Fhi + off) = h;
-      *reinterpret_cast<uint4*>(Flo + off) = lo;
-    }
-    // the tile's last stage A has read Gs: stream the next tile's G into it
-    if (last && has_next) prefetch_g(kn, s0n);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    // ---- B: grid values on all angles, D_B[col][p] (tensor memory columns 0 .. NB-1)
-    if (tid == 0) {
+      __syncthreads();
+      // ---- A: Legendre sums (4 pairs x 4 states per item) into the FP32 F rows [kap][col],
+      //      kap = m + lmax
+      {
+        constexpr int NPB = RC / 4, NSB = ST / 4, NCMB = NPB * NSB;
+        for (int it = tid; it < M2 * NCMB; it += kTaThreads) {
+          const int mo = it / NCMB, cmb = it - mo * NCMB;
+          const int pb = cmb / NSB, sb = cmb - pb * NSB;
+          const int am = (mo + 1) >> 1, m = (mo & 1) ? am : -am;
+          const int p0 = 4 * pb, s0l = 4 * sb;
+          float E[4][4], O[4][4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u)
+  #pragma unroll
+            for (int v = 0; v < 4; ++v) E[u][v] = O[u][v] = 0.f;
+          const float* prow = PT + (size_t)theta_off(L, am) * RC + p0;
+          for (int l0 = am; l0 <= lmax; l0 += 4) {
+            float4 P4[4], g4[4];
+  #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int l = l0 + i;
+              P4[i] = ld4(prow + (size_t)(l - am) * RC);  // finite past lmax; times 0 below
+              g4[i] = (l <= lmax) ? ld4(Gs + (size_t)(l * l + l + m) * ST + s0l)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+  #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float pv[4], gv[4];
+              unpack4(P4[i], pv);
+              unpack4(g4[i], gv);
+  #pragma unroll
+              for (int u = 0; u < 4; ++u)
+  #pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                  if (i & 1) O[u][v] = fmaf(pv[u], gv[v], O[u][v]);
+                  else       E[u][v] = fmaf(pv[u], gv[v], E[u][v]);
+                }
+            }
+          }
+          // columns 16 p + 4 sp + 2 r + e: r = 0 row j (E + O), r = 1 mirror row jb (E - O)
+          float* frow = F32 + (size_t)(m + lmax) * kNCp + 2 * s0l;
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float* f = frow + (size_t)(p0 + u) * 16;
+            st4(f, E[u][0] + O[u][0], E[u][1] + O[u][1], E[u][0] - O[u][0], E[u][1] - O[u][1]);
+            st4(f + 4, E[u][2] + O[u][2], E[u][3] + O[u][3], E[u][2] - O[u][2], E[u][3] - O[u][3]);
+          }
+        }
+      }
+      __syncthreads();
+      // F rows -> split BF16 F operand (row = column col, K = kap; kap >= M2 zero). Task = one
+      // column and 8 consecutive kap: 8 lanes fill 128 contiguous bytes of each plane.
+      for (int t = tid; t < NC * (Kb / 8); t += kTaThreads) {
+        const int col = t & (NC - 1), k0 = (t >> 7) * 8;
+        float x[8];
+  #pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = (k0 + i < M2) ? F32[(size_t)(k0 + i) * kNCp + col] : 0.f;
+        uint4 h, lo;
+        split2(x[0], x[1], h.x, lo.x);
+        split2(x[2], x[3], h.y, lo.y);
+        split2(x[4], x[5], h.z, lo.z);
+        split2(x[6], x[7], h.w, lo.w);
+        const int off = canon_off(col, k0, NC);
+        *reinterpret_cast<uint4*>(Fhi + off) = h;
+        *reinterpret_cast<uint4*>(Flo + off) = lo;
+      }
+      // the tile's last stage A has read Gs: stream the next tile's G into it
+      if (last && has_next) prefetch_g(kn, s0n);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      // ---- B: grid values on all angles, D_B[col][p] (tensor memory columns 0 .. NB-1)
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(Fhi), a_lo = smem_u32(Flo);
+        const uint32_t b_hi = smem_u32(smem + sh.off_tb);
+        const uint32_t b_lo = b_hi + (uint32_t)NB * Kb * 2;
+        for (int ks = 0; ks < Kb / 16; ++ks) {
+          const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (NB / 8) * 256;
+          const uint64_t dah = make_desc(a_hi + ao, 128, 256), dal = make_desc(a_lo + ao, 128, 256);
+          const uint64_t dbh = make_desc(b_hi + bo, 128, 256), dbl = make_desc(b_lo + bo, 128, 256);
+          mma_bf16(tmem, dah, dbh, idesc_b, ks > 0 ? 1u : 0u);
+          mma_bf16(tmem, dah, dbl, idesc_b, 1u);
+          mma_bf16(tmem, dal, dbh, idesc_b, 1u);
+        }
+        mma_commit(bar_mma);
+      }
+      // the next chunk's rows: their loads run while the MMAs and the later stages compute
+      if (!last) fetch_chunk(wvk, c0 + RC, ch + 1);
+      else if (has_next) fetch_chunk(a.wv + (size_t)kn * Nt * Np, 0, 0);
+      bool w_ok = mbar_wait(bar_mma, phase);
+      phase ^= 1u;
+      if (!w_ok) atomicCAS(err, 0, 2);
+      ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
+      if (!ok) break;
       tc_fence_after();
-      const uint32_t a_hi = smem_u32(Fhi), a_lo = smem_u32(Flo);
-      const uint32_t b_hi = smem_u32(smem + sh.off_tb);
-      const uint32_t b_lo = b_hi + (uint32_t)NB * Kb * 2;
-      for (int ks = 0; ks < Kb / 16; ++ks) {
-        const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (NB / 8) * 256;
-        const uint64_t dah = make_desc(a_hi + ao, 128, 256), dal = make_desc(a_lo + ao, 128, 256);
-        const uint64_t dbh = make_desc(b_hi + bo, 128, 256), dbl = make_desc(b_lo + bo, 128, 256);
-        mma_bf16(tmem, dah, dbh, idesc_b, ks > 0 ? 1u : 0u);
-        mma_bf16(tmem, dah, dbl, idesc_b, 1u);
-        mma_bf16(tmem, dal, dbh, idesc_b, 1u);
+      // ---- W V on the grid; g = W V x D_B as split BF16 at (col, p) of the g operand. Warp:
+      //      lane quarter lq (columns 32 lq ..), half hb of the angles.
+      {
+        const int col = my_col;
+        const int pr = 2 * (col >> 4) + ((col >> 1) & 1);
+        const float* wrow = WV + (size_t)pr * Np;
+        const int half = NB / 2;
+        const bool wv4 = (Np & 3) == 0;  // W V rows 16-byte aligned
+        for (int pb0 = hb * half; pb0 < (hb + 1) * half; pb0 += 32) {
+          float v[32];
+          const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)pb0;
+          tmem_ld16_issue(ta, v);
+          tmem_ld16_issue(ta + 16, v + 16);
+          tmem_ld_wait();
+  #pragma unroll
+          for (int o8 = 0; o8 < 4; ++o8) {
+            const int p0 = pb0 + 8 * o8;
+            float w[8];
+            if (wv4 && p0 + 8 <= Np) {
+              unpack4(ld4(wrow + p0), w);
+              unpack4(ld4(wrow + p0 + 4), w + 4);
+            } else {
+  #pragma unroll
+              for (int i = 0; i < 8; ++i) w[i] = (p0 + i < Np) ? wrow[p0 + i] : 0.f;
+            }
+            const float* vv = v + 8 * o8;
+            uint4 h, lo;
+            split2(vv[0] * w[0], vv[1] * w[1], h.x, lo.x);
+            split2(vv[2] * w[2], vv[3] * w[3], h.y, lo.y);
+            split2(vv[4] * w[4], vv[5] * w[5], h.z, lo.z);
+            split2(vv[6] * w[6], vv[7] * w[7], h.w, lo.w);
+            const int off = canon_off(col, p0, NC);
+            *reinterpret_cast<uint4*>(Ghi + off) = h;
+            *reinterpret_cast<uint4*>(Glo + off) = lo;
+          }
+        }
       }
-      mma_commit(bar_mma);
-    }
-    // the next chunk's rows: their loads run while the MMAs and the later stages compute
-    if (!last) fetch_chunk(wvk, c0 + RC, ch + 1);
-    else if (has_next) fetch_chunk(a.wv + (size_t)kn * Nt * Np, 0, 0);
-    bool w_ok = mbar_wait(bar_mma, phase);
-    phase ^= 1u;
-    if (!w_ok) atomicCAS(err, 0, 2);
-    ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
-    if (!ok) break;
-    tc_fence_after();
-    // ---- W V on the grid; g = W V x D_B as split BF16 at (col, p) of the g operand. Warp:
-    //      lane quarter lq (columns 32 lq ..), half hb of the angles.
-    {
-      const int col = my_col;
-      const int pr = 2 * (col >> 4) + ((col >> 1) & 1);
-      const float* wrow = WV + (size_t)pr * Np;
-      const int half = NB / 2;
-      const bool wv4 = (Np & 3) == 0;  // W V rows 16-byte aligned
-      for (int pb0 = hb * half; pb0 < (hb + 1) * half; pb0 += 32) {
-        float v[32];
-        const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)pb0;
-        tmem_ld16_issue(ta, v);
-        tmem_ld16_issue(ta + 16, v + 16);
-        tmem_ld_wait();
-#pragma unroll
-        for (int o8 = 0; o8 < 4; ++o8) {
-          const int p0 = pb0 + 8 * o8;
-          float w[8];
-          if (wv4 && p0 + 8 <= Np) {
-            unpack4(ld4(wrow + p0), w);
-            unpack4(ld4(wrow + p0 + 4), w + 4);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      // ---- C: phi quadrature. The B operand stacks the hi rows of T^T over its lo rows, so one
+      //      MMA of N = 2 Kb gives hi*hi (columns NB ..) and hi*lo (columns NB + Kb ..), and one of
+      //      N = Kb adds lo*hi to the first block: D_C = sum of the two blocks.
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(Ghi), a_lo = smem_u32(Glo);
+        const uint32_t b = smem_u32(smem + sh.off_tc);
+        for (int ks = 0; ks < NB / 16; ++ks) {
+          const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (2 * Kb / 8) * 256;
+          const uint64_t dah = make_desc(a_hi + ao, 128, 256), dal = make_desc(a_lo + ao, 128, 256);
+          const uint64_t db = make_desc(b + bo, 128, 256);
+          mma_bf16(tmem + (uint32_t)NB, dah, db, idesc_c2, ks > 0 ? 1u : 0u);
+          mma_bf16(tmem + (uint32_t)NB, dal, db, idesc_c, 1u);
+        }
+        mma_commit(bar_mma);
+      }
+      w_ok = mbar_wait(bar_mma, phase);
+      phase ^= 1u;
+      if (!w_ok) atomicCAS(err, 0, 3);
+      ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      // ---- combine the mirror rows: AP[kap][p][0][s] = A_j + A_jb, AP[kap][p][1][s] = A_j - A_jb;
+      //      the mirror of column col is col ^ 2 (lane ^ 2)
+      {
+        const int col = my_col;
+        const int pp = col >> 4, r = (col >> 1) & 1, s = 2 * ((col >> 2) & 3) + (col & 1);
+        const int half = Kb / 2;
+        for (int kb0 = hb * half; kb0 < (hb + 1) * half; kb0 += 16) {
+          float v[16], w[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(NB + kb0);
+          tmem_ld16_issue(ta, v);
+          tmem_ld16_issue(ta + (uint32_t)Kb, w);
+          tmem_ld_wait();
+  #pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += w[i];
+  #pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float other = __shfl_xor_sync(0xffffffffu, v[i], 2);
+            const int kap = kb0 + i;
+            if (kap < M2)
+              AP[(size_t)kap * kAPS + (pp * 2 + r) * ST + s] = r ? other - v[i] : v[i] + other;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      // ---- D: Legendre quadrature into the item's register sums (rows past lmax read as zero)
+      if (d_live) {
+        float pv[kGmLq][RC];
+  #pragma unroll
+        for (int v = 0; v < kGmLq; ++v) {
+          const int l = d_lbase + 2 * v;
+          if (l <= lmax) {
+            const float* prw = PT + (size_t)(theta_off(L, d_am) + l - d_am) * RC;
+            unpack4(ld4(prw), pv[v]);
+            unpack4(ld4(prw + 4), pv[v] + 4);
           } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) w[i] = (p0 + i < Np) ? wrow[p0 + i] : 0.f;
+  #pragma unroll
+            for (int q = 0; q < RC; ++q) pv[v][q] = 0.f;
           }
-          const float* vv = v + 8 * o8;
-          uint4 h, lo;
-          split2(vv[0] * w[0], vv[1] * w[1], h.x, lo.x);
-          split2(vv[2] * w[2], vv[3] * w[3], h.y, lo.y);
-          split2(vv[4] * w[4], vv[5] * w[5], h.z, lo.z);
-          split2(vv[6] * w[6], vv[7] * w[7], h.w, lo.w);
-          const int off = canon_off(col, p0, NC);
-          *reinterpret_cast<uint4*>(Ghi + off) = h;
-          *reinterpret_cast<uint4*>(Glo + off) = lo;
+        }
+        const float* arow = AP + (size_t)d_mi * kAPS + (d_par ? ST : 0);
+  #pragma unroll
+        for (int pp = 0; pp < RC; ++pp) {
+          float av[ST];
+          unpack4(ld4(arow + (size_t)pp * 2 * ST), av);
+          unpack4(ld4(arow + (size_t)pp * 2 * ST + 4), av + 4);
+  #pragma unroll
+          for (int v = 0; v < kGmLq; ++v)
+  #pragma unroll
+            for (int q = 0; q < ST; ++q) dacc[v][q] = fmaf(pv[v][pp], av[q], dacc[v][q]);
         }
       }
     }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    // ---- C: phi quadrature. The B operand stacks the hi rows of T^T over its lo rows, so one
-    //      MMA of N = 2 Kb gives hi*hi (columns NB ..) and hi*lo (columns NB + Kb ..), and one of
-    //      N = Kb adds lo*hi to the first block: D_C = sum of the two blocks.
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a_hi = smem_u32(Ghi), a_lo = smem_u32(Glo);
-      const uint32_t b = smem_u32(smem + sh.off_tc);
-      for (int ks = 0; ks < NB / 16; ++ks) {
-        const uint32_t ao = ks * (NC / 8) * 256, bo = ks * (2 * Kb / 8) * 256;
-        const uint64_t dah = make_desc(a_hi + ao, 128, 256), dal = make_desc(a_lo + ao, 128, 256);
-        const uint64_t db = make_desc(b + bo, 128, 256);
-        mma_bf16(tmem + (uint32_t)NB, dah, db, idesc_c2, ks > 0 ? 1u : 0u);
-        mma_bf16(tmem + (uint32_t)NB, dal, db, idesc_c, 1u);
-      }
-      mma_commit(bar_mma);
-    }
-    w_ok = mbar_wait(bar_mma, phase);
-    phase ^= 1u;
-    if (!w_ok) atomicCAS(err, 0, 3);
-    ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
     if (!ok) break;
-    tc_fence_after();
-    // ---- combine the mirror rows: AP[kap][p][0][s] = A_j + A_jb, AP[kap][p][1][s] = A_j - A_jb;
-    //      the mirror of column col is col ^ 2 (lane ^ 2)
-    {
-      const int col = my_col;
-      const int pp = col >> 4, r = (col >> 1) & 1, s = 2 * ((col >> 2) & 3) + (col & 1);
-      const int half = Kb / 2;
-      for (int kb0 = hb * half; kb0 < (hb + 1) * half; kb0 += 16) {
-        float v[16], w[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(NB + kb0);
-        tmem_ld16_issue(ta, v);
-        tmem_ld16_issue(ta + (uint32_t)Kb, w);
-        tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += w[i];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float other = __shfl_xor_sync(0xffffffffu, v[i], 2);
-          const int kap = kb0 + i;
-          if (kap < M2)
-            AP[(size_t)kap * kAPS + (pp * 2 + r) * ST + s] = r ? other - v[i] : v[i] + other;
-        }
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    // ---- D: Legendre quadrature into the item's register sums (rows past lmax read as zero)
+    // the item's sums go straight to G (8 consecutive states of one (l, m) row), then reset
     if (d_live) {
-      float pv[kGmLq][RC];
-#pragma unroll
+      const bool vec = (S & 3) == 0 && ns == ST && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+  #pragma unroll
       for (int v = 0; v < kGmLq; ++v) {
         const int l = d_lbase + 2 * v;
         if (l <= lmax) {
-          const float* prw = PT + (size_t)(theta_off(L, d_am) + l - d_am) * RC;
-          unpack4(ld4(prw), pv[v]);
-          unpack4(ld4(prw + 4), pv[v] + 4);
-        } else {
-#pragma unroll
-          for (int q = 0; q < RC; ++q) pv[v][q] = 0.f;
+          float* gr = G + ((size_t)k * L2 + l * l + l + d_m) * S + s0;
+          if (vec) {
+            st4(gr, dacc[v][0], dacc[v][1], dacc[v][2], dacc[v][3]);
+            st4(gr + 4, dacc[v][4], dacc[v][5], dacc[v][6], dacc[v][7]);
+          } else {
+  #pragma unroll
+            for (int q = 0; q < ST; ++q)
+              if (q < ns) gr[q] = dacc[v][q];
+          }
         }
-      }
-      const float* arow = AP + (size_t)d_mi * kAPS + (d_par ? ST : 0);
-#pragma unroll
-      for (int pp = 0; pp < RC; ++pp) {
-        float av[ST];
-        unpack4(ld4(arow + (size_t)pp * 2 * ST), av);
-        unpack4(ld4(arow + (size_t)pp * 2 * ST + 4), av + 4);
-#pragma unroll
-        for (int v = 0; v < kGmLq; ++v)
-#pragma unroll
-          for (int q = 0; q < ST; ++q) dacc[v][q] = fmaf(pv[v][pp], av[q], dacc[v][q]);
+  #pragma unroll
+        for (int q = 0; q < ST; ++q) dacc[v][q] = 0.f;
       }
     }
-  }
-  if (!ok) break;
-  // the item's sums go straight to G (8 consecutive states of one (l, m) row), then reset
-  if (d_live) {
-    const bool vec = (S & 3) == 0 && ns == ST && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
-#pragma unroll
-    for (int v = 0; v < kGmLq; ++v) {
-      const int l = d_lbase + 2 * v;
-      if (l <= lmax) {
-        float* gr = G + ((size_t)k * L2 + l * l + l + d_m) * S + s0;
-        if (vec) {
-          st4(gr, dacc[v][0], dacc[v][1], dacc[v][2], dacc[v][3]);
-          st4(gr + 4, dacc[v][4], dacc[v][5], dacc[v][6], dacc[v][7]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < ST; ++q)
-            if (q < ns) gr[q] = dacc[v][q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < ST; ++q) dacc[v][q] = 0.f;
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();  // the next tile's Gs is complete
+    cp_async_wait_all();
+    __syncthreads();  // the next tile's Gs is complete
   }
   cp_async_wait_all();
   tc_fence_before();
