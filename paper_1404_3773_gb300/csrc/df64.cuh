@@ -12,7 +12,29 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <cstring>
+
 namespace cs {
+
+__host__ __device__ inline uint64_t df64_bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ inline float df64_float_of(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
 
 // the df64 overload of fma below must not hide the FP64/FP32 ones for unqualified calls
 using ::fma;
@@ -21,8 +43,32 @@ struct __align__(8) df64 {
   float hi, lo;
   df64() = default;
   __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
-  // exact split of a double into hi + lo (lo carries the next 24 bits)
-  __host__ __device__ df64(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  // split of a double into hi = fl(x) and lo = fl(x - hi), both rounded to nearest even (lo
+  // carries the next 24 bits). Where hi and the unit of x's last bit are normal floats
+  // (2^-74 <= |x| < 2^126) this is done on the integer and FP32 pipes from x's bits: hi is
+  // x's top 24 significant bits rounded to nearest even, and x - hi is the remaining 29-bit
+  // integer (minus 2^29 when hi rounded up) times 2^(e - 1075), converted with one rounding.
+  // Elsewhere the same values come from FP64 arithmetic, which GB300 runs at 1/64 rate.
+  __host__ __device__ df64(double x) {
+    const uint64_t b = df64_bits_of(x);
+    const int e = (int)((b >> 52) & 0x7FF);  // biased exponent
+    if (e >= 949 && e <= 1148) {
+      const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+      const uint32_t r = (uint32_t)(mant & 0x1FFFFFFFu);  // the 29 bits below hi
+      uint32_t hb = ((uint32_t)(b >> 63) << 31) | ((uint32_t)(e - 896) << 23) |
+                    (uint32_t)(mant >> 29);
+      const bool up = r > 0x10000000u || (r == 0x10000000u && (hb & 1u));
+      hb += up ? 1u : 0u;  // a carry moves into the exponent, as rounding does
+      int res = (int)r - (up ? 0x20000000 : 0);  // |res| <= 2^28
+      if (b >> 63) res = -res;                    // signed residual; zero stays +0
+      const float scale = df64_float_of((uint32_t)(e - 1075 + 127) << 23);  // 2^(e - 1075)
+      hi = df64_float_of(hb);
+      lo = (float)res * scale;
+    } else {
+      hi = (float)x;
+      lo = (float)(x - (double)(float)x);
+    }
+  }
   __host__ __device__ df64(int x) : df64((double)x) {}
   __host__ __device__ double to_double() const { return (double)hi + (double)lo; }
 };

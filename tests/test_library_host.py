@@ -113,3 +113,21 @@ def test_atom_descriptors_match_oracle():
     got = cs.cs_atom_descriptors(atoms, mu, 0.5)
     ref = LD.descriptors(atoms, mu, 0.5)
     assert np.max(np.abs(got - ref)) <= 1e-13
+
+
+def test_df64_split_of_a_double_matches_fp64_rounding(tmp_path):
+    """The double-float split of a double takes an integer/FP32 path where its parts are normal
+    floats and FP64 arithmetic elsewhere; both give hi = fl(x), lo = fl(x - hi) bit for bit.
+    Checked by a host program built with nvcc (no GPU needed)."""
+    import shutil
+    import subprocess
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    src = os.path.join(os.path.dirname(__file__), "native", "df64_split_check.cu")
+    exe = str(tmp_path / "df64_split_check")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, src], check=True,
+                   capture_output=True, timeout=300)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout[-2000:]
