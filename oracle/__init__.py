@@ -25,6 +25,9 @@ primitives:
   scf.py          - electron density, Hartree potential (eqs. hartree_calc1,
                     zeta_definition), LDA exchange-correlation, Fermi-Dirac occupations,
                     Anderson mixing and the SCF loop (Sec. 2.1, 2.2.5, 2.3.1, 3.4.1)
+  ozaki.py        - FP64 products A^T B of the dense steps (Sec. 3.2) from exact products of
+                    small-integer slices (Ozaki, Ogita, Oishi, Rump 2012), with the FP32
+                    accumulation bound a tensor-core kernel relies on
 
 Parity status: every function is pinned by the -m "not gpu" tests in tests/ against
 closed forms, an independent library (scipy.special), brute force, or invariants.
