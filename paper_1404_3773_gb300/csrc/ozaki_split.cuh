@@ -113,4 +113,32 @@ __host__ __device__ inline void oz_slices(double x, int E, int beta, int s, int*
   }
 }
 
+// 2^e as a double (|e| <= 1022)
+__host__ __device__ inline double oz_pow2(int e) {
+  const uint64_t b = (uint64_t)(e + 1023) << 52;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  std::memcpy(&v, &b, sizeof v);
+  return v;
+#endif
+}
+
+// One entry of C = A^T B from the exact slice products S[k * s + l] = a_k^T b_l of its column
+// pair (column exponents E of A, F of B): the sum over the pairs with k + l <= s - 1, smallest
+// terms first (k + l from s - 1 down to 0, k ascending within), in FP64. Each term
+// 2^(E + F - 2 (beta - 1) - (k + l) beta) S is exact; the additions are the only roundings.
+// Requires |S| < 2^53 and the exponents inside the normal FP64 range.
+__host__ __device__ inline double oz_combine(const int64_t* S, int E, int F, int beta, int s) {
+  double c = 0.0;
+  for (int m = s - 1; m >= 0; --m)
+    for (int k = 0; k <= m; ++k) {
+      const int l = m - k;
+      const double term = (double)S[k * s + l] * oz_pow2(E + F - 2 * (beta - 1) - m * beta);
+      c = c + term;
+    }
+  return c;
+}
+
 }  // namespace cs

@@ -67,3 +67,32 @@ def test_integer_slices_match_oracle_bit_for_bit(checker, tmp_path, beta, s):
         a.astype(np.int64).tofile(f)
     r = subprocess.run([checker, str(path)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def gram_checker(tmp_path_factory):
+    src = os.path.join(os.path.dirname(__file__), "native", "ozaki_gram_check.cu")
+    exe = str(tmp_path_factory.mktemp("ozg") / "ozaki_gram_check")
+    subprocess.run([_nvcc(), "-O2", "-std=c++17", "-o", exe, src], check=True,
+                   capture_output=True, timeout=300)
+    return exe
+
+
+@pytest.mark.parametrize("beta,s", [(9, 6), (8, 7)])
+def test_slice_product_pipeline_matches_oracle_gram_bit_for_bit(gram_checker, tmp_path, beta,
+                                                                 s):
+    """Split, exact integer slice products and oz_combine reproduce oracle.gram exactly: the
+    kernel's only rounding is the FP64 sum over pairs, in the oracle's order."""
+    rng = np.random.default_rng(77 + beta)
+    A = _columns(rng, 300)
+    B = _columns(rng, 300)[:, ::-1].copy()
+    B[:, 1] = A[:, 2]  # a shared column (a Gram diagonal entry)
+    C = ozaki.gram(A, B, beta, s)
+    path = tmp_path / "gram.bin"
+    with open(path, "wb") as f:
+        np.array([A.shape[0], A.shape[1], B.shape[1], beta, s], dtype=np.int32).tofile(f)
+        A.ravel(order="F").astype(np.float64).tofile(f)
+        B.ravel(order="F").astype(np.float64).tofile(f)
+        np.ascontiguousarray(C).astype(np.float64).tofile(f)
+    r = subprocess.run([gram_checker, str(path)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:]
