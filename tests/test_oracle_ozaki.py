@@ -155,3 +155,18 @@ def test_zero_and_power_of_two_columns():
 def test_digits_needed():
     assert ozaki.digits_needed(9) == 6 and ozaki.digits_needed(8) == 7
     assert ozaki.digits_needed(7) == 8
+
+
+def test_rotation_shape_matches_exact_product():
+    """The dense step's rotations X Q (d x n times n x n) are the same scheme with the
+    contraction over n: gram(X^T, Q), with one exponent per row of X. Checked against exact
+    rational arithmetic within the bound."""
+    rng = np.random.default_rng(2024)
+    X = rng.standard_normal((12, 5)) * np.ldexp(1.0, rng.integers(-5, 6, size=12))[:, None]
+    Q = np.linalg.qr(rng.standard_normal((5, 5)))[0]
+    C = ozaki.gram(X.T, Q)
+    Ce = ozaki.exact_gram(X.T, Q)
+    bound = ozaki.error_bound(X.T, Q, 9, 6) + np.abs(Ce) * 2.0 ** -53
+    assert C.shape == (12, 5)
+    assert np.all(np.abs(C - Ce) <= bound)
+    assert np.max(np.abs(C - X @ Q) / (np.abs(X) @ np.abs(Q))) < 64 * 2.0 ** -53
