@@ -96,3 +96,49 @@ def test_slice_product_pipeline_matches_oracle_gram_bit_for_bit(gram_checker, tm
         np.ascontiguousarray(C).astype(np.float64).tofile(f)
     r = subprocess.run([gram_checker, str(path)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def plan_checker(tmp_path_factory):
+    src = os.path.join(os.path.dirname(__file__), "native", "ozaki_plan_check.cu")
+    exe = str(tmp_path_factory.mktemp("ozp") / "ozaki_plan_check")
+    subprocess.run([_nvcc(), "-O2", "-std=c++17", "-o", exe, src], check=True,
+                   capture_output=True, timeout=300)
+    return exe
+
+
+def _run_plan(plan_checker, tmp_path, A, B, beta, s, chunk):
+    C = ozaki.gram(A, B, beta, s)
+    path = tmp_path / "plan.bin"
+    with open(path, "wb") as f:
+        np.array([A.shape[0], A.shape[1], B.shape[1], beta, s, chunk], dtype=np.int32).tofile(f)
+        A.ravel(order="F").astype(np.float64).tofile(f)
+        B.ravel(order="F").astype(np.float64).tofile(f)
+        np.ascontiguousarray(C).astype(np.float64).tofile(f)
+    return subprocess.run([plan_checker, str(path)], capture_output=True, text=True, timeout=600)
+
+
+def test_chunked_slice_product_plan_is_exact_and_matches_oracle(plan_checker, tmp_path):
+    """The planned kernel layout, beta = 7 and s = 8 with 4096-row chunks (the FP32 exactness
+    length 2^(26 - 2 beta)), reproduces oracle.gram bit for bit over 9000 rows (three chunks,
+    the last ragged), with no running sum past 2^24, including the worst case of every slice at
+    its bound."""
+    rng = np.random.default_rng(4096)
+    A = _columns(rng, 9000)[:, :6]
+    B = _columns(rng, 9000)[:, 2:8].copy()
+    B[:, 0] = A[:, 1]
+    r = _run_plan(plan_checker, tmp_path, A, B, 7, 8, ozaki.max_exact_chunk(7))
+    assert r.returncode == 0, r.stdout[-2000:]
+    # every leading slice at +2^(beta - 1) = 64: the products reach 2^12 and a full chunk of
+    # them reaches 2^24, the limit
+    W = np.full((9000, 2), 1.0)
+    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, ozaki.max_exact_chunk(7))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+def test_chunk_past_the_exactness_length_is_flagged(plan_checker, tmp_path):
+    """Twice the exactness length lets the worst-case running sum pass 2^24: the check that
+    guards the kernel's chunk length fails, as it must."""
+    W = np.full((9000, 2), 1.0)
+    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, 2 * ozaki.max_exact_chunk(7))
+    assert r.returncode != 0 and "beyond 2^24" in r.stdout
