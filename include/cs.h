@@ -72,8 +72,9 @@ typedef enum {
   CS_MIXED_BF16 = 2  /* FP32 storage; the per-l radial contractions on the tensor cores
                         (tcgen05) with operands split into two BF16 terms (hi + lo, three
                         products, FP32 accumulation), and so are the two projector
-                        products; angular sums and the recurrence in FP32. Blocks are
-                        float.                                                           */,
+                        products and, up to lmax 31, the angular block's phi synthesis and
+                        phi quadrature; the Legendre sums and the recurrence in FP32.
+                        Blocks are float.                                                */,
   CS_DF64 = 3        /* FP64 storage (blocks are double); H X computed in double-float
                         arithmetic on the FP32 pipe (each value an unevaluated sum of two
                         floats, about 48 significant bits; Dekker/Knuth error-free
