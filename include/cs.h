@@ -169,7 +169,10 @@ cs_status cs_workspace_bytes(const cs_ctx* ctx, int n_s, cs_precision prec, size
  * transforms with the pointwise W*V product, per-l radial analysis GEMMs (eq.
  * Arlm_to_coeff), plus 1/2 Lambda X and the projector pair. X, HX: DEVICE, d x n_s,
  * leading dimension ld, element type per prec; X and HX must not overlap.
- * Requires cs_set_potential first (CS_ERR_STATE otherwise). */
+ * Requires cs_set_potential first (CS_ERR_STATE otherwise). The tensor-core kernels of
+ * CS_MIXED_BF16 bound every wait; one that expires leaves HX invalid, sets the context's
+ * device error word and still returns CS_OK (the call does not synchronise): mixed-precision
+ * callers read cs_device_error after synchronising (cs_cheb_filter likewise). */
 cs_status cs_apply_H(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
                      cs_precision prec, void* work, cs_stream stream);
 
@@ -180,16 +183,33 @@ cs_status cs_cheb_filter(cs_ctx* ctx, int n_s, void* X, long long ld, int degree
                          double b, double a0, cs_precision prec, void* work,
                          cs_stream stream);
 
+/* The same filter p_m(H) X for a block of Ritz vectors, in residual form (Sec. 3.2.1; the
+ * algebra is this library's, the filter is the paper's). With R = H X - X Theta and s_i the
+ * scaled filter polynomials evaluated at the Ritz values,
+ *   p_m(H) X = X s_m(Theta) + D_m,  D_0 = 0,  D_1 = (sigma_1/e) R,
+ *   D_{i+1} = (2 sigma_{i+1}/e) [(H - c) D_i + R s_i(Theta)] - sigma_i sigma_{i+1} D_{i-1},
+ * an identity for any Theta. Only D meets H, in precision prec, so the rounding of an FP32 or
+ * mixed H.X is relative to ||R||, not ||X||: as the Ritz pairs converge the filter's error
+ * shrinks with them. It takes degree - 1 H.X products (D_1 needs none).
+ * X: DEVICE FP64 d x n_s (ld), on entry the block, on exit p_m(H) X. HX: DEVICE FP64 H X
+ * (ldh >= d), read only. theta: DEVICE n_s doubles. 1 <= degree <= 64, a0 < a < b as in
+ * cs_cheb_filter. prec: CS_FP64, CS_DF64, CS_FP32 or CS_MIXED_BF16 (the arithmetic of the D
+ * recurrence). work: cs_workspace_bytes(ctx, n_s, prec). */
+cs_status cs_cheb_filter_ritz(cs_ctx* ctx, int n_s, double* X, long long ld, const double* HX,
+                              long long ldh, const double* theta, int degree, double a, double b,
+                              double a0, cs_precision prec, void* work, cs_stream stream);
+
 /* Cholesky-QR with column scaling (Sec. 3.1.1, 3.2.1), applied twice: X <- X D R^{-1}
  * with D = diag(X^T X)^(-1/2), D X^T X D = R^T R. X: DEVICE FP64 d x n_s (ld).
  * Synchronising. CS_ERR_CHOLESKY if a pivot is not positive. */
 cs_status cs_cholqr(cs_ctx* ctx, int n_s, double* X, long long ld, void* work,
                     cs_stream stream);
 
-/* Rayleigh-Ritz on an orthonormal FP64 block (Sec. 3.2.1): HX = H X (FP64), Hs =
- * sym(X^T H X) = Q Theta Q^T (Jacobi eigensolver on the device), X <- X Q, and the
- * residual norms ||H x_i - theta_i x_i||_2. theta, resid: DEVICE n_s doubles (ascending
- * theta). If HX_out is not NULL it receives H X Q (DEVICE d x n_s, ld). Synchronising. */
+/* Rayleigh-Ritz on an orthonormal FP64 block (Sec. 3.2.1): HX = H X (precision set by
+ * cs_set_rr_precision), Hs = sym(X^T H X) = Q Theta Q^T (device eigensolver), X <- X Q, and
+ * the residual norms ||H x_i - theta_i x_i||_2. theta, resid: DEVICE n_s doubles (ascending
+ * theta). If HX_out is not NULL it receives H X Q (DEVICE d x n_s, ld; must not overlap X).
+ * Synchronising. */
 cs_status cs_rayleigh_ritz(cs_ctx* ctx, int n_s, double* X, long long ld, double* theta,
                            double* resid, double* HX_out, void* work, cs_stream stream);
 
@@ -201,7 +221,10 @@ cs_status cs_lanczos_bound(cs_ctx* ctx, int k, const double* v0, double* b, doub
 
 /* ChFSI loop (Sec. 3.2.1): Lanczos bounds from v0, then [filter (precision prec) ->
  * Cholesky-QR (FP64) -> Rayleigh-Ritz (FP64)] until the largest residual of the n_want
- * lowest Ritz pairs is <= tol or max_iter iterations. X: DEVICE FP64 d x n_s (ld), the
+ * lowest Ritz pairs is <= tol or max_iter iterations. With prec CS_FP32 or CS_MIXED_BF16 (and
+ * degree <= 64) every iteration after the first filters in residual form (as
+ * cs_cheb_filter_ritz, from the previous iteration's Ritz values and H X), so its residuals
+ * fall below the filter precision's level; FP64 and double-float filters stay plain. X: DEVICE FP64 d x n_s (ld), the
  * initial block on entry, the Ritz vectors on exit. theta, resid: DEVICE n_s doubles.
  * *iters receives the iteration count. First pass: a0 = smallest Lanczos Ritz value,
  * a = a0 + (b - a0)/10; later passes: a = largest Ritz value, a0 = smallest.
@@ -217,6 +240,16 @@ cs_status cs_chfsi(cs_ctx* ctx, int n_s, int n_want, double* X, long long ld, in
 cs_status cs_chfsi_step(cs_ctx* ctx, int n_s, double* X, long long ld, int degree, double a,
                         double b, double a0, cs_precision prec, double* theta, double* resid,
                         void* work, cs_stream stream);
+
+/* One ChFSI iteration (Sec. 3.2.1) whose filter takes the residual form (cs_cheb_filter_ritz):
+ * X, HX, theta in: Ritz vectors (DEVICE FP64 d x n_s, ld), their H X (same shape and ld) and
+ * Ritz values (DEVICE n_s); out: the next Ritz vectors, their H X and Ritz values, and resid
+ * (DEVICE n_s) the residual norms. Cholesky-QR and Rayleigh-Ritz as in cs_chfsi_step; the
+ * outgoing H X is Rayleigh-Ritz's (cs_set_rr_precision) rotated by Q. 1 <= degree <= 64.
+ * Synchronising. */
+cs_status cs_chfsi_step_ritz(cs_ctx* ctx, int n_s, double* X, double* HX, long long ld,
+                             int degree, double a, double b, double a0, cs_precision prec,
+                             double* theta, double* resid, void* work, cs_stream stream);
 
 /* LOBPCG (Sec. 3.1) with the diagonal Teter-Payne-Allan preconditioner (Sec. 3.1.2), FP64:
  * the lowest n_s eigenpairs of H from the block X (DEVICE FP64 d x n_s, ld; Ritz vectors on
@@ -259,11 +292,13 @@ cs_status cs_profile_end(cs_ctx* ctx, double* ms, long long* launches);
  * its scratch is a 32 MiB array compiled into the library, present on every GPU that loads
  * the library until the process exits; it calls no allocation routine. The paper has no
  * counterpart; this is a deployment variant of the same H.X kernels.
- * Limits and rules: N_r (lmax+1)^2 n_s x element size must be <= 32 MiB (else
- * CS_ERR_ARG); no projectors (CS_ERR_STATE if set); the first call on a device looks up the
- * array's device address, so make it before any stream capture on that device; all calls
- * on a device share the array (it keeps the last call's contents; nothing in it must start
- * at zero), so calls that overlap on the GPU race and must be serialised. Arguments as
+ * Limits and rules: prec must be CS_FP64 or CS_FP32 (CS_ERR_ARG otherwise); N_r (lmax+1)^2
+ * n_s x element size must be <= 32 MiB (else CS_ERR_ARG); no projectors (CS_ERR_STATE if
+ * set); the first call on a device looks up the array's device address and keeps it, so make
+ * that call before any stream capture on that device, and make no call on a device after a
+ * cudaDeviceReset of it; all calls on a device share the array (it keeps the last call's
+ * contents; nothing in it must start at zero), so calls that overlap on the GPU race and must
+ * be serialised. The caller's current device is restored on return. Other arguments as
  * cs_apply_H without `work`. */
 cs_status cs_apply_H_noalloc(cs_ctx* ctx, int n_s, const void* X, void* HX, long long ld,
                              cs_precision prec, cs_stream stream);

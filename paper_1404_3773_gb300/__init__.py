@@ -23,7 +23,7 @@ __all__ = [
     "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
-    "cs_chfsi_step", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
+    "cs_chfsi_step", "cs_cheb_filter_ritz", "cs_chfsi_step_ritz", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
     "cs_set_rr_precision", "cs_set_dense_precision",
     "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
@@ -114,6 +114,9 @@ _SIGS = {
                       ctypes.POINTER(_i), _vp, _vp]),
     "cs_apply_H_noalloc": (_i, [_vp, _i, _vp, _vp, _ll, _i, _vp]),
     "cs_chfsi_step": (_i, [_vp, _i, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp, _vp, _vp]),
+    "cs_cheb_filter_ritz": (_i, [_vp, _i, _vp, _ll, _vp, _ll, _vp, _i, _d, _d, _d, _i, _vp, _vp]),
+    "cs_chfsi_step_ritz": (_i, [_vp, _i, _vp, _vp, _ll, _i, _d, _d, _d, _i, _vp, _vp, _vp,
+                                _vp]),
     "cs_profile_begin": (_i, [_vp]),
     "cs_device_error": (_i, [_vp, ctypes.POINTER(_i)]),
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
@@ -416,6 +419,33 @@ def cs_chfsi_step(ctx: Context, X: torch.Tensor, degree: int, a: float, b: float
     ctx.check(_lib.cs_chfsi_step(ctx.handle, n_s, _ptr(X), ld, int(degree), float(a), float(b),
                                  float(a0), int(precision), _ptr(theta), _ptr(resid),
                                  _ptr(work), _stream_ptr(stream)))
+
+
+def cs_cheb_filter_ritz(ctx: Context, X: torch.Tensor, HX: torch.Tensor, theta: torch.Tensor,
+                        degree: int, a: float, b: float, a0: float, precision: int = CS_FP64,
+                        work=None, stream=None):
+    """p_m(H) X in residual form: X (FP64 Ritz vectors, filtered in place), HX = H X (FP64),
+    theta = Ritz values (device, float64)."""
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    _, ldh = _check_block(ctx, HX, torch.float64)
+    assert HX.shape[0] == n_s and theta.is_cuda and theta.dtype == torch.float64
+    work = ctx.workspace(n_s, precision) if work is None else work
+    ctx.check(_lib.cs_cheb_filter_ritz(ctx.handle, n_s, _ptr(X), ld, _ptr(HX), ldh, _ptr(theta),
+                                       int(degree), float(a), float(b), float(a0),
+                                       int(precision), _ptr(work), _stream_ptr(stream)))
+
+
+def cs_chfsi_step_ritz(ctx: Context, X: torch.Tensor, HX: torch.Tensor, degree: int, a: float,
+                       b: float, a0: float, theta: torch.Tensor, resid: torch.Tensor,
+                       precision: int = CS_FP64, work=None, stream=None):
+    """One ChFSI iteration with the residual-form filter; X, HX, theta in/out."""
+    n_s, ld = _check_block(ctx, X, torch.float64)
+    assert HX.shape == X.shape and HX.stride() == X.stride() and HX.dtype == X.dtype
+    work = ctx.workspace(n_s, precision) if work is None else work
+    ctx.check(_lib.cs_chfsi_step_ritz(ctx.handle, n_s, _ptr(X), _ptr(HX), ld, int(degree),
+                                      float(a), float(b), float(a0), int(precision),
+                                      _ptr(theta), _ptr(resid), _ptr(work),
+                                      _stream_ptr(stream)))
 
 
 def cs_device_error(ctx: Context) -> int:

@@ -607,13 +607,11 @@ cudaError_t launch_angular_tc(const AngArgs<float>& a, const void* tphi, float* 
   cudaError_t e = cudaFuncSetAttribute(k_angular_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)s.total);
   if (e != cudaSuccess) return e;
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-  }
+  // SM count of the current device, looked up on every launch (no shared state)
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
   const int ntiles = ((a.S + kST - 1) / kST) * a.n_r;
   const int grid = ntiles < nsm ? ntiles : nsm;  // persistent: one CTA per SM
   k_angular_tc<<<grid, kTaThreads, s.total, stream>>>(

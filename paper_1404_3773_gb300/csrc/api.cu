@@ -25,10 +25,12 @@ thread_local std::string g_init_error;
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, kbtc, total;
+  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, kbtc, total;
 };
 
 constexpr int kMaxLanczos = 64;
+// largest degree of the residual-form filter (its weight table is sized for it)
+constexpr int kMaxRitzDegree = 64;
 
 Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   const HostTables& T = c->host;
@@ -57,6 +59,10 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.small = take((12 * mm * mm + 32 * mm + 4096) * 8);
   o.lanV = take(d * (kMaxLanczos + 2) * 8);
   o.status = take(64 * sizeof(int));
+  // H X of the current Ritz vectors, kept between ChFSI iterations (residual-form filter)
+  o.HXr = take(d * ns * 8);
+  // weights s_i(theta_j) of the residual-form filter: FP64 table and one in the block type
+  o.chw = take((size_t)(kMaxRitzDegree + 1) * ns * 16);
   // last, so that every other offset is the same for both precisions
   auto is_f32 = [](cs_precision p) { return p == CS_FP32 || p == CS_MIXED_BF16; };
   const bool reduced = is_f32(prec) || is_f32(c->rr_prec);
@@ -206,7 +212,7 @@ cs_status upload_tables(cs_ctx* c) {
 template <typename T>
 cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long long ldo, int mode,
                   double cA, double cB, double csh, const T* Yprev, char* work, cudaStream_t st,
-                  bool tc = false) {
+                  bool tc = false, const T* src = nullptr, const T* src_w = nullptr) {
   const HostTables& H = c->host;
   DevTables<T>& D = tables<T>(c);
   const Layout lay = layout(c, n_s, CS_FP64);
@@ -279,6 +285,9 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   ep.cA = (T)cA;
   ep.cB = (T)cB;
   ep.cshift = (T)csh;
+  ep.src = src;
+  ep.src_w = src_w;
+  ep.src_ld = H.d;
   if (tc_rad) {
     CS_LAUNCH_CLS(c, prof_cls<T>(2), 1, launch_tc_radial_anal(tt, H, reinterpret_cast<const float*>(G), n_s,
                                                  *reinterpret_cast<const Epilogue<float>*>(&ep),
@@ -318,6 +327,62 @@ cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a
   }
   if (cur != X) CS_LAUNCH(c, 1, launch_copy_block<T>(cur, ldc, X, ld, H.d, n_s, st));
   return CS_OK;
+}
+
+// Residual form of the filter (cheb_ritz.cu): X <- X s_m(Theta) + D_m for Ritz vectors X
+// (FP64), their H X (FP64) and Ritz values theta (device). The deviation D runs through the
+// recurrence in the block type T, with R = H X - X Theta as the source of each step: degree - 1
+// H.X products (D_1 needs none). Buffers: R in tmp; D alternates between two block buffers
+// (X32 and Yalt for float, Yalt and HX for double and double-float).
+template <typename T>
+cs_status cheb_ritz_core(cs_ctx* c, int n_s, double* X, long long ld, const double* HX,
+                         long long ldh, const double* theta, int degree, double a, double b,
+                         double a0, char* work, cudaStream_t st, bool tc = false) {
+  const HostTables& H = c->host;
+  const cs_precision pl = std::is_same<T, float>::value ? (tc ? CS_MIXED_BF16 : CS_FP32) : CS_FP64;
+  const Layout lay = layout(c, n_s, pl);
+  T* R = reinterpret_cast<T*>(work + lay.tmp);
+  T* Da = std::is_same<T, float>::value ? reinterpret_cast<T*>(work + lay.X32)
+                                        : reinterpret_cast<T*>(work + lay.Yalt);
+  T* Db = std::is_same<T, float>::value ? reinterpret_cast<T*>(work + lay.Yalt)
+                                        : reinterpret_cast<T*>(work + lay.HX);
+  double* wd = reinterpret_cast<double*>(work + lay.chw);
+  T* wt = reinterpret_cast<T*>(wd + (size_t)(kMaxRitzDegree + 1) * n_s);
+  const double cc = 0.5 * (a + b), e = 0.5 * (b - a);
+  const double s1 = e / (a0 - cc);
+  CS_LAUNCH(c, 1, launch_cheb_weights<T>(theta, n_s, degree, cc, e, s1, wd, wt, st));
+  CS_LAUNCH(c, 1, launch_ritz_residual<T>(X, ld, HX, ldh, theta, H.d, n_s, s1 / e, R, Da, st));
+  T* cur = Da;
+  T* prev = Db;
+  double sig = s1;
+  for (int i = 1; i < degree; ++i) {
+    const double sn = 1.0 / (2.0 / s1 - sig);
+    // D_{i+1} = (2 sn/e)[(H - c) D_i + s_i(Theta) R] - sig sn D_{i-1}   (D_0 = 0)
+    cs_status r = hx_core<T>(c, n_s, cur, H.d, prev, H.d, EP_CHEB, 2.0 * sn / e, sig * sn, cc,
+                             i == 1 ? nullptr : prev, work, st, tc, R, wt + (size_t)i * n_s);
+    if (r != CS_OK) return r;
+    std::swap(prev, cur);
+    sig = sn;
+  }
+  CS_LAUNCH(c, 1, launch_ritz_combine<T>(X, ld, cur, H.d, n_s, wd + (size_t)degree * n_s, st));
+  return CS_OK;
+}
+
+cs_status cheb_ritz_dispatch(cs_ctx* c, int n_s, double* X, long long ld, const double* HX,
+                             long long ldh, const double* theta, int degree, double a, double b,
+                             double a0, cs_precision prec, char* work, cudaStream_t st) {
+  switch (prec) {
+    case CS_FP64:
+      return cheb_ritz_core<double>(c, n_s, X, ld, HX, ldh, theta, degree, a, b, a0, work, st);
+    case CS_DF64:
+      return cheb_ritz_core<df64>(c, n_s, X, ld, HX, ldh, theta, degree, a, b, a0, work, st);
+    case CS_FP32:
+    case CS_MIXED_BF16:
+      return cheb_ritz_core<float>(c, n_s, X, ld, HX, ldh, theta, degree, a, b, a0, work, st,
+                                   prec == CS_MIXED_BF16);
+    default:
+      return fail(c, CS_ERR_ARG, "unknown precision");
+  }
 }
 
 // Gram matrix and block rotation of the ChFSI iteration in the context's dense precision
@@ -360,7 +425,9 @@ cs_status read_status(cs_ctx* c, const int* dev, int n, int* host, cudaStream_t 
 }
 
 cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, double* resid,
-                  double* HX_out, char* work, cudaStream_t st, int* status_dev) {
+                  double* HX_out, char* work, cudaStream_t st, int* status_dev,
+                  long long ldho = 0) {
+  if (ldho == 0) ldho = ld;
   const HostTables& H = c->host;
   const Layout lay = layout(c, n_s, CS_FP64);
   double* HX = reinterpret_cast<double*>(work + lay.HX);
@@ -397,9 +464,11 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   CS_LAUNCH(c, 1, launch_sym_eig(Hs, n_s, theta, Q, jw, status_dev, st));
   CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
   CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
-  CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
-  CS_LAUNCH(c, 1, launch_residuals(X, ld, tmp, H.d, H.d, n_s, theta, resid, st));
-  if (HX_out) CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, HX_out, ld, H.d, n_s, st));
+  // H X Q straight into HX_out when the caller keeps it, else into tmp
+  double* HXq = HX_out ? HX_out : tmp;
+  const long long ldq = HX_out ? ldho : H.d;
+  CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, HXq, ldq, st));
+  CS_LAUNCH(c, 1, launch_residuals(X, ld, HXq, ldq, H.d, n_s, theta, resid, st));
   return CS_OK;
 }
 
@@ -416,15 +485,22 @@ cs_status check_dev_err(cs_ctx* c, cudaStream_t st) {
   return CS_OK;
 }
 
-// filter (precision prec) -> Cholesky-QR (FP64) -> Rayleigh-Ritz (FP64); synchronising
+// filter (precision prec) -> Cholesky-QR (FP64) -> Rayleigh-Ritz (FP64); synchronising.
+// With ritz_HX the filter takes the residual form: X are Ritz vectors, ritz_HX their H X and
+// theta their Ritz values (all on entry). HX_out (may equal ritz_HX) receives H X of the new
+// Ritz vectors.
 cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degree, double a,
                           double b, double a0, cs_precision prec, double* theta, double* resid,
-                          char* wk, cudaStream_t st) {
+                          char* wk, cudaStream_t st, const double* ritz_HX = nullptr,
+                          double* HX_out = nullptr, long long ldh = 0) {
+  if (ldh == 0) ldh = ld;
   const HostTables& H = c->host;
   const Layout lay = layout(c, n_s, prec);
   int* status = reinterpret_cast<int*>(wk + lay.status);
   cs_status s;
-  if (prec == CS_FP64) {
+  if (ritz_HX) {
+    s = cheb_ritz_dispatch(c, n_s, X, ld, ritz_HX, ldh, theta, degree, a, b, a0, prec, wk, st);
+  } else if (prec == CS_FP64) {
     s = cheb_core<double>(c, n_s, X, ld, degree, a, b, a0, wk, st);
   } else if (prec == CS_DF64) {
     df64* Xd = reinterpret_cast<df64*>(wk + lay.tmp);
@@ -439,7 +515,8 @@ cs_status chfsi_step_core(cs_ctx* c, int n_s, double* X, long long ld, int degre
   }
   if (s != CS_OK) return s;
   if ((s = cholqr_core(c, n_s, X, ld, wk, st, status)) != CS_OK) return s;
-  if ((s = rr_core(c, n_s, X, ld, theta, resid, nullptr, wk, st, status + 4)) != CS_OK) return s;
+  if ((s = rr_core(c, n_s, X, ld, theta, resid, HX_out, wk, st, status + 4, ldh)) != CS_OK)
+    return s;
   int hs[5];
   if ((s = read_status(c, status, 5, hs, st)) != CS_OK) return s;
   if ((s = check_dev_err(c, st)) != CS_OK) return s;
@@ -894,10 +971,16 @@ cs_status cs_chfsi(cs_ctx* c, int n_s, int n_want, double* X, long long ld, int 
   double a0 = tmin, a = a0 + (bnd - a0) / 10.0;
   if ((s = cs_cholqr(c, n_s, X, ld, work, stream)) != CS_OK) return s;
   std::vector<double> hth(n_s), hres(n_s);
+  // FP32 and mixed filters run in residual form once Ritz vectors exist: their H.X rounding
+  // then scales with the residual, so the iteration converges past the filter's precision
+  const bool ritz = (prec == CS_FP32 || prec == CS_MIXED_BF16) && degree <= kMaxRitzDegree;
+  double* HXr = reinterpret_cast<double*>(wk + lay.HXr);
   int it = 0;
   bool conv = false;
   for (it = 1; it <= max_iter; ++it) {
-    if ((s = chfsi_step_core(c, n_s, X, ld, degree, a, bnd, a0, prec, theta, resid, wk, st)) != CS_OK)
+    const bool use_ritz = ritz && it > 1;
+    if ((s = chfsi_step_core(c, n_s, X, ld, degree, a, bnd, a0, prec, theta, resid, wk, st,
+                             use_ritz ? HXr : nullptr, ritz ? HXr : nullptr, H.d)) != CS_OK)
       return s;
     CS_CHECK_CUDA(c, cudaMemcpyAsync(hth.data(), theta, n_s * 8, cudaMemcpyDeviceToHost, st));
     CS_CHECK_CUDA(c, cudaMemcpyAsync(hres.data(), resid, n_s * 8, cudaMemcpyDeviceToHost, st));
@@ -931,6 +1014,41 @@ cs_status cs_chfsi_step(cs_ctx* c, int n_s, double* X, long long ld, int degree,
   if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
   return chfsi_step_core(c, n_s, X, ld, degree, a, b, a0, prec, theta, resid, (char*)work,
                          (cudaStream_t)stream);
+}
+
+cs_status cs_cheb_filter_ritz(cs_ctx* c, int n_s, double* X, long long ld, const double* HX,
+                              long long ldh, const double* theta, int degree, double a, double b,
+                              double a0, cs_precision prec, void* work, cs_stream stream) {
+  cs_status s = need_device(c);
+  if (s != CS_OK) return s;
+  if ((s = check_block(c, n_s, X, ld)) != CS_OK) return s;
+  if (!HX || !theta || !work) return fail(c, CS_ERR_ARG, "NULL HX, theta or workspace");
+  if (ldh < c->host.d) return fail(c, CS_ERR_ARG, "ldh must be >= d");
+  if (degree < 1 || degree > kMaxRitzDegree)
+    return fail(c, CS_ERR_ARG, "degree must be in 1 .. 64 for the residual-form filter");
+  if (!(a < b) || !(a0 < a)) return fail(c, CS_ERR_ARG, "need a0 < a < b");
+  if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
+  return cheb_ritz_dispatch(c, n_s, X, ld, HX, ldh, theta, degree, a, b, a0, prec, (char*)work,
+                            (cudaStream_t)stream);
+}
+
+cs_status cs_chfsi_step_ritz(cs_ctx* c, int n_s, double* X, double* HX, long long ld, int degree,
+                             double a, double b, double a0, cs_precision prec, double* theta,
+                             double* resid, void* work, cs_stream stream) {
+  cs_status s = need_device(c);
+  if (s != CS_OK) return s;
+  if ((s = check_block(c, n_s, X, ld)) != CS_OK) return s;
+  if (!HX || HX == X || !theta || !resid || !work)
+    return fail(c, CS_ERR_ARG, "bad ChFSI step arguments");
+  if (degree < 1 || degree > kMaxRitzDegree)
+    return fail(c, CS_ERR_ARG, "degree must be in 1 .. 64 for the residual-form filter");
+  if (!(a < b) || !(a0 < a)) return fail(c, CS_ERR_ARG, "need a0 < a < b");
+  if (n_s > 1024) return fail(c, CS_ERR_ARG, "n_s > 1024 not supported");
+  if (prec != CS_FP64 && prec != CS_FP32 && prec != CS_MIXED_BF16 && prec != CS_DF64)
+    return fail(c, CS_ERR_ARG, "unknown precision");
+  if (!c->has_potential) return fail(c, CS_ERR_STATE, "cs_set_potential has not been called");
+  return chfsi_step_core(c, n_s, X, ld, degree, a, b, a0, prec, theta, resid, (char*)work,
+                         (cudaStream_t)stream, HX, HX, ld);
 }
 
 cs_status cs_device_error(cs_ctx* c, int* code) {

@@ -143,6 +143,7 @@ __device__ __forceinline__ void radial_anal_tile(const T* __restrict__ G,
       T x = ep.X[a + (size_t)s * ep.ld];
       T hx = ep.half_lambda[a] * x + z;
       if (ep.kb) hx += ep.kb[a + (size_t)s * ep.kb_ld];
+      if (ep.src) hx += ep.src_w[s] * ep.src[a + (size_t)s * ep.src_ld];
       if (ep.mode == EP_APPLY) {
         ep.out[o] = hx;
       } else {  // EP_CHEB: out = cA (HX - c X) - cB Yprev   (out may alias Yprev)

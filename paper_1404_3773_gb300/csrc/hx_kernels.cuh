@@ -17,7 +17,10 @@ enum { ANG_FULL = 0, ANG_SYNTH = 1, ANG_ANAL = 2 };
 // Epilogue of the radial analysis GEMM, for element (alpha, s):
 //   EP_PLAIN : out = Z
 //   EP_APPLY : out = 1/2 Lambda X + Z (+ kb)
-//   EP_CHEB  : out = cA (1/2 Lambda X + Z (+ kb) - cshift X) - cB Yprev   (Yprev may be out)
+//   EP_CHEB  : out = cA (1/2 Lambda X + Z (+ kb) (+ src_w[s] src) - cshift X) - cB Yprev
+//              (Yprev may be out). The src term is the source of the residual form of the
+//              filter: the Chebyshev recurrence run on the deviation D = p(H) X - X p(Theta)
+//              of a block of Ritz vectors gains cA s_i(theta_s) R[:, s], R = H X - X Theta.
 template <typename T>
 struct Epilogue {
   int mode = EP_PLAIN;
@@ -29,6 +32,9 @@ struct Epilogue {
   const T* half_lambda = nullptr;
   const T* kb = nullptr;
   long long kb_ld = 0;
+  const T* src = nullptr;    // d x S source block (residual form), or null
+  const T* src_w = nullptr;  // S per-column weights of src
+  long long src_ld = 0;
   T cA = T(0), cB = T(0), cshift = T(0);
 };
 
@@ -157,6 +163,21 @@ cudaError_t launch_to_df64(const double* x, long long ldx, df64* y, long long ld
                            int n, cudaStream_t stream);
 cudaError_t launch_from_df64(const df64* x, long long ldx, double* y, long long ldy, long long d,
                              int n, cudaStream_t stream);
+// Residual form of the Chebyshev filter (cheb_ritz.cu), T = double, float or df64:
+// wd[i n + j] = s_i(theta_j), i = 0 .. m, the scaled filter polynomials on the Ritz values
+// (c, e, sigma_1 = s1 as in the filter), and wt = wd rounded to T;
+template <typename T>
+cudaError_t launch_cheb_weights(const double* theta, int n, int m, double c, double e, double s1,
+                                double* wd, T* wt, cudaStream_t stream);
+// R = H X - X Theta and D1 = f1 R as T blocks with leading dimension d;
+template <typename T>
+cudaError_t launch_ritz_residual(const double* X, long long ldx, const double* HX, long long ldh,
+                                 const double* theta, long long d, int n, double f1, T* R, T* D1,
+                                 cudaStream_t stream);
+// X <- X diag(sm) + D (D: T block with leading dimension d).
+template <typename T>
+cudaError_t launch_ritz_combine(double* X, long long ldx, const T* D, long long d, int n,
+                                const double* sm, cudaStream_t stream);
 // Lanczos tridiagonal T (k x k) from alpha[k] and the squared off-diagonals beta2[k-1]
 cudaError_t launch_build_tridiag(const double* alpha, const double* beta2, int k, double* T,
                                  cudaStream_t stream);

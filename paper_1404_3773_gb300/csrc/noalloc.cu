@@ -14,7 +14,11 @@
 //     the process exits. Calls whose G does not fit are rejected with CS_ERR_ARG.
 //   - The first call on each device looks the array's device address up
 //     (cudaGetSymbolAddress) with that device current; make that first call before any
-//     stream capture begins on that device.
+//     stream capture begins on that device. The address is kept for the process: after a
+//     cudaDeviceReset of that device it is stale, and no later call may be made.
+//   - Only CS_FP64 and CS_FP32 blocks are accepted (the split-BF16 and double-float modes
+//     need staging buffers beyond G).
+//   - The caller's current device is restored before the call returns.
 //   - All calls on a device share the one array and it keeps the contents of the last
 //     call. Two calls whose kernels overlap in time on the GPU (different streams, or
 //     different host threads) race on it: serialise them.
@@ -68,7 +72,9 @@ cs_status run(cs_ctx* c, int n_s, const T* X, T* HX, long long ld, T* G, cudaStr
   cudaError_t e = cs::launch_radial_synth<T>(X, ld, G, D.rad, H.L, H.N, H.n_r, n_s, st);
   if (e == cudaSuccess) {
     c->launches += 1;
-    cs::AngArgs<T> a{H.L, H.n_r, H.n_theta, H.n_phi, c->Q4, n_s, D.theta, D.trig, D.wv, D.wkj};
+    // the same angular kernel as cs_apply_H (the FP32 one needs the transposed Legendre rows)
+    cs::AngArgs<T> a{H.L,     H.n_r,   H.n_theta, H.n_phi, c->Q4, n_s,
+                     D.theta, D.trig,  D.wv,      D.wkj,   D.theta_pairs};
     e = cs::launch_angular<T>(a, cs::ANG_FULL, G, nullptr, nullptr, st);
   }
   if (e == cudaSuccess) {
@@ -104,7 +110,7 @@ extern "C" cs_status cs_apply_H_noalloc(cs_ctx* c, int n_s, const void* X, void*
     return CS_ERR_ARG;
   }
   if (prec != CS_FP64 && prec != CS_FP32) {
-    c->err = "cs_apply_H_noalloc: unknown precision";
+    c->err = "cs_apply_H_noalloc: precision must be CS_FP64 or CS_FP32";
     return CS_ERR_ARG;
   }
   if (!c->has_potential) {
@@ -123,15 +129,21 @@ extern "C" cs_status cs_apply_H_noalloc(cs_ctx* c, int n_s, const void* X, void*
              " bytes; use fewer states per call or cs_apply_H";
     return CS_ERR_ARG;
   }
-  cudaError_t e = cudaSetDevice(c->device);
+  int prev_dev = -1;
+  cudaError_t e = cudaGetDevice(&prev_dev);
+  if (e == cudaSuccess) e = cudaSetDevice(c->device);
   if (e != cudaSuccess) {
     c->err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
     return CS_ERR_CUDA;
   }
+  cs_status r = CS_ERR_CUDA;
   void* scratch = scratch_on_device(c->device, c->err);
-  if (!scratch) return CS_ERR_CUDA;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (prec == CS_FP64)
-    return run<double>(c, n_s, (const double*)X, (double*)HX, ld, (double*)scratch, st);
-  return run<float>(c, n_s, (const float*)X, (float*)HX, ld, (float*)scratch, st);
+  if (scratch) {
+    cudaStream_t st = (cudaStream_t)stream;
+    r = prec == CS_FP64
+            ? run<double>(c, n_s, (const double*)X, (double*)HX, ld, (double*)scratch, st)
+            : run<float>(c, n_s, (const float*)X, (float*)HX, ld, (float*)scratch, st);
+  }
+  if (prev_dev != c->device) cudaSetDevice(prev_dev);
+  return r;
 }

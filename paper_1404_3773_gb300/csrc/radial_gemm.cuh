@@ -202,6 +202,7 @@ __device__ __forceinline__ void radial_gemm_tile(const float* __restrict__ X, lo
         const float x = ep.X[a_ + (size_t)s * ep.ld];
         float hx = fmaf(ep.half_lambda[a_], x, z);
         if (ep.kb) hx = __fadd_rn(hx, ep.kb[a_ + (size_t)s * ep.kb_ld]);
+        if (ep.src) hx = fmaf(ep.src_w[s], ep.src[a_ + (size_t)s * ep.src_ld], hx);
         if (ep.mode == EP_APPLY) {
           ep.out[o] = hx;
         } else {  // EP_CHEB: out = cA (HX - c X) - cB Yprev   (out may alias Yprev)

@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
                       ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   // 16-byte runs in the analysis epilogue: rows of N and all leading dimensions multiples of 4
   const bool vec_ep = MODE == 1 && (sh.N % 4) == 0 && (ep.ld % 4) == 0 && (ep.ld_out % 4) == 0 &&
-                      (!ep.kb || (ep.kb_ld % 4) == 0) &&
+                      (!ep.kb || (ep.kb_ld % 4) == 0) && (!ep.src || (ep.src_ld % 4) == 0) &&
                       ((reinterpret_cast<uintptr_t>(ep.out) | reinterpret_cast<uintptr_t>(ep.X) |
                         reinterpret_cast<uintptr_t>(ep.half_lambda) |
-                        reinterpret_cast<uintptr_t>(ep.kb) |
+                        reinterpret_cast<uintptr_t>(ep.kb) | reinterpret_cast<uintptr_t>(ep.src) |
                         reinterpret_cast<uintptr_t>(ep.Yprev)) & 15) == 0;
   const uint32_t bar_tma = smem_u32(&bars[0]);
   const uint32_t bar_mma = smem_u32(&bars[1]);
@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
     mi = c / sh.S;
     s = c - mi * sh.S;
   }
+  // weight of the residual-form source term of this column (0 when there is none)
+  const float sw = (MODE == 1 && ep.src && c < ncol) ? ep.src_w[s] : 0.f;
   if (ok) {
     for (int rb = 0; rb < rows; rb += 16) {
       float v[16];
@@ -260,14 +262,17 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
             ep.kb ? reinterpret_cast<const float4*>(ep.kb + a + (size_t)s * ep.kb_ld) : nullptr;
         const float4* y4 =
             ep.Yprev ? reinterpret_cast<const float4*>(ep.Yprev + o) : nullptr;
+        const float4* s4 =
+            ep.src ? reinterpret_cast<const float4*>(ep.src + a + (size_t)s * ep.src_ld) : nullptr;
         // all loads of the run first (out may alias Yprev: no store before the last load)
-        float4 xv[4], hv[4], kv[4], yv[4];
+        float4 xv[4], hv[4], kv[4], yv[4], sv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           xv[q] = x4[q];
           hv[q] = h4[q];
           kv[q] = k4 ? k4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
           yv[q] = (y4 && ep.mode != EP_APPLY) ? y4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          sv[q] = s4 ? s4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -275,11 +280,13 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
           const float hs[4] = {hv[q].x, hv[q].y, hv[q].z, hv[q].w};
           const float ks[4] = {kv[q].x, kv[q].y, kv[q].z, kv[q].w};
           const float ys[4] = {yv[q].x, yv[q].y, yv[q].z, yv[q].w};
+          const float ss[4] = {sv[q].x, sv[q].y, sv[q].z, sv[q].w};
           float r[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             float hx = fmaf(hs[j], xs[j], v[4 * q + j]);
             if (k4) hx = __fadd_rn(hx, ks[j]);
+            if (s4) hx = fmaf(sw, ss[j], hx);
             if (ep.mode == EP_APPLY) {
               r[j] = hx;
             } else {
@@ -307,6 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
         const float x = ep.X[a + (size_t)s * ep.ld];
         float hx = fmaf(ep.half_lambda[a], x, z);
         if (ep.kb) hx = __fadd_rn(hx, ep.kb[a + (size_t)s * ep.kb_ld]);
+        if (ep.src) hx = fmaf(sw, ep.src[a + (size_t)s * ep.src_ld], hx);
         if (ep.mode == EP_APPLY) {
           ep.out[o] = hx;
         } else {

@@ -28,7 +28,7 @@ def make_ctx(w, with_potential=True, device=0):
     return ctx
 
 
-@functools.lru_cache(maxsize=8)
+@functools.lru_cache(maxsize=16)
 def oracle_H(w_key):
     from oracle.basis import basis_for
     from oracle.hamiltonian import Hamiltonian

@@ -235,9 +235,10 @@ def test_chfsi_double_float_rayleigh_ritz_holds_fp64_bars():
     """Rayleigh-Ritz H X in double-float (cs_set_rr_precision CS_DF64). All-double-float
     ChFSI (filter too) converges to residuals of 1e-8 with the oscillator's ten lowest levels
     within 1e-9 Ha of the dense oracle eigenvalues. With the FP32 filter the subspace carries
-    the FP32 filter's noise (about 1e-7 per iteration), so residuals level off near 1e-6, but
-    the Ritz values, quadratic in that noise, stay within 1e-9 Ha: checked on the oscillator
-    against the dense oracle and on the 32-atom cluster against the all-FP64 ChFSI."""
+    the FP32 filter's noise only in its first iteration: after it the filter runs in residual
+    form, and the FP32-filter run reaches the same 1e-8 residuals, with the Ritz values within
+    1e-9 Ha: checked on the oscillator against the dense oracle and on the 32-atom cluster
+    against the all-FP64 ChFSI."""
     torch, cs = need_gpu()
     w = HO
     lam = np.linalg.eigvalsh(oracle_H(w.name).dense())
@@ -266,8 +267,7 @@ def test_chfsi_double_float_rayleigh_ritz_holds_fp64_bars():
         thr = torch.empty_like(th64)
         rr = torch.empty_like(th64)
         it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-8,
-                         max_iter=it64 + 10, precision=filt,
-                         raise_not_converged=(filt == cs.CS_DF64))
+                         max_iter=it64 + 10, precision=filt)
         dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
         floor = float(rr.cpu().numpy()[:w.n_want].max())
         print(f"filter {filt}: {it} iterations (FP64: {it64}), max |dtheta| vs FP64 "
@@ -278,9 +278,9 @@ def test_chfsi_double_float_rayleigh_ritz_holds_fp64_bars():
 def test_chfsi_double_float_gram_and_rotations():
     """Cholesky-QR and Rayleigh-Ritz Gram matrices and block rotations in double-float
     (cs_set_dense_precision CS_DF64), with the double-float Rayleigh-Ritz apply: the
-    all-double-float ChFSI of the 32-atom cluster reaches residuals of 1e-8 with its 64 lowest
-    Ritz values within 1e-9 Ha of the all-FP64 ChFSI, and the FP32-filter one within 1e-9 Ha
-    after as many iterations as the FP64 solve plus ten."""
+    all-double-float ChFSI of the 32-atom cluster and the FP32-filter one (residual form after
+    the first iteration) reach residuals of 1e-8 within the FP64 solve's iterations plus ten,
+    with their 64 lowest Ritz values within 1e-9 Ha of the all-FP64 ChFSI."""
     torch, cs = need_gpu()
     w = W.erf_cluster_32()
     ctx = make_ctx(w)
@@ -296,8 +296,7 @@ def test_chfsi_double_float_gram_and_rotations():
         thr = torch.empty_like(th64)
         rr = torch.empty_like(th64)
         it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-8,
-                         max_iter=it64 + 10, precision=filt,
-                         raise_not_converged=(filt == cs.CS_DF64))
+                         max_iter=it64 + 10, precision=filt)
         dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
         print(f"dense df64, filter {filt}: {it} iterations (FP64: {it64}), max |dtheta| "
               f"{dev:.3e}, max residual {float(rr.cpu().numpy()[:w.n_want].max()):.3e}")
@@ -305,11 +304,12 @@ def test_chfsi_double_float_gram_and_rotations():
 
 
 def test_chfsi_mixed_filter_meets_eigenvalue_gate():
-    """The mixed form (split-BF16 radial and projector contractions, FP32 elsewhere in the
-    filter) with the double-float Rayleigh-Ritz apply and Gram/rotations: on the 32-atom
-    cluster the 64 lowest Ritz values land within 1e-6 Ha of the all-FP64 ChFSI (the
-    acceptance gate of the mixed-precision form) after as many iterations as the FP64 solve
-    plus ten."""
+    """The mixed form (split-BF16 radial, phi and projector contractions, FP32 elsewhere in the
+    filter; residual form after the first iteration) with the double-float Rayleigh-Ritz apply
+    and Gram/rotations: on the 32-atom cluster the run meets the reduced-precision criterion
+    (residuals <= 1e-5) within the FP64 solve's iterations plus ten, and the 64 lowest Ritz
+    values land within 1e-6 Ha of the all-FP64 ChFSI (the acceptance gate of the
+    mixed-precision form)."""
     torch, cs = need_gpu()
     w = W.erf_cluster_32()
     ctx = make_ctx(w)
@@ -323,8 +323,9 @@ def test_chfsi_mixed_filter_meets_eigenvalue_gate():
     cs.cs_set_dense_precision(ctx, cs.CS_DF64)
     thr = torch.empty_like(th64)
     rr = torch.empty_like(th64)
-    cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-8,
-                max_iter=it64 + 10, precision=cs.CS_MIXED_BF16, raise_not_converged=False)
+    it = cs.cs_chfsi(ctx, X0.clone(), w.n_want, w.degree, v0, thr, rr, tol=1e-5,
+                     max_iter=it64 + 10, precision=cs.CS_MIXED_BF16)
     dev = np.max(np.abs(thr.cpu().numpy()[:w.n_want] - th64.cpu().numpy()[:w.n_want]))
-    print(f"mixed filter: max |dtheta| vs FP64 {dev:.3e}")
+    print(f"mixed filter: {it} iterations to 1e-5, max |dtheta| vs FP64 {dev:.3e}")
+    assert float(rr.cpu().numpy()[:w.n_want].max()) <= 1e-5
     assert dev < 1e-6, dev
