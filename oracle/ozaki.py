@@ -16,8 +16,11 @@ taken from low-precision products that are exact:
   2^(2 beta - 2). Accumulated in FP32 over chunks of at most 2^(26 - 2 beta) rows, every partial
   sum is an integer below 2^24 and so exact. The chunk sums are integers that FP64 adds exactly
   while they stay below 2^53.
-- **Sum.** C_ij ~= sum over pairs (k, l) with k + l <= s + 1 of u_k(i) v_l(j) P_kl(i, j), summed
-  in FP64. Dropping the pairs with k + l > s + 1 and the residuals leaves an error of order
+- **Sum.** C_ij ~= sum over pairs (k, l) with k + l <= s + 1 of u_k(i) v_l(j) P_kl(i, j). Every
+  term is an integer times a power of two, so the truncated sum has an exact value; C_ij is that
+  value rounded once to FP64 (round to nearest, ties to even). The method fixes no order for
+  this sum; rounding the exact sum once is the one result that does not depend on an order.
+  Dropping the pairs with k + l > s + 1 and the residuals leaves an error of order
   2^(2 - s beta) mu_i nu_j d, like that of an FP64 product for s beta >= 53.
 
 Here P_kl is computed in int64 (its plain definition); `fp32_chunk_sum` states the FP32
@@ -86,24 +89,43 @@ def max_exact_chunk(beta: int) -> int:
     return 1 << (26 - 2 * beta)
 
 
+def max_exact_diagonal_window(beta: int, s: int) -> int:
+    """Rows over which the products of all pairs on one diagonal k + l = t (at most s pairs)
+    always sum exactly in FP32: s 2^(2 beta - 2) per row, so the largest power of two with
+    rows s 2^(2 beta - 2) <= 2^24."""
+    w = (1 << 24) // (s << (2 * beta - 2))
+    return 1 << (w.bit_length() - 1)
+
+
 def gram(A: np.ndarray, B: np.ndarray, beta: int = 9, s: int = 6) -> np.ndarray:
     """C = A^T B (A: d x na, B: d x nb, FP64) from the exact slice products of the pairs
-    (k, l) with k + l <= s + 1 (1-based), summed in FP64 in order of decreasing k + l."""
-    a, u, _ = split(A, beta, s)
-    b, v, _ = split(B, beta, s)
+    (k, l) with k + l <= s + 1 (1-based): their scaled sum, exact, rounded once to FP64.
+
+    All pairs with the same k + l = t (0-based) share the unit 2^(E_i + F_j - 2 (beta - 1) -
+    t beta), so the exact value is 2^(E_i + F_j - 2 (beta - 1) - (s - 1) beta) times the
+    integer sum over t of D_t 2^((s - 1 - t) beta), D_t = sum_{k + l = t} P_kl. Python
+    integers hold it exactly, and float() of an integer rounds to nearest even."""
+    a, _, _ = split(A, beta, s)
+    b, _, _ = split(B, beta, s)
+    E = column_exponents(A)
+    F = column_exponents(B)
     na, nb = a.shape[2], b.shape[2]
+    D = [sum(slice_product(a[k], b[t - k]) for k in range(t + 1)) for t in range(s)]
     C = np.zeros((na, nb), dtype=np.float64)
-    pairs = [(k, l) for k in range(s) for l in range(s) if k + l <= s - 1]
-    for k, l in sorted(pairs, key=lambda kl: -(kl[0] + kl[1])):  # small terms first
-        P = slice_product(a[k], b[l]).astype(np.float64)  # exact below 2^53
-        C += (u[k][:, None] * v[l][None, :]) * P
+    for i in range(na):
+        for j in range(nb):
+            T = 0
+            for t in range(s):
+                T += int(D[t][i, j]) << ((s - 1 - t) * beta)
+            C[i, j] = math.ldexp(float(T), int(E[i] + F[j]) - 2 * (beta - 1) - (s - 1) * beta)
     return C
 
 
 def error_bound(A: np.ndarray, B: np.ndarray, beta: int, s: int) -> np.ndarray:
     """A bound on |gram(A, B) - A^T B| per entry. The dropped pairs (k + l > s + 1) and the two
-    residuals contribute at most (s + 2) 2^(E_i + F_j - s beta) d; each of the FP64 additions
-    of the kept pairs adds at most 2^-53 of the running magnitude."""
+    residuals contribute at most (s + 2) 2^(E_i + F_j - s beta) d; the final rounding adds at
+    most 2^-53 of the result, which the term below (written for a sum that rounds after every
+    pair) covers."""
     d = A.shape[0]
     E = column_exponents(A)
     F = column_exponents(B)

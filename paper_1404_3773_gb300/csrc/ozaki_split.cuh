@@ -125,20 +125,75 @@ __host__ __device__ inline double oz_pow2(int e) {
 #endif
 }
 
-// One entry of C = A^T B from the exact slice products S[k * s + l] = a_k^T b_l of its column
-// pair (column exponents E of A, F of B): the sum over the pairs with k + l <= s - 1, smallest
-// terms first (k + l from s - 1 down to 0, k ascending within), in FP64. Each term
-// 2^(E + F - 2 (beta - 1) - (k + l) beta) S is exact; the additions are the only roundings.
-// Requires |S| < 2^53 and the exponents inside the normal FP64 range.
-__host__ __device__ inline double oz_combine(const int64_t* S, int E, int F, int beta, int s) {
-  double c = 0.0;
-  for (int m = s - 1; m >= 0; --m)
-    for (int k = 0; k <= m; ++k) {
-      const int l = m - k;
-      const double term = (double)S[k * s + l] * oz_pow2(E + F - 2 * (beta - 1) - m * beta);
-      c = c + term;
+// A signed 128-bit integer as two's complement (hi, lo), enough for the exact sums below.
+struct OzI128 {
+  int64_t hi = 0;
+  uint64_t lo = 0;
+};
+
+// acc += v * 2^sh  (0 <= sh < 64, |v| 2^sh < 2^126)
+__host__ __device__ inline void oz_add_shifted(OzI128& acc, int64_t v, int sh) {
+  const uint64_t lo = (uint64_t)v << sh;
+  const int64_t hi = sh == 0 ? (v < 0 ? -1 : 0) : (v >> (64 - sh));  // arithmetic shift
+  const uint64_t nlo = acc.lo + lo;
+  acc.hi = acc.hi + hi + (nlo < acc.lo ? 1 : 0);
+  acc.lo = nlo;
+}
+
+// The integer acc rounded to the nearest double (ties to even), times 2^e (the result must stay
+// in the normal range; e only shifts the exponent).
+__host__ __device__ inline double oz_round_i128(OzI128 acc, int e) {
+  const bool neg = acc.hi < 0;
+  uint64_t hi = (uint64_t)acc.hi, lo = acc.lo;
+  if (neg) {  // magnitude: two's complement negation
+    lo = ~lo + 1;
+    hi = ~hi + (lo == 0 ? 1 : 0);
+  }
+  if (hi == 0 && lo == 0) return 0.0;
+  // top bit position p of the 128-bit magnitude
+  const int p = hi ? 64 + oz_bit_length(hi) - 1 : oz_bit_length(lo) - 1;
+  uint64_t m;
+  int ex;  // value = m 2^ex, m < 2^53
+  if (p <= 52) {
+    m = lo;
+    ex = 0;
+  } else {
+    const int sh = p - 52;  // bits below the kept 53
+    // m = magnitude >> sh; rem = magnitude mod 2^sh (as a comparison against half)
+    if (sh >= 64) {
+      m = hi >> (sh - 64);
+    } else {
+      m = (lo >> sh) | (sh ? (hi << (64 - sh)) : 0);
     }
-  return c;
+    // round bit and sticky bits
+    const int rb = sh - 1;  // position of the round bit
+    const bool round_bit =
+        rb >= 64 ? ((hi >> (rb - 64)) & 1) != 0 : ((lo >> rb) & 1) != 0;
+    bool sticky;
+    if (rb >= 64) {
+      sticky = lo != 0 || (rb - 64 > 0 && (hi & ((1ull << (rb - 64)) - 1)) != 0);
+    } else {
+      sticky = rb > 0 && (lo & ((1ull << rb) - 1)) != 0;
+    }
+    if (round_bit && (sticky || (m & 1))) ++m;
+    ex = sh;
+    if (m == (1ull << 53)) {  // carried into a new bit
+      m >>= 1;
+      ++ex;
+    }
+  }
+  const double v = (double)m * oz_pow2(ex + e);  // m < 2^53: exact; times a power of two
+  return neg ? -v : v;
+}
+
+// One entry of C = A^T B from the exact diagonal sums D[t] = sum_{k + l = t} a_k^T b_l of its
+// column pair (t = 0 .. s - 1; column exponents E of A, F of B): the exact value
+// sum_t D[t] 2^(E + F - 2 (beta - 1) - t beta) rounded once to FP64 (nearest, ties to even).
+// Requires (s - 1) beta <= 63 and |D[t]| 2^((s - 1 - t) beta) < 2^125 (no 128-bit overflow).
+__host__ __device__ inline double oz_combine(const int64_t* D, int E, int F, int beta, int s) {
+  OzI128 acc;
+  for (int t = 0; t < s; ++t) oz_add_shifted(acc, D[t], (s - 1 - t) * beta);
+  return oz_round_i128(acc, E + F - 2 * (beta - 1) - (s - 1) * beta);
 }
 
 }  // namespace cs

@@ -1,6 +1,6 @@
 // Host check of the whole slice-product pipeline of ozaki_split.cuh: split both operands,
-// form every slice product as an exact integer, combine (oz_combine), and compare with the
-// oracle's C = A^T B bit for bit. Input file: int32 d, na, nb, beta, s; A (d x na, FP64,
+// form the exact integer sum of the slice products on each diagonal k + l = t, combine
+// (oz_combine: exact sum, one rounding), and compare with the oracle's C = A^T B bit for bit. Input file: int32 d, na, nb, beta, s; A (d x na, FP64,
 // column-major); B (d x nb); the oracle's C (na x nb, row-major). Exit status 0 on agreement.
 #include <cmath>
 #include <cstdint>
@@ -42,18 +42,20 @@ int main(int argc, char** argv) {
   slices(A, d, na, beta, s, EA, a);
   slices(B, d, nb, beta, s, EB, b);
   long bad = 0;
-  std::vector<int64_t> S((size_t)s * s);
+  std::vector<int64_t> D((size_t)s);
   for (int i = 0; i < na; ++i)
     for (int j = 0; j < nb; ++j) {
-      for (int k = 0; k < s; ++k)
-        for (int l = 0; l < s; ++l) {
-          int64_t acc = 0;
+      // exact diagonal sums D_t = sum_{k + l = t} a_k^T b_l
+      for (int t = 0; t < s; ++t) {
+        int64_t acc = 0;
+        for (int k = 0; k <= t; ++k) {
           const int* ak = &a[((size_t)k * na + i) * d];
-          const int* bl = &b[((size_t)l * nb + j) * d];
+          const int* bl = &b[((size_t)(t - k) * nb + j) * d];
           for (int r = 0; r < d; ++r) acc += (int64_t)ak[r] * bl[r];
-          S[(size_t)k * s + l] = acc;
         }
-      const double c = cs::oz_combine(S.data(), EA[i], EB[j], beta, s);
+        D[t] = acc;
+      }
+      const double c = cs::oz_combine(D.data(), EA[i], EB[j], beta, s);
       const double want = C[(size_t)i * nb + j];
       uint64_t x, y;
       std::memcpy(&x, &c, 8);

@@ -1,8 +1,10 @@
-// Host emulation of the planned tensor-core data flow for C = A^T B from integer slices
+// Host emulation of the tensor-core data flow for C = A^T B from integer slices
 // (ozaki_split.cuh): per-column exponents from a max pre-pass; the split; per chunk of
-// `chunk` rows and per slice pair, a partial sum that the FP32 accumulators of one CTA must
-// hold exactly (checked: every running sum stays within 2^24 in magnitude); the partials added
-// in 64-bit integers; oz_combine. The result is compared with the oracle's C bit for bit.
+// `chunk` rows and per diagonal k + l = t, a partial sum that one FP32 tensor-memory
+// accumulator of a CTA must hold exactly (checked: the sum of the magnitudes of its products
+// stays within 2^24, which bounds every running sum in any order of addition); the
+// partials added in 64-bit integers; oz_combine. The result is compared with the oracle's C
+// bit for bit.
 // Input file: int32 d, na, nb, beta, s, chunk; A (d x na, FP64, column-major); B (d x nb);
 // the oracle's C (na x nb, row-major). Exit status 0 on agreement.
 #include <cmath>
@@ -47,27 +49,30 @@ int main(int argc, char** argv) {
   const long long lim = 1ll << 24;  // FP32 holds every integer of magnitude <= 2^24
   long overflow = 0, bad = 0;
   const int nchunks = (d + chunk - 1) / chunk;
-  std::vector<int64_t> S((size_t)s * s);
+  std::vector<int64_t> D((size_t)s);
   for (int i = 0; i < na; ++i)
     for (int j = 0; j < nb; ++j) {
-      for (int k = 0; k < s; ++k)
-        for (int l = 0; l < s; ++l) {
-          int64_t total = 0;
-          if (k + l <= s - 1) {
-            const int* ak = &a[((size_t)k * na + i) * d];
-            const int* bl = &b[((size_t)l * nb + j) * d];
-            for (int c = 0; c < nchunks; ++c) {
-              int64_t part = 0;  // one CTA's FP32 accumulator over this chunk
-              for (int r = c * chunk; r < d && r < (c + 1) * chunk; ++r) {
-                part += (int64_t)ak[r] * bl[r];
-                if (part > lim || part < -lim) ++overflow;
-              }
-              total += part;  // the reduction pass, in 64-bit integers
+      for (int t = 0; t < s; ++t) {
+        // one FP32 tensor-memory accumulator per diagonal k + l = t, over each chunk of rows:
+        // the MMAs of every pair on the diagonal add into it, one row step at a time
+        int64_t total = 0;
+        for (int c = 0; c < nchunks; ++c) {
+          int64_t part = 0, mag = 0;
+          for (int r = c * chunk; r < d && r < (c + 1) * chunk; ++r) {
+            for (int k = 0; k <= t; ++k) {
+              const int64_t p = (int64_t)a[((size_t)k * na + i) * d + r] *
+                                b[((size_t)(t - k) * nb + j) * d + r];
+              part += p;
+              mag += p < 0 ? -p : p;
             }
           }
-          S[(size_t)k * s + l] = total;
+          // every partial sum, in any order of addition, is at most the sum of magnitudes
+          if (mag > lim) ++overflow;
+          total += part;  // the drain of the accumulator, in 64-bit integers
         }
-      const double c = cs::oz_combine(S.data(), EA[i], EB[j], beta, s);
+        D[t] = total;
+      }
+      const double c = cs::oz_combine(D.data(), EA[i], EB[j], beta, s);
       const double want = C[(size_t)i * nb + j];
       uint64_t x, y;
       std::memcpy(&x, &c, 8);
@@ -78,6 +83,6 @@ int main(int argc, char** argv) {
       }
     }
   std::printf("%d x %d over %d rows in chunks of %d (beta %d, %d slices): %ld mismatches, %ld "
-              "running sums beyond 2^24\n", na, nb, d, chunk, beta, s, bad, overflow);
+              "chunk sums whose magnitudes reach beyond 2^24\n", na, nb, d, chunk, beta, s, bad, overflow);
   return (bad != 0 || overflow != 0) ? 1 : 0;
 }

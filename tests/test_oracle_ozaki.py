@@ -170,3 +170,24 @@ def test_rotation_shape_matches_exact_product():
     assert C.shape == (12, 5)
     assert np.all(np.abs(C - Ce) <= bound)
     assert np.max(np.abs(C - X @ Q) / (np.abs(X) @ np.abs(Q))) < 64 * 2.0 ** -53
+
+
+def test_gram_is_the_truncated_sum_rounded_once():
+    """gram() is the exact value of the kept slice pairs' scaled products rounded once to FP64:
+    checked against exact rational sums over the pairs (k, l) themselves, rounded by
+    float(Fraction), entry by entry and bit for bit."""
+    rng = np.random.default_rng(31)
+    A = _rand(rng, 50, 3)
+    B = _rand(rng, 50, 3)
+    beta, s = 7, 8
+    a, u, _ = ozaki.split(A, beta, s)
+    b, v, _ = ozaki.split(B, beta, s)
+    C = ozaki.gram(A, B, beta, s)
+    for i in range(3):
+        for j in range(3):
+            tot = Fraction(0)
+            for k in range(s):
+                for l in range(s - k):
+                    P = sum(int(x) * int(y) for x, y in zip(a[k][:, i], b[l][:, j]))
+                    tot += Fraction(P) * Fraction(float(u[k, i])) * Fraction(float(v[l, j]))
+            assert C[i, j] == float(tot)

@@ -81,8 +81,8 @@ def gram_checker(tmp_path_factory):
 @pytest.mark.parametrize("beta,s", [(9, 6), (8, 7)])
 def test_slice_product_pipeline_matches_oracle_gram_bit_for_bit(gram_checker, tmp_path, beta,
                                                                  s):
-    """Split, exact integer slice products and oz_combine reproduce oracle.gram exactly: the
-    kernel's only rounding is the FP64 sum over pairs, in the oracle's order."""
+    """Split, exact integer sums of the slice products on each diagonal and oz_combine
+    reproduce oracle.gram exactly: the only rounding is the single rounding of the exact sum."""
     rng = np.random.default_rng(77 + beta)
     A = _columns(rng, 300)
     B = _columns(rng, 300)[:, ::-1].copy()
@@ -119,26 +119,28 @@ def _run_plan(plan_checker, tmp_path, A, B, beta, s, chunk):
 
 
 def test_chunked_slice_product_plan_is_exact_and_matches_oracle(plan_checker, tmp_path):
-    """The planned kernel layout, beta = 7 and s = 8 with 4096-row chunks (the FP32 exactness
-    length 2^(26 - 2 beta)), reproduces oracle.gram bit for bit over 9000 rows (three chunks,
-    the last ragged), with no running sum past 2^24, including the worst case of every slice at
-    its bound."""
+    """The kernel's layout, beta = 7 and s = 8 with one FP32 accumulator per diagonal
+    k + l = t over windows of 512 rows (the exactness length for up to 8 pairs of products of
+    at most 2^12), reproduces oracle.gram bit for bit over 9000 rows (18 windows, the last
+    ragged), with the magnitudes of every window's products within 2^24."""
+    win = ozaki.max_exact_diagonal_window(7, 8)
+    assert win == 512
     rng = np.random.default_rng(4096)
     A = _columns(rng, 9000)[:, :6]
     B = _columns(rng, 9000)[:, 2:8].copy()
     B[:, 0] = A[:, 1]
-    r = _run_plan(plan_checker, tmp_path, A, B, 7, 8, ozaki.max_exact_chunk(7))
+    r = _run_plan(plan_checker, tmp_path, A, B, 7, 8, win)
     assert r.returncode == 0, r.stdout[-2000:]
-    # every leading slice at +2^(beta - 1) = 64: the products reach 2^12 and a full chunk of
-    # them reaches 2^24, the limit
     W = np.full((9000, 2), 1.0)
-    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, ozaki.max_exact_chunk(7))
+    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, win)
     assert r.returncode == 0, r.stdout[-2000:]
 
 
 def test_chunk_past_the_exactness_length_is_flagged(plan_checker, tmp_path):
-    """Twice the exactness length lets the worst-case running sum pass 2^24: the check that
-    guards the kernel's chunk length fails, as it must."""
+    """Columns of ones have a leading slice of 64 in every row: 4096 rows of products 2^12
+    reach 2^24, so a window of 8192 rows is flagged, as it must be."""
     W = np.full((9000, 2), 1.0)
-    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, 2 * ozaki.max_exact_chunk(7))
+    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, 8192)
     assert r.returncode != 0 and "beyond 2^24" in r.stdout
+    r = _run_plan(plan_checker, tmp_path, W, W, 7, 8, 4096)
+    assert r.returncode == 0, r.stdout[-2000:]
