@@ -1,18 +1,22 @@
 """Benchmark: ChFSI H.X applies/s on the 32-atom erf cluster (lmax 30, 48 radial functions,
 d = 46128, 96 x 60 x 120 grid, 80 states, Chebyshev degree 16) on one GB300.
 
-A step is one ChFSI iteration (Sec. 3.2.1):
-  - the degree-16 Chebyshev filter: 16 H.X block products in the chosen precision, with the
-    three-term recurrence fused into the H.X epilogue. The default is the mixed form:
-    split-BF16 tensor-core radial contractions and FP32 transforms;
+A step is one ChFSI iteration (Sec. 3.2.1) in its steady state, from Ritz vectors, their
+H X and Ritz values (cs_chfsi_step_ritz):
+  - the degree-16 Chebyshev filter in residual form: 15 H.X block products in the chosen
+    precision on the deviation from X s_16(Theta), with the three-term recurrence fused into
+    the H.X epilogue. The default is the mixed form: split-BF16 tensor-core radial
+    contractions and phi transforms, FP32 Legendre sums;
   - Cholesky-QR (two passes);
   - Rayleigh-Ritz: one H.X, Gram, eigensolve, rotations and residual norms. By default the H.X
     and the Gram matrices and rotations run in double-float (FP64-class); the factorisation,
     eigensolve and residual norms run in FP64.
-value = state-columns multiplied by H per second = (degree + 1) * n_s / step time, summed over
-ranks (each rank runs its own block: weak scaling, no collective on the data path).
+value = state-columns multiplied by H per second = (H.X products per step) * n_s / step time
+(16 * 80 in residual form, 17 * 80 with --form plain), summed over ranks (each rank runs its
+own block: weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64|df64]
+                    [--form ritz|plain]
     python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 """
 from __future__ import annotations
@@ -235,8 +239,9 @@ def run_ours(args):
     import paper_1404_3773_gb300 as cs
     from paper_1404_3773_gb300 import CS_FP32, CS_FP64, CS_MIXED_BF16
 
-    from paper_1404_3773_gb300 import CS_DF64
-    PREC = {"fp64": CS_FP64, "fp32": CS_FP32, "mixed": CS_MIXED_BF16, "df64": CS_DF64}
+    from paper_1404_3773_gb300 import CS_DF64, CS_FP64_SLICED
+    PREC = {"fp64": CS_FP64, "fp32": CS_FP32, "mixed": CS_MIXED_BF16, "df64": CS_DF64,
+            "sliced": CS_FP64_SLICED}
     NAME = {v: k for k, v in PREC.items()}
     prec = PREC[args.precision]
     w = W.erf_cluster_32()
@@ -268,14 +273,31 @@ def run_ours(args):
     th = theta.cpu().numpy()
     a, a0 = float(th[-1]), float(th[0])
     X0.copy_(Xs)
+    # H X and Ritz values of the starting Ritz vectors (the residual form's inputs, which a
+    # ChFSI loop carries from one iteration to the next)
+    HX0 = torch.empty_like(X0)
+    cs.cs_rayleigh_ritz(ctx, X0, theta, resid, HX0, work)
+    th0 = theta.clone()
     X = torch.empty_like(X0)
+    HX = torch.empty_like(X0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    ritz = args.form == "ritz"
+    hx_per_step = degree if ritz else degree + 1  # filter products + the Rayleigh-Ritz one
+
+    def reset():
+        X.copy_(X0)
+        if ritz:
+            HX.copy_(HX0)
+            theta.copy_(th0)
 
     def step():
-        cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, prec, work)
+        if ritz:
+            cs.cs_chfsi_step_ritz(ctx, X, HX, degree, a, b, a0, theta, resid, prec, work)
+        else:
+            cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, prec, work)
 
     for _ in range(args.warmup):
-        X.copy_(X0)
+        reset()
         step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -291,7 +313,7 @@ def run_ours(args):
     total_ms = 0.0
     launches_timed = 0
     for _ in range(args.steps):
-        X.copy_(X0)
+        reset()
         flush.fill_(1.0)  # L2 flush between timed iterations (not timed)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -311,13 +333,16 @@ def run_ours(args):
         time.sleep(0.3)
         clocks.stop()
     ms_per_step = total_ms / args.steps
-    applies_per_step = (degree + 1) * n_s
+    applies_per_step = hx_per_step * n_s
     value = job_value(applies_per_step, world, ms_per_step)
 
-    # ---- end to end through the public API: host (pinned) X in, Ritz vectors + values out
-    Xh = torch.empty_like(X0, device="cpu").pin_memory()
-    Xh.copy_(X0.cpu())
+    # ---- end to end through the public API: host (pinned) inputs in (the block, and in
+    # residual form its H X and Ritz values), Ritz vectors + values (and their H X) out
+    Xh = X0.cpu().pin_memory()
+    HXh = HX0.cpu().pin_memory()
+    thh_in = th0.cpu().pin_memory()
     Xout = torch.empty_like(Xh).pin_memory()
+    HXout = torch.empty_like(Xh).pin_memory()
     thh = torch.empty(n_s, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
@@ -326,14 +351,20 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         X.copy_(Xh, non_blocking=True)
+        if ritz:
+            HX.copy_(HXh, non_blocking=True)
+            theta.copy_(thh_in, non_blocking=True)
         step()
         Xout.copy_(X, non_blocking=True)
         thh.copy_(theta, non_blocking=True)
+        if ritz:
+            HXout.copy_(HX, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    h2d = X0.numel() * 8
-    d2h = X0.numel() * 8 + n_s * 8
+    nblk = 2 if ritz else 1
+    h2d = nblk * X0.numel() * 8 + (n_s * 8 if ritz else 0)
+    d2h = nblk * X0.numel() * 8 + n_s * 8
 
     # ---- Ritz values of one step from X0 with the reduced Rayleigh-Ritz apply against the
     # same step with an FP64 apply (wanted states), and the other precisions' step times
@@ -349,36 +380,60 @@ def run_ours(args):
     th_64, _ = one_step(prec, CS_FP64, CS_FP64)
     ritz_dev = float(np.max(np.abs(th_red[:w.n_want] - th_64[:w.n_want])))
 
-    def time_variant(p_filter, p_rr, p_dense, reps=3):
+    def time_variant(p_filter, p_rr, p_dense, form, reps=3):
         one_step(p_filter, p_rr, p_dense)  # warm (tables, workspace)
         wk = ctx.workspace(n_s, p_filter)
+        # the residual form's inputs: H X of X0 in this Rayleigh-Ritz precision
+        Xr, HXr = X0.clone(), torch.empty_like(X0)
+        cs.cs_rayleigh_ritz(ctx, Xr, theta, resid, HXr, wk)
+        thr = theta.clone()
+
+        def run():
+            X.copy_(Xr)
+            if form == "ritz":
+                HX.copy_(HXr)
+                theta.copy_(thr)
+                cs.cs_chfsi_step_ritz(ctx, X, HX, degree, a, b, a0, theta, resid, p_filter, wk)
+            else:
+                cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+
         for _ in range(2):
-            X.copy_(X0)
-            cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+            run()
         tot = 0.0
         for _ in range(reps):
-            X.copy_(X0)
             flush.fill_(1.0)
+            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            # the block copies sit inside this interval (two device block copies, ~20 us)
             e0.record(stream)
-            cs.cs_chfsi_step(ctx, X, degree, a, b, a0, theta, resid, p_filter, wk)
+            run()
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
         ms = tot / reps
-        return {"ms_per_step": round(ms, 4),
-                "value": round(applies_per_step / (ms / 1e3), 2)}
+        nhx = degree if form == "ritz" else degree + 1
+        return {"ms_per_step": round(ms, 4), "form": form, "hx_per_step": nhx,
+                "value": round(nhx * n_s / (ms / 1e3), 2)}
 
     variants = None
     if not args.no_variants:
         variants = {}
-        for name, pf, prr, pd in (("fp64", CS_FP64, CS_FP64, CS_FP64),
-                                  ("df64", CS_DF64, CS_DF64, CS_DF64),
-                                  ("fp32_rr_fp64", CS_FP32, CS_FP64, CS_FP64),
-                                  ("fp32_rr_df64", CS_FP32, CS_DF64, CS_DF64),
-                                  ("mixed_rr_df64", CS_MIXED_BF16, CS_DF64, CS_DF64)):
-            v = time_variant(pf, prr, pd)
+        for name, pf, prr, pd, form in (
+                ("fp64", CS_FP64, CS_FP64, CS_FP64, "plain"),
+                ("df64", CS_DF64, CS_DF64, CS_DF64, "plain"),
+                ("fp32_rr_fp64", CS_FP32, CS_FP64, CS_FP64, "plain"),
+                ("fp32_rr_df64", CS_FP32, CS_DF64, CS_DF64, "plain"),
+                ("mixed_rr_df64", CS_MIXED_BF16, CS_DF64, CS_DF64, "plain"),
+                ("mixed_rr_fp64", CS_MIXED_BF16, CS_FP64, CS_FP64, "plain"),
+                ("fp64_ritz", CS_FP64, CS_FP64, CS_FP64, "ritz"),
+                ("fp32_ritz_rr_df64", CS_FP32, CS_DF64, CS_DF64, "ritz"),
+                ("mixed_ritz_rr_df64", CS_MIXED_BF16, CS_DF64, CS_DF64, "ritz"),
+                ("mixed_ritz_rr_fp64", CS_MIXED_BF16, CS_FP64, CS_FP64, "ritz"),
+                ("mixed_ritz_rr_df64_sliced", CS_MIXED_BF16, CS_DF64, CS_FP64_SLICED, "ritz"),
+                ("mixed_ritz_rr_fp64_sliced", CS_MIXED_BF16, CS_FP64, CS_FP64_SLICED,
+                 "ritz")):
+            v = time_variant(pf, prr, pd, form)
             v.update({"filter": NAME[pf], "rayleigh_ritz_apply": NAME[prr],
                       "gram_and_rotations": NAME[pd]})
             variants[name] = v
@@ -394,10 +449,12 @@ def run_ours(args):
     roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps,
                                        dense_prec)
 
-    step_times = step_breakdown(classes, args.steps, degree, ms_per_step, prec, rr_prec)
+    step_times = step_breakdown(classes, args.steps, hx_per_step - 1, ms_per_step, prec,
+                                rr_prec)
 
     batched = None if args.no_batched else batched_measure(dev)
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
+    at_scale_chfsi = at_scale_chfsi_measure(dev) if args.at_scale_chfsi else None
     scf = None if args.no_scf else scf_measure(dev)
     first_solve = None if args.no_scf else first_solve_measure(dev)
     eigen_gate = None if args.no_scf else eigen_gate_measure(dev)
@@ -412,8 +469,13 @@ def run_ours(args):
         "data": "synthetic (seeded erf pseudo-atom cluster and Gaussian state block)",
         "config": {"workload": "erf32_l30_n48: 32 erf atoms in r<=8, R=14, lmax=30, 48 radial "
                                "fns/l, d=46128, grid 96x60x120, 80 states, degree 16",
-                   "step": "one ChFSI iteration: filter (16 H.X) + CholQR x2 + Rayleigh-Ritz "
-                           "(1 H.X in the rayleigh_ritz_apply precision)",
+                   "step": ("one steady-state ChFSI iteration: residual-form filter (15 H.X on "
+                            "the deviation) + CholQR x2 + Rayleigh-Ritz (1 H.X in the "
+                            "rayleigh_ritz_apply precision)") if ritz else
+                           ("one ChFSI iteration: filter (16 H.X) + CholQR x2 + Rayleigh-Ritz "
+                            "(1 H.X in the rayleigh_ritz_apply precision)"),
+                   "filter_form": args.form,
+                   "hx_per_step": hx_per_step,
                    "filter_precision": args.precision,
                    "rayleigh_ritz_apply": NAME[rr_prec],
                    "gram_and_rotations": NAME[dense_prec],
@@ -429,6 +491,7 @@ def run_ours(args):
         "gpu_launches": int(launches_timed),
         "batched": batched,
         "at_scale": at_scale,
+        "at_scale_chfsi": at_scale_chfsi,
         "scf": scf,
         "first_solve": first_solve,
         "eigen_gate": eigen_gate,
@@ -892,6 +955,197 @@ def at_scale_measure(dev, chunk=128):
     return out
 
 
+def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
+    """ChFSI iterations on the 400-atom cluster with s and p projectors (R = 26, lmax 60, 96
+    radial functions, d = 357216, 192 x 120 x 240 grid, 1600 projectors), 880 states, degree
+    20: the mixed filter in residual form over chunks of 128 states (19 split-BF16 H.X per
+    state), then Cholesky-QR twice and Rayleigh-Ritz over all 880 states with an FP64 H.X and
+    double-float Gram matrices and rotations (FP64 factorisation, eigensolve and residuals).
+    The block starts random (seeded); one untimed iteration with the first-pass interval
+    (Lanczos bounds), then `timed_iters` timed iterations (CUDA events, per-class device
+    times). Every call goes through the C ABI."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t, kb_couplings, kb_projector_values_t
+    w = W.erf_cluster_400_kb()
+    n_s, degree = w.n_s, w.degree
+    idx = torch.device(dev).index or 0
+    t_setup = time.time()
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, idx)
+    xyz = torch.tensor(cs.grid_points(ctx), device=dev)
+    atoms = w.atoms()
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, atoms).contiguous())
+    pcoef = torch.empty((4 * len(atoms), ctx.d), dtype=torch.float64, device=dev)
+    per = 16
+    for f in range(0, len(atoms), per):
+        cnt = min(per, len(atoms) - f)
+        pg = kb_projector_values_t(xyz, atoms, rc=1.0, first=f, count=cnt)
+        pg = pg.reshape(4 * cnt, ctx.n_r, ctx.n_theta, ctx.n_phi).contiguous()
+        cs.cs_forward_transform(ctx, pg, pcoef[4 * f:4 * (f + cnt)])
+        del pg
+    cs.cs_set_projectors(ctx, pcoef, kb_couplings(len(atoms)))
+    del pcoef, xyz
+    ctx._ws.clear()
+    torch.cuda.empty_cache()
+    cs.cs_set_rr_precision(ctx, cs.CS_FP64)
+    cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.x_seed)
+    X = torch.randn((n_s, ctx.d), generator=gen, dtype=torch.float64, device=dev)
+    v0 = torch.randn(ctx.d, generator=gen, dtype=torch.float64, device=dev)
+    HX = torch.empty_like(X)
+    theta = torch.empty(n_s, dtype=torch.float64, device=dev)
+    resid = torch.empty_like(theta)
+    work = ctx.workspace(n_s, cs.CS_MIXED_BF16)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    b, tmin = cs.cs_lanczos_bound(ctx, v0, 10, work)
+    stream = torch.cuda.current_stream()
+
+    def iteration(a, a0):
+        for c0 in range(0, n_s, chunk):
+            c1 = min(n_s, c0 + chunk)
+            cs.cs_cheb_filter_ritz(ctx, X[c0:c1], HX[c0:c1], theta[c0:c1], degree, a, b, a0,
+                                   cs.CS_MIXED_BF16, work)
+        cs.cs_cholqr(ctx, X, work)
+        cs.cs_rayleigh_ritz(ctx, X, theta, resid, HX, work)
+
+    # the random block: Cholesky-QR and Rayleigh-Ritz give its Ritz values and H X, then the
+    # first iteration with the first-pass interval
+    t0 = time.time()
+    cs.cs_cholqr(ctx, X, work)
+    cs.cs_rayleigh_ritz(ctx, X, theta, resid, HX, work)
+    iteration(tmin + (b - tmin) / 10.0, tmin)
+    torch.cuda.synchronize()
+    first_s = time.time() - t0
+    hist = [float(resid[:w.n_want].max())]
+    times = []
+    cs.cs_profile_begin(ctx)
+    for _ in range(timed_iters):
+        th = theta.cpu().numpy()
+        a, a0 = float(th[-1]), float(th[0])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iteration(a, a0)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        hist.append(float(resid[:w.n_want].max()))
+    pms, pn = cs.cs_profile_end(ctx)
+    names = cs.profile_class_names()
+    ms = sum(times) / len(times)
+    hx_per_iter = degree  # degree - 1 filter products + the Rayleigh-Ritz one, per state
+    applies = hx_per_iter * n_s
+    # ---- end to end through the public API: the block, its H X and Ritz values in from pinned
+    # host memory, the same out
+    Xh, HXh, thh = X.cpu().pin_memory(), HX.cpu().pin_memory(), theta.cpu().pin_memory()
+    th_np = thh.numpy().copy()
+    a, a0 = float(th_np[-1]), float(th_np[0])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    X.copy_(Xh, non_blocking=True)
+    HX.copy_(HXh, non_blocking=True)
+    theta.copy_(thh, non_blocking=True)
+    iteration(a, a0)
+    Xh.copy_(X, non_blocking=True)
+    HXh.copy_(HX, non_blocking=True)
+    thh.copy_(theta, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    hist.append(float(resid[:w.n_want].max()))
+    # per-class device time over the timed iterations, and the dominant single-kernel class
+    # rated against its pipe (the lmax-60 angular block runs on the FP32 pipe)
+    classes = {}
+    for i, nm in enumerate(names):
+        if pn[i]:
+            classes[nm] = {"ms_per_iteration": round(pms[i] / timed_iters, 3),
+                           "launches_per_iteration": pn[i] / timed_iters,
+                           "share": round(pms[i] / max(1e-9, sum(pms)), 4)}
+    L, N, nr, nt, nph = w.L, w.nmax, w.n_r, w.n_theta, w.n_phi
+    f_leg = 2.0 * nt * L * L * nr / 2.0
+    f_phi = 2.5 * nph * math.log2(nph) * nr * nt
+    ang_flops_state = 2 * f_leg + 2 * f_phi + float(nr * nt * nph)
+    roof = None
+    single = {k: v for k, v in classes.items() if not k.startswith("dense")}
+    if single:
+        dom = max(single, key=lambda k: single[k]["ms_per_iteration"])
+        n_launch = pn[names.index(dom)]
+        avg_ms = pms[names.index(dom)] / n_launch
+        if dom == "angular_f32":
+            per_launch = ang_flops_state * chunk  # one launch per 128-state chunk
+            ach = per_launch / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4),
+                    "peak": round(FP32_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+                    "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                    "flops_per_launch": per_launch, "avg_launch_ms": round(avg_ms, 4),
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "note": "flops per launch include the last, ragged chunk's 112 states as "
+                            "128"}
+        else:
+            roof = {"kernel": dom, "avg_launch_ms": round(avg_ms, 4), "frac": None}
+    cpu = cpu_baseline_local(w, dev, budget_s=cpu_seconds)
+    out = {"workload": f"erf400kb_l60_n96: 400 erf atoms + s,p projectors (1600), R=26, "
+                       f"lmax=60, 96 radial fns/l, d={ctx.d}, grid 192x120x240, {n_s} states "
+                       f"(filter in chunks of {chunk}), degree {degree}",
+           "step": "one ChFSI iteration: residual-form mixed filter (19 split-BF16 H.X per "
+                   "state) + CholQR x2 (double-float Gram/rotations) + Rayleigh-Ritz (FP64 H.X, "
+                   "double-float Gram/rotations, FP64 eigensolve and residuals)",
+           "ms_per_iteration": round(ms, 1),
+           "iteration_ms": [round(t, 1) for t in times],
+           "value": round(applies / (ms / 1e3), 1), "unit": "applies/s",
+           "hx_per_iteration_per_state": hx_per_iter,
+           "e2e": {"value": round(applies / (e2e_ms / 1e3), 1), "unit": "applies/s",
+                   "h2d_bytes_per_step": 2 * X.numel() * 8 + n_s * 8,
+                   "d2h_bytes_per_step": 2 * X.numel() * 8 + n_s * 8},
+           "kernel_classes": classes, "roofline": roof, "cpu_baseline": cpu,
+           "first_iteration_s": round(first_s, 2), "setup_s": round(t_setup, 1),
+           "max_resid_800_lowest_by_iteration": hist}
+    ctx.close()
+    return out
+
+
+def cpu_baseline_local(w, dev=None, budget_s=10.0, cols=1):
+    """The FP64 oracle's H.X on `cols` state(s) of a workload's basis and grid with its local
+    potential only, on the host cores, for about budget_s seconds. The projector pair is left
+    out: the oracle would form its coefficients from grid values of every projector (1600 x
+    5.5 million doubles for the 400-atom cluster, 70 GB). The seeded input generator
+    evaluates the potential on the oracle's own grid points (with torch on `dev` when given:
+    numpy takes over a minute for 400 atoms on 5.5 million points)."""
+    from oracle.basis import basis_for
+    from oracle.hamiltonian import Hamiltonian
+    t0 = time.perf_counter()
+    b = basis_for(w)
+    pts = b.points()
+    if dev is not None:
+        import torch
+        from workloads.device import erf_cluster_potential_t
+        v = erf_cluster_potential_t(torch.tensor(pts, device=dev), w.atoms(),
+                                    w.extra["Z"], w.extra["rc"]).cpu().numpy()
+    else:
+        v = w.potential_at(pts)
+    H = Hamiltonian(b, v)
+    setup = time.perf_counter() - t0
+    X = w.x_block(cols)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        H.apply(X)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(n * cols / el, 5), "unit": "applies/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n} oracle H.X calls on {cols} state(s) of the same basis and grid, local "
+                      f"potential only (no projectors); {el:.1f} s after {setup:.0f} s of set-up"}
+
+
 def cpu_baseline(w, budget_s=15.0, cols=8):
     """The FP64 oracle as it stands, on the host cores: H.X on `cols` states of the same
     workload, repeated for about `budget_s` seconds. Returns applies/s (state columns per
@@ -965,10 +1219,16 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--rr-precision", default="df64", choices=["same", "fp64", "df64"],
                     help="precision of the H X that Rayleigh-Ritz projects")
-    ap.add_argument("--dense-precision", default="df64", choices=["fp64", "df64"],
-                    help="arithmetic of the Gram matrices and block rotations")
+    ap.add_argument("--dense-precision", default="df64", choices=["fp64", "df64", "sliced"],
+                    help="arithmetic of the Gram matrices and block rotations (sliced: exact "
+                         "integer-slice products on the tensor cores, rounded once)")
+    ap.add_argument("--form", default="ritz", choices=["ritz", "plain"],
+                    help="filter form of the timed step: residual form from Ritz vectors "
+                         "(steady state of a ChFSI loop) or the plain recurrence")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-at-scale", action="store_true")
+    ap.add_argument("--at-scale-chfsi", action="store_true",
+                    help="also time ChFSI iterations of the 400-atom cluster (880 states)")
     ap.add_argument("--no-scf", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -80,7 +80,13 @@ typedef enum {
                         floats, about 48 significant bits; Dekker/Knuth error-free
                         transformations). On a GPU whose FP64 pipe runs at 1/64 of the FP32
                         rate this is several times faster than CS_FP64 at relative errors
-                        near 1e-14. Not available with projectors.                       */
+                        near 1e-14. Not available with projectors.                       */,
+  CS_FP64_SLICED = 4 /* dense products only (cs_set_dense_precision): FP64 Gram matrices and
+                        rotations from exact products of 7-bit integer slices on the tensor
+                        cores (Ozaki-Ogita-Oishi-Rump splitting, 8 slices per value, one
+                        power of two per column or row); the result is the exactly rounded
+                        value of the truncated slice sum, FP64-class (relative to |A|^T|B|
+                        below 2^-53 d).                                                  */
 } cs_precision;
 
 /* ------------------------------------------------------------------ basis / context */
@@ -152,10 +158,24 @@ cs_status cs_inverse_transform(cs_ctx* ctx, int n, const double* coef, long long
 cs_status cs_set_rr_precision(cs_ctx* ctx, cs_precision prec);
 
 /* Arithmetic of the tall-skinny Gram matrices (X^T X, X^T H X) and block rotations (X R^-1,
- * X Q, H X Q) of Cholesky-QR and Rayleigh-Ritz (Sec. 3.1.1, 3.2.1): CS_FP64 (default) or
- * CS_DF64 (double-float on the FP32 pipe, FP64 storage, relative errors near 1e-14). The
- * small factorisation, eigensolve and residual norms stay FP64. CS_ERR_ARG otherwise. */
+ * X Q, H X Q) of Cholesky-QR and Rayleigh-Ritz (Sec. 3.1.1, 3.2.1): CS_FP64 (default),
+ * CS_DF64 (double-float on the FP32 pipe, FP64 storage, relative errors near 1e-14) or
+ * CS_FP64_SLICED (exact integer-slice products on the tensor cores, rounded once). The small
+ * factorisation, eigensolve and residual norms stay FP64. Workspaces must be sized
+ * (cs_workspace_bytes) after this call. CS_ERR_ARG otherwise. */
 cs_status cs_set_dense_precision(cs_ctx* ctx, cs_precision prec);
+
+/* The dense steps' two products alone, in the context's dense precision (Sec. 3.2.1):
+ * cs_dense_gram: C (na x nb, column-major, ldc >= na) = A^T B, A: d x na (lda), B: d x nb
+ * (ldb), d the basis size; cs_dense_rotate: C (d x n, ldc >= d) = A Q, A: d x k (lda, must
+ * not overlap C), Q: k x n (ldq >= k). All DEVICE FP64. work: cs_workspace_bytes(ctx,
+ * max(na, nb) or max(k, n), CS_FP64) after cs_set_dense_precision. Enqueued on stream. */
+cs_status cs_dense_gram(cs_ctx* ctx, int na, int nb, const double* A, long long lda,
+                        const double* B, long long ldb, double* C, long long ldc, void* work,
+                        cs_stream stream);
+cs_status cs_dense_rotate(cs_ctx* ctx, int k, int n, const double* A, long long lda,
+                          const double* Q, long long ldq, double* C, long long ldc, void* work,
+                          cs_stream stream);
 
 /* Device workspace (bytes) needed by cs_apply_H / cs_cheb_filter / transforms on n_s
  * columns at precision `prec`, and by cs_rayleigh_ritz / cs_chfsi (their FP64 needs are

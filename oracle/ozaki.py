@@ -67,7 +67,13 @@ def split(X: np.ndarray, beta: int, s: int):
 
 
 def slice_product(a_k: np.ndarray, b_l: np.ndarray) -> np.ndarray:
-    """P = a_k^T b_l exactly (int64)."""
+    """P = a_k^T b_l exactly (int64). Where every partial sum stays below 2^53 in magnitude
+    (d max|a| max|b| < 2^53) an FP64 matrix product is exact in any order of summation and
+    takes its place (int64 products have no BLAS)."""
+    d = a_k.shape[0]
+    m = max(int(np.abs(a_k).max(initial=0)), 1) * max(int(np.abs(b_l).max(initial=0)), 1)
+    if d * m < 2 ** 53:
+        return np.rint(a_k.T.astype(np.float64) @ b_l.astype(np.float64)).astype(np.int64)
     return a_k.T.astype(np.int64) @ b_l.astype(np.int64)
 
 
@@ -109,16 +115,13 @@ def gram(A: np.ndarray, B: np.ndarray, beta: int = 9, s: int = 6) -> np.ndarray:
     b, _, _ = split(B, beta, s)
     E = column_exponents(A)
     F = column_exponents(B)
-    na, nb = a.shape[2], b.shape[2]
     D = [sum(slice_product(a[k], b[t - k]) for k in range(t + 1)) for t in range(s)]
-    C = np.zeros((na, nb), dtype=np.float64)
-    for i in range(na):
-        for j in range(nb):
-            T = 0
-            for t in range(s):
-                T += int(D[t][i, j]) << ((s - 1 - t) * beta)
-            C[i, j] = math.ldexp(float(T), int(E[i] + F[j]) - 2 * (beta - 1) - (s - 1) * beta)
-    return C
+    # T = sum_t D_t 2^((s - 1 - t) beta) in Python integers (object arrays: exact, any size)
+    T = np.zeros(D[0].shape, dtype=object)
+    for t in range(s):
+        T = T + (D[t].astype(object) << ((s - 1 - t) * beta))
+    e = (E[:, None] + F[None, :]).astype(object) - (2 * (beta - 1) + (s - 1) * beta)
+    return np.frompyfunc(lambda v, x: math.ldexp(float(v), x), 2, 1)(T, e).astype(np.float64)
 
 
 def error_bound(A: np.ndarray, B: np.ndarray, beta: int, s: int) -> np.ndarray:

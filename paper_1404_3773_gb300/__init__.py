@@ -18,13 +18,13 @@ import os
 import torch  # loads the CUDA runtime that the library links against
 
 __all__ = [
-    "CS_FP64", "CS_FP32", "CS_MIXED_BF16", "CS_DF64", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
+    "CS_FP64", "CS_FP32", "CS_MIXED_BF16", "CS_DF64", "CS_FP64_SLICED", "CS_RADIAL_GAUSS_LEGENDRE", "CS_RADIAL_GAUSS_JACOBI_R2",
     "CsError", "Context", "cs_basis_init", "cs_basis_free", "cs_basis_dims", "cs_grid",
     "cs_kinetic", "cs_bessel_zeros", "cs_set_potential", "cs_set_projectors",
     "cs_forward_transform", "cs_inverse_transform", "cs_workspace_bytes", "cs_apply_H",
     "cs_cheb_filter", "cs_cholqr", "cs_rayleigh_ritz", "cs_lanczos_bound", "cs_chfsi",
     "cs_chfsi_step", "cs_cheb_filter_ritz", "cs_chfsi_step_ritz", "cs_profile_begin", "cs_profile_end", "cs_apply_H_noalloc",
-    "cs_set_rr_precision", "cs_set_dense_precision",
+    "cs_set_rr_precision", "cs_set_dense_precision", "cs_dense_gram", "cs_dense_rotate",
     "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
     "cs_batch_last_error",
@@ -45,7 +45,7 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libclusterspec.so")
 
-CS_FP64, CS_FP32, CS_MIXED_BF16, CS_DF64 = 0, 1, 2, 3
+CS_FP64, CS_FP32, CS_MIXED_BF16, CS_DF64, CS_FP64_SLICED = 0, 1, 2, 3, 4
 CS_RADIAL_GAUSS_LEGENDRE, CS_RADIAL_GAUSS_JACOBI_R2 = 0, 1
 _STATUS = {0: "CS_OK", 1: "CS_ERR_ARG", 2: "CS_ERR_ALLOC", 3: "CS_ERR_CUDA",
            4: "CS_ERR_STATE", 5: "CS_ERR_CHOLESKY", 6: "CS_ERR_NOT_CONVERGED",
@@ -122,6 +122,8 @@ _SIGS = {
     "cs_profile_end": (_i, [_vp, _dp, ctypes.POINTER(_ll)]),
     "cs_set_rr_precision": (_i, [_vp, _i]),
     "cs_set_dense_precision": (_i, [_vp, _i]),
+    "cs_dense_gram": (_i, [_vp, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _vp]),
+    "cs_dense_rotate": (_i, [_vp, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _vp]),
     "cs_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, ctypes.POINTER(_vp)]),
     "cs_batch_free": (_i, [_vp]),
     "cs_batch_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -464,8 +466,36 @@ def cs_set_rr_precision(ctx: Context, precision: int):
 
 def cs_set_dense_precision(ctx: Context, precision: int):
     """Arithmetic of the Cholesky-QR / Rayleigh-Ritz Gram matrices and block rotations:
-    CS_FP64 (default) or CS_DF64 (double-float on the FP32 pipe, FP64 storage)."""
+    CS_FP64 (default), CS_DF64 (double-float on the FP32 pipe, FP64 storage) or CS_FP64_SLICED
+    (exact integer-slice products on the tensor cores, rounded once)."""
     ctx.check(_lib.cs_set_dense_precision(ctx.handle, int(precision)))
+    ctx._ws.clear()  # the workspace size depends on it
+
+
+def cs_dense_gram(ctx: Context, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, work=None,
+                  stream=None):
+    """C = A^T B in the dense precision. A: (na, lda), B: (nb, ldb) float64 device blocks
+    (rows = columns of the d x n matrices); C: (nb, ldc) float64, C[j, i] = (A^T B)[i, j]."""
+    na, lda = _check_block(ctx, A, torch.float64)
+    nb, ldb = _check_block(ctx, B, torch.float64)
+    assert C.is_cuda and C.dtype == torch.float64 and C.stride(1) == 1 and C.shape[0] == nb
+    assert C.shape[1] >= na
+    work = ctx.workspace(max(na, nb)) if work is None else work
+    ctx.check(_lib.cs_dense_gram(ctx.handle, na, nb, _ptr(A), lda, _ptr(B), ldb, _ptr(C),
+                                 C.stride(0), _ptr(work), _stream_ptr(stream)))
+
+
+def cs_dense_rotate(ctx: Context, A: torch.Tensor, Q: torch.Tensor, C: torch.Tensor, work=None,
+                    stream=None):
+    """C = A Q in the dense precision. A: (k, lda) float64 device block (d x k), Q: (n, ldq)
+    float64 (the k x n matrix column by column), C: (n, ldc) (d x n)."""
+    k, lda = _check_block(ctx, A, torch.float64)
+    n, ldc = _check_block(ctx, C, torch.float64)
+    assert Q.is_cuda and Q.dtype == torch.float64 and Q.stride(1) == 1 and Q.shape[0] == n
+    assert Q.shape[1] >= k
+    work = ctx.workspace(max(k, n)) if work is None else work
+    ctx.check(_lib.cs_dense_rotate(ctx.handle, k, n, _ptr(A), lda, _ptr(Q), Q.stride(0),
+                                   _ptr(C), ldc, _ptr(work), _stream_ptr(stream)))
 
 
 def cs_profile_begin(ctx: Context):

@@ -25,7 +25,7 @@ thread_local std::string g_init_error;
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, kbtc, total;
+  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, oz, kbtc, total;
 };
 
 constexpr int kMaxLanczos = 64;
@@ -63,6 +63,11 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.HXr = take(d * ns * 8);
   // weights s_i(theta_j) of the residual-form filter: FP64 table and one in the block type
   o.chw = take((size_t)(kMaxRitzDegree + 1) * ns * 16);
+  // split operands and partial sums of the slice-product Gram matrices and rotations
+  o.oz = take(c->dense_prec == CS_FP64_SLICED
+                  ? std::max(oz_gram_work_bytes(T.d, n_s, n_s, false),
+                             oz_rotate_work_bytes(T.d, n_s, n_s))
+                  : 0);
   // last, so that every other offset is the same for both precisions
   auto is_f32 = [](cs_precision p) { return p == CS_FP32 || p == CS_MIXED_BF16; };
   const bool reduced = is_f32(prec) || is_f32(c->rr_prec);
@@ -386,15 +391,21 @@ cs_status cheb_ritz_dispatch(cs_ctx* c, int n_s, double* X, long long ld, const 
 }
 
 // Gram matrix and block rotation of the ChFSI iteration in the context's dense precision
+// (oz: the slice-product workspace, layout slot `oz`)
 cudaError_t dense_gram(const cs_ctx* c, const double* A, long long lda, const double* B,
                        long long ldb, long long d, int na, int nb, double* C, int ldc,
-                       double* part, cudaStream_t st) {
+                       double* part, cudaStream_t st, void* oz) {
+  if (c->dense_prec == CS_FP64_SLICED)
+    return launch_oz_gram(A, lda, B, ldb, d, na, nb, C, ldc, oz, c->dev_err, st);
   return c->dense_prec == CS_DF64
              ? launch_gram_df(A, lda, B, ldb, d, na, nb, C, ldc, part, st)
              : launch_gram<double>(A, lda, B, ldb, d, na, nb, C, ldc, part, st);
 }
 cudaError_t dense_rotate(const cs_ctx* c, const double* A, long long lda, const double* Q, int ldq,
-                         long long d, int k, int n, double* C, long long ldc, cudaStream_t st) {
+                         long long d, int k, int n, double* C, long long ldc, cudaStream_t st,
+                         void* oz) {
+  if (c->dense_prec == CS_FP64_SLICED)
+    return launch_oz_rotate(A, lda, Q, ldq, d, k, n, C, ldc, oz, c->dev_err, st);
   return c->dense_prec == CS_DF64
              ? launch_gemm_nn_df(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st)
              : launch_gemm_nn<double>(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st);
@@ -409,10 +420,11 @@ cs_status cholqr_core(cs_ctx* c, int n_s, double* X, long long ld, char* work, c
   double* M = reinterpret_cast<double*>(work + lay.small);
   double* U = M + (size_t)n_s * n_s;
   double* w = U + (size_t)n_s * n_s;
+  void* oz = work + lay.oz;
   for (int pass = 0; pass < 2; ++pass) {
-    CS_LAUNCH(c, 2, dense_gram(c, X, ld, X, ld, H.d, n_s, n_s, M, n_s, part, st));
+    CS_LAUNCH(c, 2, dense_gram(c, X, ld, X, ld, H.d, n_s, n_s, M, n_s, part, st, oz));
     CS_LAUNCH(c, 1, launch_cholqr_factor(M, n_s, U, w, status_dev + pass, st));
-    CS_LAUNCH(c, 1, dense_rotate(c, X, ld, U, n_s, H.d, n_s, n_s, tmp, H.d, st));
+    CS_LAUNCH(c, 1, dense_rotate(c, X, ld, U, n_s, H.d, n_s, n_s, tmp, H.d, st, oz));
     CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   }
   return CS_OK;
@@ -460,14 +472,15 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
     CS_LAUNCH(c, 1, launch_convert_f32_to_f64(HX32, H.d, HX, H.d, H.d, n_s, st));
   }
   if (r != CS_OK) return r;
-  CS_LAUNCH(c, 2, dense_gram(c, X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st));
+  void* oz = work + lay.oz;
+  CS_LAUNCH(c, 2, dense_gram(c, X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st, oz));
   CS_LAUNCH(c, 1, launch_sym_eig(Hs, n_s, theta, Q, jw, status_dev, st));
-  CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st));
+  CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st, oz));
   CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   // H X Q straight into HX_out when the caller keeps it, else into tmp
   double* HXq = HX_out ? HX_out : tmp;
   const long long ldq = HX_out ? ldho : H.d;
-  CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, HXq, ldq, st));
+  CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, HXq, ldq, st, oz));
   CS_LAUNCH(c, 1, launch_residuals(X, ld, HXq, ldq, H.d, n_s, theta, resid, st));
   return CS_OK;
 }
@@ -756,9 +769,42 @@ cs_status cs_set_rr_precision(cs_ctx* c, cs_precision prec) {
 
 cs_status cs_set_dense_precision(cs_ctx* c, cs_precision prec) {
   if (!c) return CS_ERR_ARG;
-  if (prec != CS_FP64 && prec != CS_DF64)
-    return fail(c, CS_ERR_ARG, "dense precision must be CS_FP64 or CS_DF64");
+  if (prec != CS_FP64 && prec != CS_DF64 && prec != CS_FP64_SLICED)
+    return fail(c, CS_ERR_ARG, "dense precision must be CS_FP64, CS_DF64 or CS_FP64_SLICED");
   c->dense_prec = prec;
+  return CS_OK;
+}
+
+cs_status cs_dense_gram(cs_ctx* c, int na, int nb, const double* A, long long lda,
+                        const double* B, long long ldb, double* C, long long ldc, void* work,
+                        cs_stream stream) {
+  cs_status s = need_device(c);
+  if (s != CS_OK) return s;
+  const long long d = c->host.d;
+  if (na < 1 || nb < 1 || !A || !B || !C || !work || lda < d || ldb < d || ldc < na ||
+      ldc > 0x7fffffff)
+    return fail(c, CS_ERR_ARG, "bad Gram arguments");
+  const int n = std::max(na, nb);
+  const Layout lay = layout(c, n, CS_FP64);
+  char* wk = (char*)work;
+  cudaStream_t st = (cudaStream_t)stream;
+  CS_LAUNCH(c, 2, dense_gram(c, A, lda, B, ldb, d, na, nb, C, (int)ldc,
+                             reinterpret_cast<double*>(wk + lay.part), st, wk + lay.oz));
+  return CS_OK;
+}
+
+cs_status cs_dense_rotate(cs_ctx* c, int k, int n, const double* A, long long lda,
+                          const double* Q, long long ldq, double* C, long long ldc, void* work,
+                          cs_stream stream) {
+  cs_status s = need_device(c);
+  if (s != CS_OK) return s;
+  const long long d = c->host.d;
+  if (k < 1 || n < 1 || !A || !Q || !C || !work || lda < d || ldc < d || ldq < k ||
+      ldq > 0x7fffffff || A == C)
+    return fail(c, CS_ERR_ARG, "bad rotation arguments");
+  const Layout lay = layout(c, std::max(k, n), CS_FP64);
+  cudaStream_t st = (cudaStream_t)stream;
+  CS_LAUNCH(c, 1, dense_rotate(c, A, lda, Q, (int)ldq, d, k, n, C, ldc, st, (char*)work + lay.oz));
   return CS_OK;
 }
 

@@ -178,6 +178,18 @@ cudaError_t launch_ritz_residual(const double* X, long long ldx, const double* H
 template <typename T>
 cudaError_t launch_ritz_combine(double* X, long long ldx, const T* D, long long d, int n,
                                 const double* sm, cudaStream_t stream);
+// FP64 products from exact BF16 slice products on the tensor cores (ozaki_gemm.cu): the
+// exactly rounded value of the truncated slice sum (beta 7, 8 digits). Workspace sizes first.
+// Gram C (na x nb, ldc) = A^T B (A: d x na, B: d x nb); `same` when A and B are one block.
+size_t oz_gram_work_bytes(long long d, int na, int nb, bool same);
+cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long long ldb,
+                           long long d, int na, int nb, double* C, int ldc, void* work, int* err,
+                           cudaStream_t stream);
+// Rotation C (d x n, ldc) = A (d x k, lda) Q (k x n, ldq). A must not overlap C.
+size_t oz_rotate_work_bytes(long long d, int k, int n);
+cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, int ldq,
+                             long long d, int k, int n, double* C, long long ldc, void* work,
+                             int* err, cudaStream_t stream);
 // Lanczos tridiagonal T (k x k) from alpha[k] and the squared off-diagonals beta2[k-1]
 cudaError_t launch_build_tridiag(const double* alpha, const double* beta2, int k, double* T,
                                  cudaStream_t stream);

@@ -1,0 +1,513 @@
+// FP64 matrix products of the dense steps (Sec. 3.2.1: the Gram matrices of Cholesky-QR and
+// Rayleigh-Ritz and the rotations by their small factors) from exact products of small-integer
+// slices on the tcgen05 tensor cores: the error-free splitting of Ozaki, Ogita, Oishi and Rump
+// (2012) in its integer-slice form (ozaki_split.cuh).
+//
+//   C = A^T B (Gram: one exponent per column of A and of B) or C = A Q (rotation: one exponent
+//   per row of A, per column of Q). Each FP64 operand value becomes s = 8 integer digits of
+//   beta = 7 bits (|digit| <= 64, exact in BF16) below its row's or column's power of two.
+//   The product of digit matrices k and l carries the unit 2^(E + F - 12 - 7 (k + l)); the
+//   pairs with k + l <= 7 are kept. All pairs on one diagonal t = k + l share that unit, so
+//   each diagonal has one FP32 accumulator in tensor memory: a row adds at most 8 products of
+//   magnitude <= 2^12 to it, so over a window of 512 rows every partial sum is an integer of
+//   magnitude <= 2^24, held exactly in any order of addition. After each window the eight
+//   accumulators are read back and added, as integers, into registers; at the end the exact
+//   diagonal sums are combined in 128-bit integers and rounded once to FP64. The result is
+//   the exactly rounded value of the truncated slice sum: bit for bit what the oracle computes.
+//
+// Layout of a split operand (both sides): [K step of 16][digit][group of 8 operand rows]
+// [256 B canonical core-matrix pair]: per K step and digit, every operand row's 16 values in
+// the canonical K-major no-swizzle layout, so a tile of R consecutive operand rows is one
+// contiguous run of R / 8 x 256 bytes.
+//
+// The product kernel: one CTA per (128 rows of the A side) x (32 rows of the B side) x (a
+// group of up to 64 windows of K). Warp 8 issues the bulk copies (two stages of 32 K rows:
+// 80 KB), warp 9 issues the MMAs (36 per K step of 16) into one of two tensor-memory buffers of
+// 8 diagonals x 32 columns, and warps 0-7 drain the other buffer (warps w and w + 4 share a
+// lane quarter and take diagonals 0-3 and 4-7). Every wait is bounded; on expiry the kernel
+// records an error code in *err, lets its copies and MMAs land (bounded), frees its tensor
+// memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hx_kernels.cuh"
+#include "ozaki_split.cuh"
+#include "tc_common.cuh"
+
+namespace cs {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int kBeta = 7, kS = 8;
+constexpr int kWin = 512;                 // K rows of one exact FP32 window
+constexpr int kKC = 32;                   // K rows per pipeline stage (2 K steps)
+constexpr int kChunksPerWin = kWin / kKC; // 16
+constexpr int kTM = 128, kTN = 32;        // output tile: A-side rows x B-side rows
+constexpr int kMaxWinPerCta = 64;         // int32 window sums stay below 2^30
+constexpr int kDrainWarps = 8;
+constexpr int kThreads = 32 * (kDrainWarps + 2);
+constexpr int kAStep = kTM / 8 * 256;     // bytes of one (K step, digit) A tile: 4 KB
+constexpr int kBStep = kTN / 8 * 256;     // 1 KB
+constexpr int kStageBytes = 2 * kS * (kAStep + kBStep);  // 80 KB
+constexpr int kSmem = 2 * kStageBytes;                     // two stages
+constexpr int kTmemCols = 512;            // 2 buffers x 8 diagonals x 32 columns
+constexpr int kSms = 152;
+
+struct OzArgs {
+  const unsigned char* A;  // split A side
+  const unsigned char* B;  // split B side
+  long long a_groups;      // groups of 8 operand rows in A's layout
+  long long b_groups;
+  long long kchunks;       // K rows / 32 (padded)
+  int wins_per_cta;
+  // direct: C[i + j ldc] for i < M, j < N;  partial: part[((z 8 + t) Np + j) Mp + i]
+  int direct;
+  double* C;
+  long long ldc, M;
+  int N;
+  const int* EA;
+  const int* EB;
+  int* part;
+  long long Mp, Np;
+  int* err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2], empty[2], acc_full[2], acc_empty[2], done;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int flag_sh, issued_sh, consumed_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long mt = blockIdx.x;
+  const int nt = blockIdx.y, z = blockIdx.z;
+  const long long c0 = (long long)z * g.wins_per_cta * kChunksPerWin;
+  const long long c1 = min(g.kchunks, c0 + (long long)g.wins_per_cta * kChunksPerWin);
+  const int nk = (int)max(0ll, c1 - c0);
+  const int nw = (nk + kChunksPerWin - 1) / kChunksPerWin;
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&acc_full[s]), 1);
+      mbar_init(smem_u32(&acc_empty[s]), 32 * kDrainWarps);
+    }
+    mbar_init(smem_u32(&done), 1);
+    flag_sh = 0;
+    issued_sh = 0;
+    consumed_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_base_sh), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  auto sA = [&](int s) { return smem_u32(smem + (size_t)s * kStageBytes); };
+  auto sB = [&](int s) { return smem_u32(smem + (size_t)s * kStageBytes + 2 * kS * kAStep); };
+  int acc[4][kTN];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < kTN; ++c) acc[a][c] = 0;
+  bool ok = true;
+
+  if (warp == kDrainWarps && lane == 0) {
+    // producer: stage s is refilled once the MMAs that read it have completed
+    int i = 0;
+    for (; i < nk; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !mbar_wait(smem_u32(&empty[s]), ((i >> 1) - 1) & 1)) {
+        atomicCAS(g.err, 0, 21);
+        flag_sh = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, kStageBytes);
+      for (int ks = 0; ks < 2; ++ks) {
+        const long long kstep = (c0 + i) * 2 + ks;
+        for (int d = 0; d < kS; ++d) {
+          const unsigned char* a =
+              g.A + ((kstep * kS + d) * g.a_groups + mt * (kTM / 8)) * 256;
+          const unsigned char* b =
+              g.B + ((kstep * kS + d) * g.b_groups + (long long)nt * (kTN / 8)) * 256;
+          bulk_g2s(sA(s) + (ks * kS + d) * kAStep, a, kAStep, fb);
+          bulk_g2s(sB(s) + (ks * kS + d) * kBStep, b, kBStep, fb);
+        }
+      }
+    }
+    issued_sh = i;
+  } else if (warp == kDrainWarps + 1 && lane == 0) {
+    // MMA issuer: 36 MMAs per K step, pair (k, l) into the accumulator of diagonal k + l
+    constexpr uint32_t idesc = make_idesc(kTM, kTN);
+    int i = 0;
+    for (; i < nk; ++i) {
+      const int s = i & 1;
+      const int w = i / kChunksPerWin, buf = w & 1;
+      const bool first = (i % kChunksPerWin) == 0;
+      if (first && w >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), ((w >> 1) - 1) & 1)) {
+        atomicCAS(g.err, 0, 22);
+        flag_sh = 1;
+        break;
+      }
+      if (!mbar_wait(smem_u32(&full[s]), (i >> 1) & 1)) {
+        atomicCAS(g.err, 0, 23);
+        flag_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dbase = tmem + (uint32_t)(buf * kS * kTN);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+#pragma unroll
+          for (int k = 0; k <= t; ++k) {
+            const int l = t - k;
+            const uint64_t ad = make_desc(sA(s) + (ks * kS + k) * kAStep, 128, 256);
+            const uint64_t bd = make_desc(sB(s) + (ks * kS + l) * kBStep, 128, 256);
+            const uint32_t accum = (!first || ks > 0 || k > 0) ? 1u : 0u;
+            mma_bf16(dbase + (uint32_t)(t * kTN), ad, bd, idesc, accum);
+          }
+        }
+      }
+      mma_commit(smem_u32(&empty[s]));
+      if ((i % kChunksPerWin) == kChunksPerWin - 1 || i == nk - 1)
+        mma_commit(smem_u32(&acc_full[buf]));
+    }
+    consumed_sh = i;
+    mma_commit(smem_u32(&done));  // arrives when every MMA issued above has completed
+  } else if (warp < kDrainWarps) {
+    // drain: warp w reads lanes 32 (w % 4) .. + 31 and diagonals 4 (w / 4) .. + 3
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int t0 = (warp >> 2) * 4;
+    for (int w = 0; w < nw; ++w) {
+      const int buf = w & 1;
+      if (!mbar_wait(smem_u32(&acc_full[buf]), (w >> 1) & 1)) {
+        atomicCAS(g.err, 0, 24);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt) {
+        float v[kTN];
+        const uint32_t col = (uint32_t)(buf * kS * kTN + (t0 + tt) * kTN);
+        tmem_ld16_issue(tmem + lane_base + col, v);
+        tmem_ld16_issue(tmem + lane_base + col + 16, v + 16);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) acc[tt][c] += __float2int_rn(v[c]);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&acc_empty[buf]));
+    }
+  }
+  __syncwarp();
+  // everyone: the MMAs issued have completed
+  if (!mbar_wait(smem_u32(&done), 0)) {
+    atomicCAS(g.err, 0, 25);
+    ok = false;
+  }
+  __syncthreads();
+  if (warp == kDrainWarps && lane == 0 && flag_sh) {
+    // error path: let the copies that no MMA consumed land before the CTA exits
+    for (int i = consumed_sh; i < issued_sh; ++i)
+      mbar_wait(smem_u32(&full[i & 1]), (i >> 1) & 1);
+  }
+  ok = ok && !flag_sh;
+  const int drain_ok = __syncthreads_and((warp < kDrainWarps) ? (ok ? 1 : 0) : 1);
+  if (drain_ok && warp < kDrainWarps) {
+    const long long i = mt * kTM + (warp & 3) * 32 + lane;  // A-side row
+    const int t0 = (warp >> 2) * 4;
+    if (!g.direct) {
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt)
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) {
+          const long long j = (long long)nt * kTN + c;
+          g.part[(((long long)z * kS + t0 + tt) * g.Np + j) * g.Mp + i] = acc[tt][c];
+        }
+    }
+  }
+  if (g.direct) {
+    // warps 4-7 hand diagonals 4-7 to warps 0-3 through shared memory (the stages are idle)
+    int* stash = reinterpret_cast<int*>(smem);  // [4][kTN][kTM]
+    if (drain_ok && warp >= 4 && warp < kDrainWarps) {
+      const int r = (warp & 3) * 32 + lane;
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt)
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) stash[(tt * kTN + c) * kTM + r] = acc[tt][c];
+    }
+    __syncthreads();
+    if (drain_ok && warp < 4) {
+      const int r = warp * 32 + lane;
+      const long long i = mt * kTM + r;
+      if (i < g.M) {
+        const int ea = g.EA[i];
+        // fully unrolled, so that acc stays in registers
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) {
+          const long long j = (long long)nt * kTN + c;
+          if (j < g.N) {
+            int64_t D[kS];
+#pragma unroll
+            for (int tt = 0; tt < 4; ++tt) {
+              D[tt] = acc[tt][c];
+              D[4 + tt] = stash[(tt * kTN + c) * kTM + r];
+            }
+            g.C[i + j * g.ldc] = oz_combine(D, ea, g.EB[j], kBeta, kS);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// D[t] summed over the K groups in 64-bit integers, then combined: C[i + j ldc]
+__global__ void k_oz_reduce(const int* __restrict__ part, int groups, long long Mp, long long Np,
+                            long long M, int N, const int* __restrict__ EA,
+                            const int* __restrict__ EB, double* __restrict__ C, long long ldc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * N) return;
+  const long long i = t % M, j = t / M;
+  int64_t D[kS];
+#pragma unroll
+  for (int d = 0; d < kS; ++d) D[d] = 0;
+  for (int zz = 0; zz < groups; ++zz)
+#pragma unroll
+    for (int d = 0; d < kS; ++d) D[d] += part[(((long long)zz * kS + d) * Np + j) * Mp + i];
+  C[i + j * ldc] = oz_combine(D, EA[i], EB[j], kBeta, kS);
+}
+
+// E[c] = ceil(log2 max_r |X[r + c ld]|) over r < d (one CTA per column; 0 for zero columns and
+// for c >= n, the padding)
+__global__ void k_oz_colexp(const double* __restrict__ X, long long ld, long long d, int n,
+                            int* __restrict__ E) {
+  const int c = blockIdx.x;
+  double m = 0.0;
+  if (c < n)
+    for (long long r = threadIdx.x; r < d; r += blockDim.x) m = fmax(m, fabs(X[r + c * ld]));
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    E[c] = oz_exponent(m);
+  }
+}
+
+// E[r] = ceil(log2 max_c |X[r + c ld]|) over c < n (one thread per row; 0 past d)
+__global__ void k_oz_rowexp(const double* __restrict__ X, long long ld, long long d, int n,
+                            long long rows_pad, int* __restrict__ E) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows_pad) return;
+  double m = 0.0;
+  if (r < d)
+    for (int c = 0; c < n; ++c) m = fmax(m, fabs(X[r + c * ld]));
+  E[r] = oz_exponent(m);
+}
+
+__device__ __forceinline__ void oz_store_digits(unsigned char* out, long long kstep, int kh,
+                                                long long groups, long long row,
+                                                const int (*dig)[kS]) {
+  // dig[i][k]: digit k of the operand row's K value i of this octet
+#pragma unroll
+  for (int k = 0; k < kS; ++k) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn((float)dig[i][k]);
+    const size_t off = ((size_t)(kstep * kS + k) * groups + (row >> 3)) * 256 + kh * 128 +
+                       (row & 7) * 16;
+    *reinterpret_cast<uint4*>(out + off) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+
+// Operand rows = columns c of X (d x n, ld), K = rows r (Gram side; one exponent per column).
+// One thread per (column, octet of 8 rows); consecutive threads take consecutive columns.
+__global__ void k_oz_split_cols(const double* __restrict__ X, long long ld, long long d, int n,
+                                const int* __restrict__ E, long long cols_pad, long long kpad,
+                                unsigned char* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cols_pad * (kpad / 8)) return;
+  const long long c = t % cols_pad, oct = t / cols_pad;
+  const int e = E[c];
+  int dig[8][kS];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long r = oct * 8 + i;
+    const double x = (c < n && r < d) ? X[r + c * ld] : 0.0;
+    oz_slices(x, e, kBeta, kS, dig[i]);
+  }
+  oz_store_digits(out, oct >> 1, (int)(oct & 1), cols_pad / 8, c, dig);
+}
+
+// Operand rows = rows r of X (d x n, ld), K = columns c (rotation side; one exponent per row).
+// One thread per (row, octet of 8 columns); consecutive threads take consecutive rows.
+__global__ void k_oz_split_rows(const double* __restrict__ X, long long ld, long long d, int n,
+                                const int* __restrict__ E, long long rows_pad, long long kpad,
+                                unsigned char* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows_pad * (kpad / 8)) return;
+  const long long r = t % rows_pad, oct = t / rows_pad;
+  const int e = E[r];
+  int dig[8][kS];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long c = oct * 8 + i;
+    const double x = (r < d && c < n) ? X[r + c * ld] : 0.0;
+    oz_slices(x, e, kBeta, kS, dig[i]);
+  }
+  oz_store_digits(out, oct >> 1, (int)(oct & 1), rows_pad / 8, r, dig);
+}
+
+long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct OzPlan {
+  long long kpad, mpad, npad;  // K rows (multiple of 32); A-side rows (x128); B-side rows (x32)
+  long long wins, groups;
+  int wins_per_cta;
+  size_t offEA, offEB, offA, offB, offP, total;
+};
+
+OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
+  OzPlan p{};
+  p.kpad = rup(K, kKC);
+  p.mpad = rup(M, kTM);
+  p.npad = rup(N, kTN);
+  if (same) p.npad = p.mpad;  // one split serves both sides
+  p.wins = (p.kpad + kWin - 1) / kWin;
+  const long long tiles = (p.mpad / kTM) * (p.npad / kTN);
+  long long groups = 1;
+  if (gram) {
+    groups = (2 * kSms + tiles - 1) / tiles;  // about two CTAs per SM
+    if (groups > p.wins) groups = p.wins;
+    const long long need = (p.wins + kMaxWinPerCta - 1) / kMaxWinPerCta;
+    if (groups < need) groups = need;
+  } else if (p.wins > kMaxWinPerCta) {
+    groups = (p.wins + kMaxWinPerCta - 1) / kMaxWinPerCta;
+  }
+  p.wins_per_cta = (int)((p.wins + groups - 1) / groups);
+  p.groups = (p.wins + p.wins_per_cta - 1) / p.wins_per_cta;
+  size_t o = 0;
+  p.offEA = o;
+  o += al256((size_t)p.mpad * 4);
+  p.offEB = o;
+  o += al256((size_t)p.npad * 4);
+  p.offA = o;
+  o += al256((size_t)p.kpad * p.mpad * kS * 2);
+  p.offB = o;
+  o += same ? 0 : al256((size_t)p.kpad * p.npad * kS * 2);
+  p.offP = o;
+  o += p.groups > 1 ? al256((size_t)p.groups * kS * p.mpad * p.npad * 4) : 0;
+  p.total = o;
+  return p;
+}
+
+cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B, const int* EA,
+                const int* EB, long long M, int N, double* C, long long ldc, int* part,
+                int* err, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmem);
+  if (e != cudaSuccess) return e;
+  OzArgs g{};
+  g.A = A;
+  g.B = B;
+  g.a_groups = p.mpad / 8;
+  g.b_groups = p.npad / 8;
+  g.kchunks = p.kpad / kKC;
+  g.wins_per_cta = p.wins_per_cta;
+  g.direct = p.groups == 1;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.EA = EA;
+  g.EB = EB;
+  g.part = part;
+  g.Mp = p.mpad;
+  g.Np = p.npad;
+  g.err = err;
+  dim3 grid((unsigned)(p.mpad / kTM), (unsigned)(rup(N, kTN) / kTN), (unsigned)p.groups);
+  k_oz_mma<<<grid, kThreads, kSmem, st>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (p.groups > 1) {
+    const long long n = M * (long long)N;
+    k_oz_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, (int)p.groups, p.mpad, p.npad,
+                                                             M, N, EA, EB, C, ldc);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace
+
+size_t oz_gram_work_bytes(long long d, int na, int nb, bool same) {
+  return plan(d, na, nb, true, same).total;
+}
+
+size_t oz_rotate_work_bytes(long long d, int k, int n) {
+  return plan(k, d, n, false, false).total;
+}
+
+cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long long ldb,
+                           long long d, int na, int nb, double* C, int ldc, void* work, int* err,
+                           cudaStream_t st) {
+  const bool same = A == B && lda == ldb && na == nb;
+  const OzPlan p = plan(d, na, nb, true, same);
+  unsigned char* w = static_cast<unsigned char*>(work);
+  int* EA = reinterpret_cast<int*>(w + p.offEA);
+  int* EB = same ? EA : reinterpret_cast<int*>(w + p.offEB);
+  unsigned char* sa = w + p.offA;
+  unsigned char* sb = same ? sa : w + p.offB;
+  k_oz_colexp<<<(unsigned)p.mpad, 256, 0, st>>>(A, lda, d, na, EA);
+  long long nt = p.mpad * (p.kpad / 8);
+  k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, na, EA, p.mpad,
+                                                                p.kpad, sa);
+  if (!same) {
+    k_oz_colexp<<<(unsigned)p.npad, 256, 0, st>>>(B, ldb, d, nb, EB);
+    nt = p.npad * (p.kpad / 8);
+    k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(B, ldb, d, nb, EB, p.npad,
+                                                                  p.kpad, sb);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return run(p, sa, sb, EA, EB, na, nb, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st);
+}
+
+cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, int ldq,
+                             long long d, int k, int n, double* C, long long ldc, void* work,
+                             int* err, cudaStream_t st) {
+  const OzPlan p = plan(k, d, n, false, false);
+  unsigned char* w = static_cast<unsigned char*>(work);
+  int* EA = reinterpret_cast<int*>(w + p.offEA);
+  int* EB = reinterpret_cast<int*>(w + p.offEB);
+  unsigned char* sa = w + p.offA;
+  unsigned char* sb = w + p.offB;
+  k_oz_rowexp<<<(unsigned)((p.mpad + 255) / 256), 256, 0, st>>>(A, lda, d, k, p.mpad, EA);
+  long long nt = p.mpad * (p.kpad / 8);
+  k_oz_split_rows<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, k, EA, p.mpad, p.kpad,
+                                                                sa);
+  k_oz_colexp<<<(unsigned)p.npad, 256, 0, st>>>(Q, ldq, k, n, EB);
+  nt = p.npad * (p.kpad / 8);
+  k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(Q, ldq, k, n, EB, p.npad, p.kpad,
+                                                                sb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return run(p, sa, sb, EA, EB, d, n, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st);
+}
+
+}  // namespace cs

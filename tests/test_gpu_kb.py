@@ -83,6 +83,7 @@ def test_projector_pair_matches_oracle_all_precisions(case, prec):
     got = _apply(torch, cs, ctx, X, prec)
     fro, col = rel_errors(got, ref)
     tf, tc = TOL[prec]
+    print(f"kb {case} {prec}: fro {fro:.3e} col {col:.3e}")
     assert fro <= tf and col <= tc, (fro, col)
     # the projector term alone (difference of two applies), relative to its own size; the
     # bound allows for the rounding of the epilogue sum, whose terms are about 10^3 times
@@ -90,6 +91,7 @@ def test_projector_pair_matches_oracle_all_precisions(case, prec):
     cs.cs_set_projectors(ctx, None, None)
     kb_got = got - _apply(torch, cs, ctx, X, prec)
     kfro = np.linalg.norm(kb_got - kb_ref) / np.linalg.norm(kb_ref)
+    print(f"kb {case} {prec}: projector term alone {kfro:.3e}")
     assert kfro <= {"fp64": 1e-10, "fp32": 1e-3, "mixed": 1e-3}[prec], kfro
     assert cs.cs_device_error(ctx) == 0
 
@@ -141,6 +143,7 @@ def test_erf400kb_full_size():
     _set_library_projectors(torch, cs, ctx, sub)
     for prec in ("fp64", "fp32", "mixed"):
         fro, col = rel_errors(_apply(torch, cs, ctx, X2, prec), ref_kb)
+        print(f"erf400kb two atoms {prec}: fro {fro:.3e} col {col:.3e}")
         assert fro <= TOL[prec][0] and col <= TOL[prec][1], (prec, fro, col)
     # every projector (1600), one chunk of 128 states
     _set_library_projectors(torch, cs, ctx, atoms)
@@ -148,5 +151,6 @@ def test_erf400kb_full_size():
     y64 = _apply(torch, cs, ctx, Xc, "fp64")
     for prec in ("fp32", "mixed"):
         fro, col = rel_errors(_apply(torch, cs, ctx, Xc, prec), y64)
+        print(f"erf400kb 1600 projectors, 128 states {prec}: fro {fro:.3e} col {col:.3e}")
         assert fro <= TOL[prec][0] and col <= TOL[prec][1], (prec, fro, col)
     assert cs.cs_device_error(ctx) == 0
