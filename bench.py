@@ -448,6 +448,19 @@ def run_ours(args):
     # ---- roofline of the dominant kernel class (device time measured live above)
     roofline, classes = roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, args.steps,
                                        dense_prec)
+    # the FP32 / FP64 FMA rates measured on this device, beside the nominal unit-count peaks
+    alu = None
+    try:
+        f32, f64 = cs.cs_measure_peaks(local)
+        alu = {"fp32_tflops": round(f32, 2), "fp64_tflops": round(f64, 3),
+               "fp32_nominal_tflops": round(FP32_PEAK_TFLOPS, 2),
+               "fp64_nominal_tflops": FP64_PEAK_TFLOPS,
+               "how": "8 independent FMA chains per thread, 4 x 256 threads per SM, best of 5"}
+        if roofline.get("bound") == "alu" and roofline.get("achieved") and f32 > 0 and \
+                roofline.get("peak") == round(FP32_PEAK_TFLOPS, 3):
+            roofline["frac_of_measured_fp32"] = round(roofline["achieved"] / f32, 4)
+    except Exception as exc:  # the measurement is context, not the result
+        alu = {"error": str(exc)}
 
     step_times = step_breakdown(classes, args.steps, hx_per_step - 1, ms_per_step, prec,
                                 rr_prec)
@@ -500,6 +513,7 @@ def run_ours(args):
         "ritz": {"theta_min": float(th_red[0]), "max_dev_wanted_vs_fp64_rr": ritz_dev,
                  "n_wanted": w.n_want},
         "variants": variants,
+        "alu_peaks": alu,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -686,15 +700,41 @@ def eigen_gate_measure(dev):
     return out
 
 
-def learned_init_measure(dev, n_train=48, n_test=16, tol=1e-6, hidden=128, steps=2000,
-                         ceiling=True):
+def _bond_midpoints(atoms, rcut):
+    """Midpoints of the atom pairs closer than rcut (bohr): centres of the bond functions."""
+    mids = [(atoms[a] + atoms[b]) / 2.0 for a in range(len(atoms)) for b in range(a + 1, len(atoms))
+            if np.linalg.norm(atoms[a] - atoms[b]) < rcut]
+    return np.array(mids, dtype=np.float64).reshape(-1, 3)
+
+
+def _center_features(cs, atoms, mids, mu, width):
+    """Network inputs of every centre: the radial descriptor (the atom's neighbours; for a bond
+    midpoint, every atom) and a flag that marks bond centres."""
+    fa = cs.cs_atom_descriptors(atoms, mu, width)
+    fb = [cs.cs_atom_descriptors(np.vstack([m[None, :], atoms]), mu, width)[0] for m in mids]
+    F = np.zeros((len(atoms) + len(mids), len(mu) + 1))
+    F[:len(atoms), :len(mu)] = fa
+    if len(mids):
+        F[len(atoms):, :len(mu)] = np.array(fb)
+        F[len(atoms):, len(mu)] = 1.0
+    return F
+
+
+def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, steps=3000,
+                         ceiling=True, rcut=4.0):
     """The learned initial density: small clusters of 4-12 Z=4 erf pseudo-atoms (R = 9, lmax 10,
     16 radial functions, 32 x 22 x 42 grid), SCF (mixed filter) from the Gaussian start to
-    |dE| <= tol. On the training clusters, the converged density minus the start is fitted by
-    atom-centred Gaussians; a 16-128-128-128-5 tanh network learns the fitted coefficients
-    from the radial descriptors (Adam). On the held-out clusters, the SCF runs from the
-    Gaussian start, from the learned start, and (ceiling) from the cluster's own best-fit
-    correction; iterations and times are compared."""
+    |dE| <= tol. The correction to the start is expanded in unit-integral Gaussians on every
+    atom and on the midpoint of every pair closer than rcut (bond functions: the converged
+    density gains bonding charge between atoms, which atom-centred spherical functions cannot
+    hold). On the training clusters the converged density minus the start is fitted by these
+    functions (weighted least squares); a 17-128-128-128-5 tanh network learns the fitted
+    coefficients from each centre's radial descriptor and a bond flag (Adam). On the held-out
+    clusters the SCF runs from the Gaussian start, from the learned start, and (ceiling) from
+    the cluster's own best fit. The learned start is the Gaussian start plus the predicted
+    correction, clipped at zero and renormalised to the electron count. Fallback: if the
+    predicted correction's integral of |correction| exceeds half the electron count (a
+    prediction far outside what training saw), the Gaussian start is kept."""
     import torch
 
     import paper_1404_3773_gb300 as cs
@@ -737,18 +777,25 @@ def learned_init_measure(dev, n_train=48, n_test=16, tol=1e-6, hidden=128, steps
         S.close()
         return it, sec, rho, rep["energy"]
 
+    def centres(atoms):
+        mids = _bond_midpoints(atoms, rcut)
+        return np.vstack([atoms, mids]), mids
+
     # training data
     D, C = [], []
+    n_bonds = 0
     for i in range(n_train):
         atoms = cluster(i)
         start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
         _, _, rho, _ = scf(atoms, start)
-        C.append(cs.cs_fit_atom_density(ctx, atoms, sig, (rho - start).contiguous(), ridge=1e-8))
-        D.append(cs.cs_atom_descriptors(atoms, mu, width))
+        cen, mids = centres(atoms)
+        n_bonds += len(mids)
+        C.append(cs.cs_fit_atom_density(ctx, cen, sig, (rho - start).contiguous(), ridge=1e-8))
+        D.append(_center_features(cs, atoms, mids, mu, width))
     D, C = np.concatenate(D), np.concatenate(C)
     d_mean, d_std = D.mean(axis=0), D.std(axis=0) + 1e-6
     c_scale = float(np.abs(C).max()) or 1.0
-    dims = [16, hidden, hidden, hidden, len(sig)]
+    dims = [D.shape[1], hidden, hidden, hidden, len(sig)]
     params = []
     for k in range(len(dims) - 1):
         params.append((W.gaussian_block(5200 + k, dims[k], dims[k + 1])
@@ -765,42 +812,52 @@ def learned_init_measure(dev, n_train=48, n_test=16, tol=1e-6, hidden=128, steps
     loss = cs.cs_mlp_loss_grad(net, Xd, Td)[0]
     train_s = time.perf_counter() - t0
     # held-out comparison
-    it_g, it_l, s_g, s_l, de, it_c = [], [], [], [], [], []
+    it_g, it_l, s_g, s_l, de, it_c, fell_back = [], [], [], [], [], [], 0
     for i in range(n_train, n_train + n_test):
         atoms = cluster(i)
+        ne = 4.0 * len(atoms)
         start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
         a, sa, rho_c, ea = scf(atoms, start)
+        cen, mids = centres(atoms)
         if ceiling:  # start from this cluster's own best-fit correction
-            cfit = cs.cs_fit_atom_density(ctx, atoms, sig, (rho_c - start).contiguous(), ridge=1e-8)
+            cfit = cs.cs_fit_atom_density(ctx, cen, sig, (rho_c - start).contiguous(), ridge=1e-8)
             fitted = start.clone()
-            cs.cs_atom_density(ctx, atoms, sig, cfit, fitted)
-            fitted *= 4.0 * len(atoms) / cs.cs_grid_integrals(ctx, [fitted])[0]
+            cs.cs_atom_density(ctx, cen, sig, cfit, fitted)
+            fitted *= ne / cs.cs_grid_integrals(ctx, [fitted])[0]
             it_c.append(scf(atoms, fitted)[0])
-        desc = (cs.cs_atom_descriptors(atoms, mu, width) - d_mean) / d_std
-        coef = cs.cs_mlp_forward(net, torch.tensor(desc.T.copy(), dtype=torch.float32,
+        feats = (_center_features(cs, atoms, mids, mu, width) - d_mean) / d_std
+        coef = cs.cs_mlp_forward(net, torch.tensor(feats.T.copy(), dtype=torch.float32,
                                                    device=dev)).cpu().numpy().T * c_scale
-        learned = start.clone()
-        cs.cs_atom_density(ctx, atoms, sig, coef.astype(np.float64), learned)
-        ne = 4.0 * len(atoms)
-        learned *= ne / cs.cs_grid_integrals(ctx, [learned])[0]
-        b, sb, _, eb = scf(atoms, learned)
+        corr = torch.zeros_like(start)
+        cs.cs_atom_density(ctx, cen, sig, coef.astype(np.float64), corr)
+        ok = cs.cs_grid_integrals(ctx, [corr.abs().contiguous()])[0] <= 0.5 * ne
+        if ok:
+            learned = torch.clamp(start + corr, min=0.0).contiguous()
+            learned *= ne / cs.cs_grid_integrals(ctx, [learned])[0]
+            b, sb, _, eb = scf(atoms, learned)
+        else:  # fallback: the Gaussian start
+            fell_back += 1
+            b, sb, eb = a, sa, ea
         it_g.append(a)
         it_l.append(b)
         s_g.append(sa)
         s_l.append(sb)
-        de.append(abs(ea - eb))
+        de.append(abs(ea - eb) / len(atoms))
     net.close()
     ctx.close()
     return {"workload": f"{n_train} training + {n_test} held-out clusters of 4-12 Z=4 erf atoms "
                         "(R 9, lmax 10, N 16, grid 32x22x42), mixed-filter SCF to "
-                        f"|dE| <= {tol:g} Ha",
-            "train_atoms": int(D.shape[0]), "train_loss_first": loss0, "train_loss_final": loss,
+                        f"|dE| <= {tol:g} Ha; correction on atoms and on bond midpoints "
+                        f"(pairs closer than {rcut:g} bohr)",
+            "train_centres": int(D.shape[0]), "train_bond_centres": int(n_bonds),
+            "train_loss_first": loss0, "train_loss_final": loss,
             "train_seconds": round(train_s, 3),
             "held_out_mean_iterations_gaussian_start": float(np.mean(it_g)),
             "held_out_mean_iterations_learned_start": float(np.mean(it_l)),
             "held_out_mean_seconds_gaussian_start": round(float(np.mean(s_g)), 4),
             "held_out_mean_seconds_learned_start": round(float(np.mean(s_l)), 4),
-            "held_out_max_energy_difference_ha": float(np.max(de)),
+            "held_out_max_energy_difference_per_atom_ha": float(np.max(de)),
+            "held_out_fallbacks": fell_back,
             "held_out_mean_iterations_own_fit_start": float(np.mean(it_c)) if it_c else None}
 
 
@@ -959,8 +1016,9 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
     """ChFSI iterations on the 400-atom cluster with s and p projectors (R = 26, lmax 60, 96
     radial functions, d = 357216, 192 x 120 x 240 grid, 1600 projectors), 880 states, degree
     20: the mixed filter in residual form over chunks of 128 states (19 split-BF16 H.X per
-    state), then Cholesky-QR twice and Rayleigh-Ritz over all 880 states with an FP64 H.X and
-    double-float Gram matrices and rotations (FP64 factorisation, eigensolve and residuals).
+    state), then Cholesky-QR twice and Rayleigh-Ritz over all 880 states with an FP64 H.X (its
+    projector pair as exact slice products) and the Gram matrices and rotations as exact slice
+    products on the tensor cores (FP64 factorisation, eigensolve and residuals).
     The block starts random (seeded); one untimed iteration with the first-pass interval
     (Lanczos bounds), then `timed_iters` timed iterations (CUDA events, per-class device
     times). Every call goes through the C ABI."""
@@ -989,7 +1047,7 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
     ctx._ws.clear()
     torch.cuda.empty_cache()
     cs.cs_set_rr_precision(ctx, cs.CS_FP64)
-    cs.cs_set_dense_precision(ctx, cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
     gen = torch.Generator(device=dev)
     gen.manual_seed(w.x_seed)
     X = torch.randn((n_s, ctx.d), generator=gen, dtype=torch.float64, device=dev)
@@ -1093,8 +1151,9 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
                        f"lmax=60, 96 radial fns/l, d={ctx.d}, grid 192x120x240, {n_s} states "
                        f"(filter in chunks of {chunk}), degree {degree}",
            "step": "one ChFSI iteration: residual-form mixed filter (19 split-BF16 H.X per "
-                   "state) + CholQR x2 (double-float Gram/rotations) + Rayleigh-Ritz (FP64 H.X, "
-                   "double-float Gram/rotations, FP64 eigensolve and residuals)",
+                   "state) + CholQR x2 + Rayleigh-Ritz (FP64 H.X with the projector pair as "
+                   "slice products; Gram matrices and rotations as exact slice products on the "
+                   "tensor cores; FP64 factorisation, eigensolve and residuals)",
            "ms_per_iteration": round(ms, 1),
            "iteration_ms": [round(t, 1) for t in times],
            "value": round(applies / (ms / 1e3), 1), "unit": "applies/s",

@@ -160,7 +160,8 @@ cs_status cs_set_rr_precision(cs_ctx* ctx, cs_precision prec);
 /* Arithmetic of the tall-skinny Gram matrices (X^T X, X^T H X) and block rotations (X R^-1,
  * X Q, H X Q) of Cholesky-QR and Rayleigh-Ritz (Sec. 3.1.1, 3.2.1): CS_FP64 (default),
  * CS_DF64 (double-float on the FP32 pipe, FP64 storage, relative errors near 1e-14) or
- * CS_FP64_SLICED (exact integer-slice products on the tensor cores, rounded once). The small
+ * CS_FP64_SLICED (exact integer-slice products on the tensor cores, rounded once; with it the
+ * projector pair of every FP64 H.X is also taken as slice products). The small
  * factorisation, eigensolve and residual norms stay FP64. Workspaces must be sized
  * (cs_workspace_bytes) after this call. CS_ERR_ARG otherwise. */
 cs_status cs_set_dense_precision(cs_ctx* ctx, cs_precision prec);
@@ -370,6 +371,12 @@ cs_status cs_device_error(cs_ctx* ctx, int* code);
 /* Last error message of the context (static storage inside ctx; "" if none). A NULL ctx
  * returns the message of the last failed cs_basis_init on this thread. */
 const char* cs_last_error(const cs_ctx* ctx);
+
+/* Measurement helper for roofline denominators (the paper has no counterpart): the
+ * sustained FP32 and FP64 fused multiply-add rates of device `cuda_device` in TFLOP/s (8
+ * independent FMA chains per thread, 4 CTAs of 256 threads per SM, best of five timed
+ * launches). Synchronising; restores the caller's current device. */
+cs_status cs_measure_peaks(int cuda_device, double* fp32_tflops, double* fp64_tflops);
 
 /* Number of kernels this library has launched on `ctx` since it was created. */
 long long cs_launch_count(const cs_ctx* ctx);

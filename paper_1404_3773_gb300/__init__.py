@@ -29,6 +29,7 @@ __all__ = [
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
     "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
+    "cs_measure_peaks",
     "cs_lobpcg_workspace_bytes", "cs_lobpcg",
     # SCF pieces (include/cs_scf.h)
     "CS_DENSITY_CHUNK", "CS_MIXER_MAX_HISTORY", "CS_GRID_INTEGRALS_MAX", "ScfParams",
@@ -135,6 +136,7 @@ _SIGS = {
                            ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
+    "cs_measure_peaks": (_i, [_i, _dp, _dp]),
     "cs_launch_count": (_ll, [_vp]),
     "cs_lobpcg_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_lobpcg": (_i, [_vp, _i, _i, _vp, _ll, _d, _i, _i, _vp, _vp, ctypes.POINTER(_i),
@@ -634,6 +636,15 @@ def cs_batch_tune_times(batch: Batch):
 
 def cs_batch_last_error(batch: Batch) -> str:
     return _lib.cs_batch_last_error(batch.handle).decode()
+
+
+def cs_measure_peaks(cuda_device: int = 0):
+    """(FP32, FP64) sustained fused multiply-add rates of the device in TFLOP/s."""
+    f32, f64 = _d(), _d()
+    st = _lib.cs_measure_peaks(int(cuda_device), ctypes.byref(f32), ctypes.byref(f64))
+    if st != 0:
+        raise CsError(st, "cs_measure_peaks failed")
+    return f32.value, f64.value
 
 
 def cs_last_error(ctx: Context | None) -> str:

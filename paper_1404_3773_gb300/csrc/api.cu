@@ -63,11 +63,16 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.HXr = take(d * ns * 8);
   // weights s_i(theta_j) of the residual-form filter: FP64 table and one in the block type
   o.chw = take((size_t)(kMaxRitzDegree + 1) * ns * 16);
-  // split operands and partial sums of the slice-product Gram matrices and rotations
-  o.oz = take(c->dense_prec == CS_FP64_SLICED
-                  ? std::max(oz_gram_work_bytes(T.d, n_s, n_s, false),
-                             oz_rotate_work_bytes(T.d, n_s, n_s))
-                  : 0);
+  // split operands and partial sums of the slice-product Gram matrices and rotations (and of
+  // the FP64 projector pair, which takes the same arithmetic)
+  size_t ozb = 0;
+  if (c->dense_prec == CS_FP64_SLICED) {
+    ozb = std::max(oz_gram_work_bytes(T.d, n_s, n_s, false), oz_rotate_work_bytes(T.d, n_s, n_s));
+    if (np)
+      ozb = std::max(ozb, std::max(oz_gram_work_bytes(T.d, (int)np, n_s, false),
+                                   oz_rotate_work_bytes(T.d, (int)np, n_s)));
+  }
+  o.oz = take(ozb);
   // last, so that every other offset is the same for both precisions
   auto is_f32 = [](cs_precision p) { return p == CS_FP32 || p == CS_MIXED_BF16; };
   const bool reduced = is_f32(prec) || is_f32(c->rr_prec);
@@ -236,6 +241,20 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
                     launch_kb_tc(c->kb_tabA, c->kb_tabB, ks, reinterpret_cast<const float*>(X),
                                  ldx, c->d32.h, reinterpret_cast<float*>(kbZ), H.d,
                                  work + lm.kbtc, c->dev_err, st, &nl));
+    } else if (std::is_same<T, double>::value && c->dense_prec == CS_FP64_SLICED) {
+      // FP64 pair as exact slice products on the tensor cores (the dense steps' arithmetic)
+      double* Wkb = reinterpret_cast<double*>(work + lay.Wkb);
+      const double* Xd = reinterpret_cast<const double*>(X);
+      double* Zd = reinterpret_cast<double*>(kbZ);
+      void* oz = work + lay.oz;
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 4,
+                    launch_oz_gram(c->d64.pcoef, H.d, Xd, ldx, H.d, c->n_p, n_s, Wkb, c->n_p, oz,
+                                   c->dev_err, st));
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 1,
+                    launch_scale_rows<double>(Wkb, c->n_p, n_s, c->n_p, c->d64.h, st));
+      CS_LAUNCH_CLS(c, prof_cls<T>(4), 4,
+                    launch_oz_rotate(c->d64.pcoef, H.d, Wkb, c->n_p, H.d, c->n_p, n_s, Zd, H.d,
+                                     oz, c->dev_err, st));
     } else {
       T* Wkb = reinterpret_cast<T*>(work + lay.Wkb);
       T* part = reinterpret_cast<T*>(work + lay.part);

@@ -1001,6 +1001,297 @@ __global__ void __launch_bounds__(1024) k_oa_final(const double* __restrict__ S,
   for (int i = tid; i < n; i += nt) theta[i] = lam[i];
 }
 
+// ------------------------------------------------------------------ large-n first stage
+// For blocks whose tridiagonal solve does not fit one CTA's shared memory (n above ~220; the
+// 880-state block of the 400-atom cluster) the first stage runs in FP64 as a sequence of
+// device-wide kernels on global (L2-resident) arrays instead of one CTA: per Householder step a
+// reflector kernel (one CTA), p = A v with one warp per row (the trailing block is symmetric,
+// so each warp reads a contiguous column), w = p - (v.p) v (one CTA) and the rank-2 update;
+// then bisection and inverse iteration with one thread per eigenvalue (as in the one-CTA
+// solver), Gram-Schmidt inside clusters (one CTA), and the reflectors applied to the
+// eigenvector block one per kernel, one warp per column. FP64 here (not FP32 as in the small
+// solver): in a dense band of eigenvalues (gaps near 1e-4 of the spectral range) FP32 vectors
+// leave couplings that the refinement cannot resolve pair by pair, and the cluster step would
+// then diagonalise most of the band on one thread.
+namespace {
+
+template <typename T>
+struct LeArrays {
+  T *A, *Y, *L, *d, *e, *e2, *lam, *vv, *pw, *bnd;
+  int* cst;
+};
+
+// A, Y, L in `big` (3 n^2 values), the vectors in `vec` (8 n + 4 values, then n ints)
+template <typename T>
+LeArrays<T> le_arrays(T* big, T* vec, int n) {
+  LeArrays<T> a;
+  const size_t n2 = (size_t)n * n;
+  a.A = big;
+  a.Y = a.A + n2;
+  a.L = a.Y + n2;
+  a.d = vec;
+  a.e = a.d + n;
+  a.e2 = a.e + n;
+  a.lam = a.e2 + n;
+  a.vv = a.lam + n;
+  a.pw = a.vv + n;
+  a.bnd = a.pw + n;
+  a.cst = reinterpret_cast<int*>(a.bnd + 4);
+  return a;
+}
+
+template <typename T>
+__device__ T le_block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = T(0);
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+template <typename T>
+__global__ void k_le_init(const double* __restrict__ Ain, int n, T* __restrict__ A) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  A[idx] = (T)(0.5 * (Ain[i + (size_t)j * n] + Ain[j + (size_t)i * n]));
+}
+
+// reflector of step k: v (unit) into vv and into column k below the diagonal; alpha into e[k]
+template <typename T>
+__global__ void __launch_bounds__(1024) k_le_reflector(T* __restrict__ A, int n, int k,
+                                                       T* __restrict__ vv, T* __restrict__ e) {
+  __shared__ T red[32];
+  const int m = n - k - 1;
+  T* col = A + (k + 1) + (size_t)k * n;
+  T xs = T(0);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) xs += col[i] * col[i];
+  const T xnorm = sqrt(le_block_sum(xs, red));
+  const T x0 = col[0];
+  const T alpha = (x0 >= T(0)) ? -xnorm : xnorm;
+  const T vnorm2 = T(2) * (xnorm * xnorm - alpha * x0);
+  const bool skip = !(vnorm2 > T(0));
+  const T inv = skip ? T(0) : T(1) / sqrt(vnorm2);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T v = skip ? T(0) : (i == 0 ? col[i] - alpha : col[i]) * inv;
+    vv[i] = v;
+    col[i] = v;
+  }
+  if (threadIdx.x == 0) e[k] = skip ? x0 : alpha;
+}
+
+// pw[i] = sum_j A[k+1+j, k+1+i] v[j] (one warp per i; column k+1+i is contiguous)
+template <typename T>
+__global__ void k_le_matvec(const T* __restrict__ A, int n, int k, const T* __restrict__ vv,
+                            T* __restrict__ pw) {
+  const int m = n - k - 1;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  const T* c = A + (k + 1) + (size_t)(k + 1 + i) * n;
+  T s = T(0);
+  for (int j = lane; j < m; j += 32) s += c[j] * vv[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) pw[i] = s;
+}
+
+// pw <- pw - (v . pw) v
+template <typename T>
+__global__ void __launch_bounds__(1024) k_le_w(int n, int k, const T* __restrict__ vv,
+                                               T* __restrict__ pw) {
+  __shared__ T red[32];
+  const int m = n - k - 1;
+  T kp = T(0);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) kp += vv[i] * pw[i];
+  const T K = le_block_sum(kp, red);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) pw[i] -= K * vv[i];
+}
+
+// trailing block -= 2 (v w^T + w v^T)
+template <typename T>
+__global__ void k_le_update(T* __restrict__ A, int n, int k, const T* __restrict__ vv,
+                            const T* __restrict__ pw) {
+  const int m = n - k - 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  A[(k + 1 + i) + (size_t)(k + 1 + j) * n] -= T(2) * (vv[i] * pw[j] + pw[i] * vv[j]);
+}
+
+// d, e of the tridiagonal; e2 = e^2; Gershgorin bounds into bnd[0..1]
+template <typename T>
+__global__ void __launch_bounds__(1024) k_le_tridiag(const T* __restrict__ A, int n,
+                                                     T* __restrict__ d, T* __restrict__ e,
+                                                     T* __restrict__ e2, T* __restrict__ bnd) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = A[i + (size_t)i * n];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (n >= 2) e[n - 2] = A[(n - 1) + (size_t)(n - 2) * n];
+    e[n - 1] = T(0);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) e2[j] = (j < n - 1) ? e[j] * e[j] : T(0);
+  if (threadIdx.x == 0) {
+    T lo = d[0], hi = d[0];
+    for (int j = 0; j < n; ++j) {
+      const T r = (j > 0 ? fabs(e[j - 1]) : T(0)) + (j < n - 1 ? fabs(e[j]) : T(0));
+      lo = fmin(lo, d[j] - r);
+      hi = fmax(hi, d[j] + r);
+    }
+    bnd[0] = lo;
+    bnd[1] = hi;
+  }
+}
+
+// eigenvalue i by bisection on Sturm counts, its eigenvector of T by inverse iteration
+// (column i of Y; L factors in column i of L), one thread per eigenvalue
+template <typename T>
+__global__ void k_le_bisect(int n, const T* __restrict__ d, const T* __restrict__ e,
+                            const T* __restrict__ e2, const T* __restrict__ bnd,
+                            T* __restrict__ lam, T* __restrict__ Y, T* __restrict__ Ls) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T glo = bnd[0], ghi = bnd[1];
+  const T tnorm = fmax(fabs(glo), fabs(ghi)) + T(1e-30);
+  const T piv = EigEps<T>::v() * tnorm;
+  T a = glo - piv, b = ghi + piv;
+  for (int it = 0; it < 128; ++it) {
+    const T x = T(0.5) * (a + b);
+    if (!(x > a && x < b)) break;
+    int cnt = 0;
+    T q = d[0] - x;
+    if (fabs(q) < piv) q = -piv;
+    cnt += (q < T(0));
+    for (int j = 1; j < n; ++j) {
+      q = d[j] - x - e2[j - 1] / q;
+      if (fabs(q) < piv) q = -piv;
+      cnt += (q < T(0));
+    }
+    if (cnt > i) b = x;
+    else a = x;
+  }
+  const T x = T(0.5) * (a + b);
+  lam[i] = x;
+  T* y = Y + (size_t)i * n;
+  T* L = Ls + (size_t)i * n;
+  for (int j = 0; j < n; ++j) {
+    const unsigned hsh = (unsigned)(j + 1) * 2654435761u ^ (unsigned)(i + 1) * 40503u;
+    y[j] = T(0.5) + (T)((hsh >> 8) & 0xffffu) * T(1.0 / 65536.0);
+  }
+  for (int rep = 0; rep < 3; ++rep) {
+    T Dp = d[0] - x;
+    if (fabs(Dp) < piv) Dp = piv;
+    T zp = y[0];
+    y[0] = zp / Dp;
+    for (int j = 1; j < n; ++j) {
+      const T l = e[j - 1] / Dp;
+      L[j] = l;
+      const T z = y[j] - l * zp;
+      T Dj = d[j] - x - l * e[j - 1];
+      if (fabs(Dj) < piv) Dj = piv;
+      y[j] = z / Dj;
+      zp = z;
+      Dp = Dj;
+    }
+    for (int j = n - 2; j >= 0; --j) y[j] -= L[j + 1] * y[j + 1];
+    T ss = T(0);
+    for (int j = 0; j < n; ++j) ss += y[j] * y[j];
+    const T sc = T(1) / sqrt(ss);
+    for (int j = 0; j < n; ++j) y[j] *= sc;
+  }
+}
+
+// clusters of eigenvalues closer than tol |T|: modified Gram-Schmidt, twice (one CTA)
+template <typename T>
+__global__ void __launch_bounds__(1024) k_le_clusters(int n, const T* __restrict__ lam,
+                                                      const T* __restrict__ bnd, T tol,
+                                                      T* __restrict__ Y,
+                                                      int* __restrict__ cst) {
+  __shared__ int kmax;
+  const T tnorm = fmax(fabs(bnd[0]), fabs(bnd[1])) + T(1e-30);
+  if (threadIdx.x == 0) {
+    int start = 0, km = 0;
+    for (int i = 0; i < n; ++i) {
+      if (i > 0 && lam[i] - lam[i - 1] > tol * tnorm) start = i;
+      cst[i] = start;
+      km = max(km, i - start);
+    }
+    kmax = km;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 2; ++sweep)
+    for (int pos = 1; pos <= kmax; ++pos) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (i - cst[i] != pos) continue;
+        T* y = Y + (size_t)i * n;
+        for (int jv = cst[i]; jv < i; ++jv) {
+          const T* u = Y + (size_t)jv * n;
+          T dot = T(0);
+          for (int j = 0; j < n; ++j) dot += u[j] * y[j];
+          for (int j = 0; j < n; ++j) y[j] -= dot * u[j];
+        }
+        T ss = T(0);
+        for (int j = 0; j < n; ++j) ss += y[j] * y[j];
+        const T sc = T(1) / sqrt(ss);
+        for (int j = 0; j < n; ++j) y[j] *= sc;
+      }
+      __syncthreads();
+    }
+}
+
+// Y[k+1:, j] -= 2 (v_k . Y[k+1:, j]) v_k for every column j (one warp per column)
+template <typename T>
+__global__ void k_le_apply(const T* __restrict__ A, int n, int k, T* __restrict__ Y) {
+  const int m = n - k - 1;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  const T* v = A + (k + 1) + (size_t)k * n;
+  T* y = Y + (k + 1) + (size_t)j * n;
+  T t = T(0);
+  for (int i = lane; i < m; i += 32) t += v[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  t *= T(2);
+  for (int i = lane; i < m; i += 32) y[i] -= t * v[i];
+}
+
+template <typename T>
+__global__ void k_le_out(const T* __restrict__ Y, long long n2, double* __restrict__ V,
+                         int* __restrict__ status) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n2) V[idx] = (double)Y[idx];
+  if (idx == 0) status[0] = 1;
+}
+
+// FP64 tridiagonal solve on device-wide kernels: A, Y, L in `big` (3 n^2 doubles), vectors in
+// `vec` (8 n + 4 doubles and n ints); V0 receives the eigenvectors (ascending eigenvalues)
+cudaError_t le_stage(const double* Ain, int n, double* big, double* vec, double* V0, int* status,
+                     cudaStream_t st) {
+  using T = double;
+  const LeArrays<T> a = le_arrays<T>(big, vec, n);
+  const long long n2 = (long long)n * n;
+  k_le_init<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(Ain, n, a.A);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    k_le_reflector<T><<<1, 1024, 0, st>>>(a.A, n, k, a.vv, a.e);
+    k_le_matvec<T><<<(m + 7) / 8, 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
+    k_le_w<T><<<1, 1024, 0, st>>>(n, k, a.vv, a.pw);
+    const long long mm = (long long)m * m;
+    k_le_update<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
+  }
+  k_le_tridiag<T><<<1, 1024, 0, st>>>(a.A, n, a.d, a.e, a.e2, a.bnd);
+  k_le_bisect<T><<<(n + 31) / 32, 32, 0, st>>>(n, a.d, a.e, a.e2, a.bnd, a.lam, a.Y, a.L);
+  k_le_clusters<T><<<1, 1024, 0, st>>>(n, a.lam, a.bnd, T(1e-10), a.Y, a.cst);
+  for (int k = n - 3; k >= 0; --k) k_le_apply<T><<<(n + 7) / 8, 256, 0, st>>>(a.A, n, k, a.Y);
+  k_le_out<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(a.Y, n2, V0, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, double* work,
                               int* status, cudaStream_t stream) {
   const size_t n2 = (size_t)n * n;
@@ -1015,7 +1306,6 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
   double* scratch = scal + 4;     // 2 n^2 + 2 n (final step)
   const int threads = 256;
   // 1. FP32 eigendecomposition of sym(A) -> V0 (FP64 copy of the FP32 vectors)
-  size_t smem = (2 * n2 + 7 * (size_t)n) * sizeof(float);
   cudaError_t e;
   const size_t smem_b = (4 * n2 + 7 * (size_t)n) * sizeof(float);
   if (smem_b <= 200 * 1024) {
@@ -1025,15 +1315,10 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
     if (e != cudaSuccess) return e;
     k_sym_eig<float, true, true><<<1, threads, smem_b, stream>>>(A, n, nullptr, V0, nullptr,
                                                                  status);
-  } else if (smem <= 200 * 1024) {
-    e = cudaFuncSetAttribute(k_sym_eig<float, true, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_sym_eig<float, true, false><<<1, threads, smem, stream>>>(A, n, nullptr, V0, nullptr,
-                                                                status);
   } else {
-    k_sym_eig<float, false, false><<<1, threads, 0, stream>>>(A, n, nullptr, V0,
-                                                              reinterpret_cast<float*>(P), status);
+    // device-wide FP64 stage: A, Y, L in P, S, G; its vectors in Ep (free until the
+    // refinement); status as the one-CTA solver's
+    if ((e = le_stage(A, n, P, Ep, V0, status, stream)) != cudaSuccess) return e;
   }
   // 2. orthonormalise to FP64 precision (Newton-Schulz), then refine in FP64
   double* Vc = V0;

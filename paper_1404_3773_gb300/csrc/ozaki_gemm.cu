@@ -275,20 +275,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// D[t] summed over the K groups in 64-bit integers, then combined: C[i + j ldc]
-__global__ void k_oz_reduce(const int* __restrict__ part, int groups, long long Mp, long long Np,
-                            long long M, int N, const int* __restrict__ EA,
-                            const int* __restrict__ EB, double* __restrict__ C, long long ldc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= M * N) return;
-  const long long i = t % M, j = t / M;
+// D[t] summed over the K groups in 64-bit integers, then combined: C[i + j ldc]. One CTA of 8
+// warps per 32 consecutive outputs i of one column j: warp w sums the groups w, w + 8, ...
+// (lanes on consecutive i: coalesced rows of the partials), the 8 warps' sums are added in
+// shared memory, and warp 0 combines.
+__global__ void __launch_bounds__(256) k_oz_reduce(const int* __restrict__ part, int groups,
+                                                   long long Mp, long long Np, long long M, int N,
+                                                   const int* __restrict__ EA,
+                                                   const int* __restrict__ EB,
+                                                   double* __restrict__ C, long long ldc) {
+  __shared__ long long acc_sh[8][kS][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long tiles_i = (M + 31) / 32;
+  const long long i0 = (blockIdx.x % tiles_i) * 32, j = blockIdx.x / tiles_i;
+  const long long i = i0 + lane;  // < Mp: the padded rows of the partials exist
   int64_t D[kS];
 #pragma unroll
   for (int d = 0; d < kS; ++d) D[d] = 0;
-  for (int zz = 0; zz < groups; ++zz)
+  for (int zz = warp; zz < groups; zz += 8)
 #pragma unroll
     for (int d = 0; d < kS; ++d) D[d] += part[(((long long)zz * kS + d) * Np + j) * Mp + i];
-  C[i + j * ldc] = oz_combine(D, EA[i], EB[j], kBeta, kS);
+#pragma unroll
+  for (int d = 0; d < kS; ++d) acc_sh[warp][d][lane] = D[d];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int d = 0; d < kS; ++d) {
+      long long t = 0;
+      for (int w = 0; w < 8; ++w) t += acc_sh[w][d][lane];
+      D[d] = t;
+    }
+    if (i < M) C[i + j * ldc] = oz_combine(D, EA[i], EB[j], kBeta, kS);
+  }
 }
 
 // E[c] = ceil(log2 max_r |X[r + c ld]|) over r < d (one CTA per column; 0 for zero columns and
@@ -445,9 +463,9 @@ cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B,
   k_oz_mma<<<grid, kThreads, kSmem, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p.groups > 1) {
-    const long long n = M * (long long)N;
-    k_oz_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, (int)p.groups, p.mpad, p.npad,
-                                                             M, N, EA, EB, C, ldc);
+    const long long blocks = ((M + 31) / 32) * (long long)N;
+    k_oz_reduce<<<(unsigned)blocks, 256, 0, st>>>(part, (int)p.groups, p.mpad, p.npad, M, N, EA,
+                                                  EB, C, ldc);
     e = cudaGetLastError();
   }
   return e;

@@ -130,11 +130,15 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
     static_assert(NT == 8, "one column (analysis) or one octet of 8 columns (synthesis)");
     float v[NT][8];
     if (MODE == 0) {
-      // A[c][n] = X[(l^2 + mi) N + n + s ldx]; task = (column cc, octet oc of n)
-      const int oc = tid % (KC / 8), n0 = kb + oc * 8;
+      // A[c][n] = X[(l^2 + mi) N + n + s ldx]; task = (column cc, octet oc of n). In one store
+      // instruction lanes 8q .. 8q+7 take eight consecutive columns of one octet, whose 16-byte
+      // runs are adjacent in the canonical layout (no bank conflicts); four lanes cover 128
+      // contiguous bytes of each column in the loads.
+      const int warp_id = tid >> 5, ln = tid & 31;
 #pragma unroll
       for (int u = 0; u < NT; ++u) {
-        const int cc = tid / (KC / 8) + u * (kThreads / (KC / 8));
+        const int cc = (warp_id * 4 + (u >> 1)) * 8 + (ln & 7);
+        const int oc = (u & 1) * 4 + (ln >> 3), n0 = kb + oc * 8;
         const int c = c0 + cc;
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[u][i] = 0.f;
@@ -155,7 +159,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_radial(TcShape sh,
       }
 #pragma unroll
       for (int u = 0; u < NT; ++u) {
-        const int cc = tid / (KC / 8) + u * (kThreads / (KC / 8));
+        const int cc = (warp_id * 4 + (u >> 1)) * 8 + (ln & 7);
+        const int oc = (u & 1) * 4 + (ln >> 3);
         __align__(16) __nv_bfloat16 h[8], lo[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) split_bf16(v[u][i], h[i], lo[i]);

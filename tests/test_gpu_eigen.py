@@ -329,3 +329,27 @@ def test_chfsi_mixed_filter_meets_eigenvalue_gate():
     print(f"mixed filter: {it} iterations to 1e-5, max |dtheta| vs FP64 {dev:.3e}")
     assert float(rr.cpu().numpy()[:w.n_want].max()) <= 1e-5
     assert dev < 1e-6, dev
+
+
+def test_rayleigh_ritz_large_block_matches_oracle():
+    """A 300-state block (the projected matrix's tridiagonal solve no longer fits one CTA's
+    shared memory, so the device-wide FP32 stage runs before the FP64 refinement): Ritz values
+    and residual norms against the oracle's Rayleigh-Ritz, on the oscillator basis (d = 1936)."""
+    torch, cs = need_gpu()
+    w = HO
+    ctx = make_ctx(w)
+    Hh = oracle_H(w.name)
+    X = eigen.cholqr(W.gaussian_block(4300, ctx.d, 300))
+    th_ref, X_ref, _, res_ref = eigen.rayleigh_ritz(Hh.apply, X)
+    Xd = to_dev(X)
+    theta = torch.empty(300, dtype=torch.float64, device="cuda")
+    resid = torch.empty_like(theta)
+    cs.cs_rayleigh_ritz(ctx, Xd, theta, resid)
+    torch.cuda.synchronize()
+    th = theta.cpu().numpy()
+    print(f"n_s 300: max |dtheta| {np.max(np.abs(th - th_ref)):.3e}, |theta| max "
+          f"{np.abs(th_ref).max():.3e}")
+    assert np.max(np.abs(th - th_ref)) < 1e-11 * np.abs(th_ref).max()
+    assert np.max(np.abs(resid.cpu().numpy() - res_ref)) < 1e-10 * np.abs(res_ref).max()
+    got = to_host(Xd, ctx.d)
+    assert np.max(np.abs(got.T @ got - np.eye(300))) < 1e-12

@@ -154,3 +154,23 @@ def test_erf400kb_full_size():
         print(f"erf400kb 1600 projectors, 128 states {prec}: fro {fro:.3e} col {col:.3e}")
         assert fro <= TOL[prec][0] and col <= TOL[prec][1], (prec, fro, col)
     assert cs.cs_device_error(ctx) == 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_projector_pair_as_slice_products_matches_oracle(case):
+    """With CS_FP64_SLICED dense products the FP64 H.X takes its projector pair as exact
+    slice products on the tensor cores: the FP64 bar against the oracle still holds."""
+    torch, cs = need_gpu()
+    w, natoms = CASES[case]
+    atoms = W.place_atoms(w.x_seed + 11, natoms, 0.6 * w.R, 1.0)
+    ctx = make_ctx(w)
+    cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
+    Hkb = _oracle_with_projectors(w, atoms)
+    X = w.x_block()
+    ref = Hkb.apply(X)
+    _set_library_projectors(torch, cs, ctx, atoms)
+    got = _apply(torch, cs, ctx, X, "fp64")
+    fro, col = rel_errors(got, ref)
+    print(f"kb {case} fp64 sliced: fro {fro:.3e} col {col:.3e}")
+    assert fro <= 1e-11 and col <= 1e-11, (fro, col)
+    assert cs.cs_device_error(ctx) == 0
