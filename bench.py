@@ -467,7 +467,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else batched_measure(dev)
     at_scale = None if args.no_at_scale else at_scale_measure(dev)
-    at_scale_chfsi = at_scale_chfsi_measure(dev) if args.at_scale_chfsi else None
+    at_scale_chfsi = None if args.no_at_scale_chfsi else at_scale_chfsi_measure(dev)
     scf = None if args.no_scf else scf_measure(dev)
     first_solve = None if args.no_scf else first_solve_measure(dev)
     eigen_gate = None if args.no_scf else eigen_gate_measure(dev)
@@ -721,7 +721,7 @@ def _center_features(cs, atoms, mids, mu, width):
 
 
 def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, steps=3000,
-                         ceiling=True, rcut=4.0):
+                         ceiling=True, rcut=4.0, ridge=1e-4, n_val=24):
     """The learned initial density: small clusters of 4-12 Z=4 erf pseudo-atoms (R = 9, lmax 10,
     16 radial functions, 32 x 22 x 42 grid), SCF (mixed filter) from the Gaussian start to
     |dE| <= tol. The correction to the start is expanded in unit-integral Gaussians on every
@@ -731,10 +731,15 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
     functions (weighted least squares); a 17-128-128-128-5 tanh network learns the fitted
     coefficients from each centre's radial descriptor and a bond flag (Adam). On the held-out
     clusters the SCF runs from the Gaussian start, from the learned start, and (ceiling) from
-    the cluster's own best fit. The learned start is the Gaussian start plus the predicted
-    correction, clipped at zero and renormalised to the electron count. Fallback: if the
-    predicted correction's integral of |correction| exceeds half the electron count (a
-    prediction far outside what training saw), the Gaussian start is kept."""
+    the cluster's own best fit. The fits are ridge-regularised (ridge tr(M)/n |c|^2): the atom
+    and bond Gaussians overlap, and unregularised fits cancel large coefficients that a network
+    cannot learn. The learned start is the Gaussian start plus alpha times the predicted
+    correction, clipped at zero and renormalised to the electron count. alpha is chosen on the
+    last n_val training clusters, which the network does not see: the value of (0, 0.25, 0.5,
+    0.75, 1) with the fewest SCF iterations there; alpha = 0 is the fallback to the Gaussian
+    start. A cluster also falls back if the integral of |predicted correction| per electron
+    exceeds twice the largest value among the training clusters' own fits (a prediction outside
+    what training saw)."""
     import torch
 
     import paper_1404_3773_gb300 as cs
@@ -784,15 +789,23 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
     # training data
     D, C = [], []
     n_bonds = 0
+    corr_max = 0.0  # largest integral of |fitted correction| per electron in training
     for i in range(n_train):
         atoms = cluster(i)
         start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
         _, _, rho, _ = scf(atoms, start)
         cen, mids = centres(atoms)
         n_bonds += len(mids)
-        C.append(cs.cs_fit_atom_density(ctx, cen, sig, (rho - start).contiguous(), ridge=1e-8))
+        cfit = cs.cs_fit_atom_density(ctx, cen, sig, (rho - start).contiguous(), ridge=ridge)
+        corr = torch.zeros_like(start)
+        cs.cs_atom_density(ctx, cen, sig, cfit, corr)
+        corr_max = max(corr_max, cs.cs_grid_integrals(ctx, [corr.abs().contiguous()])[0] /
+                       (4.0 * len(atoms)))
+        C.append(cfit)
         D.append(_center_features(cs, atoms, mids, mu, width))
-    D, C = np.concatenate(D), np.concatenate(C)
+    n_fit_centres = sum(len(centres(cluster(i))[0]) for i in range(n_train - n_val))
+    D_all, C_all = np.concatenate(D), np.concatenate(C)
+    D, C = D_all[:n_fit_centres], C_all[:n_fit_centres]
     d_mean, d_std = D.mean(axis=0), D.std(axis=0) + 1e-6
     c_scale = float(np.abs(C).max()) or 1.0
     dims = [D.shape[1], hidden, hidden, hidden, len(sig)]
@@ -811,6 +824,33 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
         cs.cs_mlp_train_step(net, Xd, Td, 1e-3, want_loss=False)
     loss = cs.cs_mlp_loss_grad(net, Xd, Td)[0]
     train_s = time.perf_counter() - t0
+    def learned_start(atoms, start, alpha):
+        """(density, accepted): start + alpha * prediction, clipped at 0, renormalised"""
+        ne = 4.0 * len(atoms)
+        cen, mids = centres(atoms)
+        feats = (_center_features(cs, atoms, mids, mu, width) - d_mean) / d_std
+        coef = cs.cs_mlp_forward(net, torch.tensor(feats.T.copy(), dtype=torch.float32,
+                                                   device=dev)).cpu().numpy().T * c_scale
+        corr = torch.zeros_like(start)
+        cs.cs_atom_density(ctx, cen, sig, coef.astype(np.float64), corr)
+        if cs.cs_grid_integrals(ctx, [corr.abs().contiguous()])[0] / ne > 2.0 * corr_max:
+            return start, False
+        rho = torch.clamp(start + alpha * corr, min=0.0).contiguous()
+        rho *= ne / cs.cs_grid_integrals(ctx, [rho])[0]
+        return rho, True
+
+    # alpha on the validation clusters (not used to fit the network)
+    alphas = (0.0, 0.25, 0.5, 0.75, 1.0)
+    val_iters = {}
+    for al in alphas:
+        its = []
+        for i in range(n_train - n_val, n_train):
+            atoms = cluster(i)
+            start = gaussian_atom_density_t(xyz, atoms, 4.0, 1.0).contiguous()
+            rho0 = start if al == 0.0 else learned_start(atoms, start, al)[0]
+            its.append(scf(atoms, rho0)[0])
+        val_iters[al] = float(np.mean(its))
+    alpha = min(alphas, key=lambda x: (val_iters[x], x))
     # held-out comparison
     it_g, it_l, s_g, s_l, de, it_c, fell_back = [], [], [], [], [], [], 0
     for i in range(n_train, n_train + n_test):
@@ -820,20 +860,13 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
         a, sa, rho_c, ea = scf(atoms, start)
         cen, mids = centres(atoms)
         if ceiling:  # start from this cluster's own best-fit correction
-            cfit = cs.cs_fit_atom_density(ctx, cen, sig, (rho_c - start).contiguous(), ridge=1e-8)
+            cfit = cs.cs_fit_atom_density(ctx, cen, sig, (rho_c - start).contiguous(), ridge=ridge)
             fitted = start.clone()
             cs.cs_atom_density(ctx, cen, sig, cfit, fitted)
             fitted *= ne / cs.cs_grid_integrals(ctx, [fitted])[0]
             it_c.append(scf(atoms, fitted)[0])
-        feats = (_center_features(cs, atoms, mids, mu, width) - d_mean) / d_std
-        coef = cs.cs_mlp_forward(net, torch.tensor(feats.T.copy(), dtype=torch.float32,
-                                                   device=dev)).cpu().numpy().T * c_scale
-        corr = torch.zeros_like(start)
-        cs.cs_atom_density(ctx, cen, sig, coef.astype(np.float64), corr)
-        ok = cs.cs_grid_integrals(ctx, [corr.abs().contiguous()])[0] <= 0.5 * ne
+        learned, ok = learned_start(atoms, start, alpha) if alpha > 0.0 else (start, False)
         if ok:
-            learned = torch.clamp(start + corr, min=0.0).contiguous()
-            learned *= ne / cs.cs_grid_integrals(ctx, [learned])[0]
             b, sb, _, eb = scf(atoms, learned)
         else:  # fallback: the Gaussian start
             fell_back += 1
@@ -845,7 +878,8 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
         de.append(abs(ea - eb) / len(atoms))
     net.close()
     ctx.close()
-    return {"workload": f"{n_train} training + {n_test} held-out clusters of 4-12 Z=4 erf atoms "
+    return {"workload": f"{n_train - n_val} training + {n_val} validation + {n_test} held-out "
+                        "clusters of 4-12 Z=4 erf atoms "
                         "(R 9, lmax 10, N 16, grid 32x22x42), mixed-filter SCF to "
                         f"|dE| <= {tol:g} Ha; correction on atoms and on bond midpoints "
                         f"(pairs closer than {rcut:g} bohr)",
@@ -858,6 +892,9 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
             "held_out_mean_seconds_learned_start": round(float(np.mean(s_l)), 4),
             "held_out_max_energy_difference_per_atom_ha": float(np.max(de)),
             "held_out_fallbacks": fell_back,
+            "validation_mean_iterations_by_alpha": {str(k): v for k, v in val_iters.items()},
+            "alpha": alpha,
+            "train_max_abs_correction_per_electron": corr_max,
             "held_out_mean_iterations_own_fit_start": float(np.mean(it_c)) if it_c else None}
 
 
@@ -932,6 +969,43 @@ def batched_measure(dev, reps=2):
         cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_FP32, work_seq)
     torch.cuda.synchronize()
     same = all(torch.equal(p, q) for p, q in zip(Y3, Y4))
+    # the mixed precision (split-BF16 tensor-core kernels): concurrent batch against 96
+    # sequential mixed filters
+    nbytes_m = max(cs.cs_workspace_bytes(c, w.n_s, cs.CS_MIXED_BF16) for c, w in zip(ctxs, ws))
+    work_m = torch.empty(nbytes_m, dtype=torch.uint8, device=dev)
+    cs.cs_batch_set_precision(batch, cs.CS_MIXED_BF16)
+    Ym = [X.clone() for X in Xs]
+    cs.cs_batch_cheb_filter(batch, Ym, a, b, a0)  # capture + warm
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cs.cs_batch_cheb_filter(batch, Ym, a, b, a0)
+    e1.record(stream)
+    e1.synchronize()
+    t_bm = e0.elapsed_time(e1) / reps
+    Ys = [X.clone() for X in Xs]
+    for c, y, w, aa, bb, aa0 in zip(ctxs, Ys, ws, a, b, a0):  # warm
+        cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_MIXED_BF16, work_m)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for c, y, w, aa, bb, aa0 in zip(ctxs, Ys, ws, a, b, a0):
+            cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_MIXED_BF16, work_m)
+    e1.record(stream)
+    e1.synchronize()
+    t_sm = e0.elapsed_time(e1) / reps
+    Y5 = [X.clone() for X in Xs]
+    cs.cs_batch_cheb_filter(batch, Y5, a, b, a0)
+    Y6 = [X.clone() for X in Xs]
+    for c, y, w, aa, bb, aa0 in zip(ctxs, Y6, ws, a, b, a0):
+        cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_MIXED_BF16, work_m)
+    torch.cuda.synchronize()
+    same_m = all(torch.equal(p, q) for p, q in zip(Y5, Y6))
+    mixed = {"applies_per_s": round(cols / (t_bm / 1e3), 1),
+             "sequential_applies_per_s": round(cols / (t_sm / 1e3), 1),
+             "speedup_vs_sequential": round(t_sm / t_bm, 3),
+             "filter_ms": round(t_bm, 3), "sequential_filter_ms": round(t_sm, 3),
+             "variant": "concurrent", "bitwise_equal_to_sequential": bool(same_m)}
     return {"workload": "96 erf clusters (4-48 atoms, R 8-16, lmax 12-32, N 24-56, "
                         f"{sum(w.n_s for w in ws)} states in total), FP32 degree-{degree} filter",
             "applies_per_s": round(cols / (t_batch / 1e3), 1),
@@ -941,7 +1015,8 @@ def batched_measure(dev, reps=2):
             "tuned_variant": cs.BATCH_VARIANTS[variant],
             "tune_filter_ms": {k: round(v, 3) for k, v in variant_ms.items()},
             "bitwise_equal_to_sequential": bool(same),
-            "launches_per_filter": launches_per_filter}
+            "launches_per_filter": launches_per_filter,
+            "mixed": mixed}
 
 
 def at_scale_measure(dev, chunk=128):
@@ -1016,9 +1091,10 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
     """ChFSI iterations on the 400-atom cluster with s and p projectors (R = 26, lmax 60, 96
     radial functions, d = 357216, 192 x 120 x 240 grid, 1600 projectors), 880 states, degree
     20: the mixed filter in residual form over chunks of 128 states (19 split-BF16 H.X per
-    state), then Cholesky-QR twice and Rayleigh-Ritz over all 880 states with an FP64 H.X (its
-    projector pair as exact slice products) and the Gram matrices and rotations as exact slice
-    products on the tensor cores (FP64 factorisation, eigensolve and residuals).
+    state), then Cholesky-QR twice and Rayleigh-Ritz over all 880 states with a double-float
+    H.X (FP64-class; its projector pair as exact slice products) and the Gram matrices and
+    rotations as exact slice products on the tensor cores (FP64 factorisation, eigensolve and
+    residuals).
     The block starts random (seeded); one untimed iteration with the first-pass interval
     (Lanczos bounds), then `timed_iters` timed iterations (CUDA events, per-class device
     times). Every call goes through the C ABI."""
@@ -1046,7 +1122,7 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
     del pcoef, xyz
     ctx._ws.clear()
     torch.cuda.empty_cache()
-    cs.cs_set_rr_precision(ctx, cs.CS_FP64)
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
     cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
     gen = torch.Generator(device=dev)
     gen.manual_seed(w.x_seed)
@@ -1151,9 +1227,9 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
                        f"lmax=60, 96 radial fns/l, d={ctx.d}, grid 192x120x240, {n_s} states "
                        f"(filter in chunks of {chunk}), degree {degree}",
            "step": "one ChFSI iteration: residual-form mixed filter (19 split-BF16 H.X per "
-                   "state) + CholQR x2 + Rayleigh-Ritz (FP64 H.X with the projector pair as "
-                   "slice products; Gram matrices and rotations as exact slice products on the "
-                   "tensor cores; FP64 factorisation, eigensolve and residuals)",
+                   "state) + CholQR x2 + Rayleigh-Ritz (double-float H.X with the projector pair "
+                   "as slice products; Gram matrices and rotations as exact slice products on "
+                   "the tensor cores; FP64 factorisation, eigensolve and residuals)",
            "ms_per_iteration": round(ms, 1),
            "iteration_ms": [round(t, 1) for t in times],
            "value": round(applies / (ms / 1e3), 1), "unit": "applies/s",
@@ -1286,8 +1362,8 @@ def main():
                          "(steady state of a ChFSI loop) or the plain recurrence")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-at-scale", action="store_true")
-    ap.add_argument("--at-scale-chfsi", action="store_true",
-                    help="also time ChFSI iterations of the 400-atom cluster (880 states)")
+    ap.add_argument("--no-at-scale-chfsi", action="store_true",
+                    help="skip the ChFSI iterations of the 400-atom cluster (880 states)")
     ap.add_argument("--no-scf", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -80,7 +80,10 @@ typedef enum {
                         floats, about 48 significant bits; Dekker/Knuth error-free
                         transformations). On a GPU whose FP64 pipe runs at 1/64 of the FP32
                         rate this is several times faster than CS_FP64 at relative errors
-                        near 1e-14. Not available with projectors.                       */,
+                        near 1e-14. With projectors it is available for cs_apply_H and the
+                        Rayleigh-Ritz apply only, and only with CS_FP64_SLICED dense
+                        products (the projector term is then formed as exact slice products
+                        and added in double-float); CS_ERR_STATE otherwise.               */,
   CS_FP64_SLICED = 4 /* dense products only (cs_set_dense_precision): FP64 Gram matrices and
                         rotations from exact products of 7-bit integer slices on the tensor
                         cores (Ozaki-Ogita-Oishi-Rump splitting, 8 slices per value, one
@@ -356,11 +359,18 @@ cs_status cs_batch_tune(cs_batch* batch, float* const* X, const long long* ld, c
 
 /* Filter time (ms) of each variant in the last cs_batch_tune (-1 where not timed), for n
  * variants: 0 .. 2 one persistent launch per Chebyshev step with row-pair angular tiles of 4, 8
- * and 2 states; 3 one launch per (stage, tile shape) group of items. */
+ * and 2 states; 3 one launch per (stage, tile shape) group of items; 4 every cluster's filter
+ * as the single-cluster kernels of cs_cheb_filter, the clusters dealt (largest first, to the
+ * least loaded) over 8 parallel branches of the graph, so that small clusters overlap. */
 cs_status cs_batch_tune_times(const cs_batch* batch, float* ms, int n);
 /* Selects a variant (as numbered above) without timing; the next filter call recaptures its
  * graph. CS_ERR_ARG for an unknown variant or one that does not fit in shared memory. */
 cs_status cs_batch_set_variant(cs_batch* batch, int variant);
+/* Precision of the batch: CS_FP32 (default) or CS_MIXED_BF16 (the split-BF16 tensor-core
+ * kernels of cs_cheb_filter's mixed mode; blocks stay float). The mixed precision runs variant
+ * 4 only, and every cluster's result is then bitwise equal to cs_cheb_filter on that cluster
+ * alone in CS_MIXED_BF16. The next filter call recaptures its graph. */
+cs_status cs_batch_set_precision(cs_batch* batch, cs_precision prec);
 const char* cs_batch_last_error(const cs_batch* batch);
 
 /* Device error word of the context (synchronising): 0 if no kernel reported a problem, else

@@ -27,6 +27,7 @@ __all__ = [
     "cs_set_rr_precision", "cs_set_dense_precision", "cs_dense_gram", "cs_dense_rotate",
     "cs_device_error", "Batch", "cs_batch_create", "cs_batch_free", "cs_batch_workspace_bytes",
     "cs_batch_cheb_filter", "cs_batch_tune", "cs_batch_tune_times", "cs_batch_set_variant",
+    "cs_batch_set_precision",
     "cs_batch_last_error",
     "cs_last_error", "cs_launch_count", "library_path", "exported_symbols", "grid_points",
     "cs_measure_peaks",
@@ -132,6 +133,7 @@ _SIGS = {
                                   _vp, _vp]),
     "cs_batch_tune_times": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
     "cs_batch_set_variant": (_i, [_vp, _i]),
+    "cs_batch_set_precision": (_i, [_vp, _i]),
     "cs_batch_tune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_ll), _dp, _dp, _dp, _vp, _vp,
                            ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "cs_batch_last_error": (ctypes.c_char_p, [_vp]),
@@ -619,13 +621,18 @@ def cs_batch_tune(batch: Batch, Xs, a, b, a0, work=None, stream=None):
 
 
 
-BATCH_VARIANTS = ("persistent_rp4", "persistent_rp8", "persistent_rp2", "staged")
+BATCH_VARIANTS = ("persistent_rp4", "persistent_rp8", "persistent_rp2", "staged", "concurrent")
 
 
 def cs_batch_set_variant(batch: Batch, variant):
     """Select a batch variant by index or by name (BATCH_VARIANTS)."""
     v = BATCH_VARIANTS.index(variant) if isinstance(variant, str) else int(variant)
     batch.check(_lib.cs_batch_set_variant(batch.handle, v))
+
+
+def cs_batch_set_precision(batch: Batch, precision: int):
+    """CS_FP32 (default) or CS_MIXED_BF16 (the concurrent variant only)."""
+    batch.check(_lib.cs_batch_set_precision(batch.handle, int(precision)))
 
 
 def cs_batch_tune_times(batch: Batch):

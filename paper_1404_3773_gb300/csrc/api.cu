@@ -222,13 +222,15 @@ cs_status upload_tables(cs_ctx* c) {
 template <typename T>
 cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long long ldo, int mode,
                   double cA, double cB, double csh, const T* Yprev, char* work, cudaStream_t st,
-                  bool tc = false, const T* src = nullptr, const T* src_w = nullptr) {
+                  bool tc = false, const T* src = nullptr, const T* src_w = nullptr,
+                  const T* kb_in = nullptr) {
   const HostTables& H = c->host;
   DevTables<T>& D = tables<T>(c);
   const Layout lay = layout(c, n_s, CS_FP64);
   T* G = reinterpret_cast<T*>(work + lay.G);
-  const T* kb = nullptr;
-  if constexpr (std::is_same<T, df64>::value) {
+  const T* kb = kb_in;  // a projector term the caller formed already (double-float apply)
+  if (kb_in) {
+  } else if constexpr (std::is_same<T, df64>::value) {
     if (c->n_p > 0) return fail(c, CS_ERR_STATE, "CS_DF64 does not apply projectors");
   } else if (c->n_p > 0) {
     // kb = P diag(h) P^T X  (Sec. 2.3.2: a pair of matrix products)
@@ -321,6 +323,13 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
   }
   return CS_OK;
 }
+
+// H X in double-float for an FP64 block X (ld), product widened into HX (ldh); the block is
+// split into `Xd`, the product formed in `Yd` (both d x n_s double-float, ld d). With projectors
+// (only with CS_FP64_SLICED dense products) their term is formed first from the FP64 block as
+// exact slice products, converted to double-float in place and handed to the epilogue.
+cs_status hx_df64_from_fp64(cs_ctx* c, int n_s, const double* X, long long ld, double* HX,
+                            long long ldh, df64* Xd, df64* Yd, char* work, cudaStream_t st);
 
 template <typename T>
 cs_status cheb_core(cs_ctx* c, int n_s, T* X, long long ld, int degree, double a, double b,
@@ -474,10 +483,7 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
     // H X in double-float: block split into tmp, product into HX, widened in place
     df64* Xd = reinterpret_cast<df64*>(work + lay.tmp);
     df64* Yd = reinterpret_cast<df64*>(work + lay.HX);
-    CS_LAUNCH(c, 1, launch_to_df64(X, ld, Xd, H.d, H.d, n_s, st));
-    r = hx_core<df64>(c, n_s, Xd, H.d, Yd, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st);
-    if (r != CS_OK) return r;
-    CS_LAUNCH(c, 1, launch_from_df64(Yd, H.d, HX, H.d, H.d, n_s, st));
+    r = hx_df64_from_fp64(c, n_s, X, ld, HX, H.d, Xd, Yd, work, st);
   } else {
     // H X in the reduced precision (FP32 block in X32, result in tmp), then back to FP64;
     // the projection, eigensolve, rotations and residual norms below stay FP64
@@ -501,6 +507,37 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   const long long ldq = HX_out ? ldho : H.d;
   CS_LAUNCH(c, 1, dense_rotate(c, HX, H.d, Q, n_s, H.d, n_s, n_s, HXq, ldq, st, oz));
   CS_LAUNCH(c, 1, launch_residuals(X, ld, HXq, ldq, H.d, n_s, theta, resid, st));
+  return CS_OK;
+}
+
+cs_status hx_df64_from_fp64(cs_ctx* c, int n_s, const double* X, long long ld, double* HX,
+                            long long ldh, df64* Xd, df64* Yd, char* work, cudaStream_t st) {
+  const HostTables& H = c->host;
+  const Layout lay = layout(c, n_s, CS_FP64);
+  const df64* kb = nullptr;
+  if (c->n_p > 0) {
+    if (c->dense_prec != CS_FP64_SLICED)
+      return fail(c, CS_ERR_STATE,
+                  "CS_DF64 applies projectors only with CS_FP64_SLICED dense products");
+    double* Wkb = reinterpret_cast<double*>(work + lay.Wkb);
+    double* kbZ = reinterpret_cast<double*>(work + lay.kbZ);
+    void* oz = work + lay.oz;
+    CS_LAUNCH_CLS(c, prof_cls<df64>(4), 4,
+                  launch_oz_gram(c->d64.pcoef, H.d, X, ld, H.d, c->n_p, n_s, Wkb, c->n_p, oz,
+                                 c->dev_err, st));
+    CS_LAUNCH_CLS(c, prof_cls<df64>(4), 1,
+                  launch_scale_rows<double>(Wkb, c->n_p, n_s, c->n_p, c->d64.h, st));
+    CS_LAUNCH_CLS(c, prof_cls<df64>(4), 4,
+                  launch_oz_rotate(c->d64.pcoef, H.d, Wkb, c->n_p, H.d, c->n_p, n_s, kbZ, H.d, oz,
+                                   c->dev_err, st));
+    CS_LAUNCH(c, 1, launch_to_df64(kbZ, H.d, reinterpret_cast<df64*>(kbZ), H.d, H.d, n_s, st));
+    kb = reinterpret_cast<const df64*>(kbZ);
+  }
+  CS_LAUNCH(c, 1, launch_to_df64(X, ld, Xd, H.d, H.d, n_s, st));
+  cs_status r = hx_core<df64>(c, n_s, Xd, H.d, Yd, H.d, EP_APPLY, 0, 0, 0, nullptr, work, st,
+                              false, nullptr, nullptr, kb);
+  if (r != CS_OK) return r;
+  CS_LAUNCH(c, 1, launch_from_df64(Yd, H.d, HX, ldh, H.d, n_s, st));
   return CS_OK;
 }
 
@@ -887,16 +924,11 @@ cs_status cs_apply_H(cs_ctx* c, int n_s, const void* X, void* HX, long long ld,
     return hx_core<float>(c, n_s, (const float*)X, ld, (float*)HX, ld, EP_APPLY, 0, 0, 0,
                           nullptr, (char*)work, st, prec == CS_MIXED_BF16);
   if (prec == CS_DF64) {
-    const HostTables& H = c->host;
     const Layout lay = layout(c, n_s, CS_DF64);
     df64* Xd = reinterpret_cast<df64*>((char*)work + lay.tmp);
     df64* Yd = reinterpret_cast<df64*>((char*)work + lay.HX);
-    CS_LAUNCH(c, 1, launch_to_df64((const double*)X, ld, Xd, H.d, H.d, n_s, st));
-    cs_status r = hx_core<df64>(c, n_s, Xd, H.d, Yd, H.d, EP_APPLY, 0, 0, 0, nullptr,
-                                (char*)work, st);
-    if (r != CS_OK) return r;
-    CS_LAUNCH(c, 1, launch_from_df64(Yd, H.d, (double*)HX, ld, H.d, n_s, st));
-    return CS_OK;
+    return hx_df64_from_fp64(c, n_s, (const double*)X, ld, (double*)HX, ld, Xd, Yd,
+                             (char*)work, st);
   }
   return fail(c, CS_ERR_ARG, "unknown precision");
 }

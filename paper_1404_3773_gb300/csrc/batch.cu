@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -200,9 +201,14 @@ int col_tiles(int L, int S) {
 // exactly RC x 32 threads, so every variant here has RC x 32 == kBatchThreads
 // variants 0 .. 2: one persistent launch per step, row-pair tiles of ST states; variant 3
 // (kStaged): one launch per (stage, tile shape) group, row-pair tiles of 4 states
-const int kVariants[][2] = {{4, 8}, {8, 8}, {2, 8}, {4, 8}};
-constexpr int kNumVariants = 4;
+// variant 4 (kConcurrent): every cluster's filter as the single-cluster kernels (those of
+// cs_cheb_filter), the clusters spread over kConcStreams parallel branches of the graph so
+// that the small clusters' kernels overlap; the only variant that runs the mixed precision
+const int kVariants[][2] = {{4, 8}, {8, 8}, {2, 8}, {4, 8}, {4, 8}};
+constexpr int kNumVariants = 5;
 constexpr int kStaged = 3;
+constexpr int kConcurrent = 4;
+constexpr int kConcStreams = 8;
 static_assert(8 * 32 == kBatchThreads, "batch variants assume 8 row pairs per chunk");
 
 // item groups of the staged form: kind 0 radial synthesis, 1 angular (register-blocked),
@@ -212,7 +218,7 @@ struct BGroup {
 };
 
 size_t variant_smem(const std::vector<cs_ctx*>& ctxs, int v) {
-  if (v == kStaged) return 0;  // each staged launch sizes its own shared memory
+  if (v == kStaged || v == kConcurrent) return 0;  // each launch sizes its own shared memory
   size_t m = sizeof(float) * rg_smem_floats<8>();
   for (cs_ctx* c : ctxs) {
     const HostTables& H = c->host;
@@ -251,7 +257,9 @@ struct cs_batch {
   std::vector<BGroup> groups;     // staged launch groups, in launch order
   size_t rp_smem = 0;             // shared memory of the staged row-pair launch
   size_t gm_smem = 0;             // shared memory of the staged register-blocked launch
-  float tune_ms[kNumVariants] = {-1.f, -1.f, -1.f, -1.f};
+  float tune_ms[kNumVariants] = {-1.f, -1.f, -1.f, -1.f, -1.f};
+  bool mixed = false;  // CS_MIXED_BF16 (concurrent variant only)
+  std::vector<cudaStream_t> conc;  // branches of the concurrent variant's capture
   std::string err;
 };
 
@@ -335,6 +343,106 @@ cudaError_t launch_staged_step(cs_batch* b, int step, cudaStream_t st) {
     }
     if (e != cudaSuccess) return e;
   }
+  return e;
+}
+
+// one cluster's filter with the single-cluster kernels (as cs_cheb_filter: step 1 into the
+// alternate block, then alternating, the result copied back after an odd degree)
+cudaError_t launch_cluster_filter(cs_batch* b, int ci, cudaStream_t st) {
+  cs_ctx* c = b->ctxs[ci];
+  const HostTables& H = c->host;
+  const BCluster& bc = b->h_cl[ci];
+  const int S = b->n_s[ci];
+  const float* cf = b->h_coef.data() + (size_t)ci * b->degree * 3;
+  TcTables tt;
+  tt.synth = c->tc_synth;
+  tt.anal = c->tc_anal;
+  tt.rows_synth = c->tc_rows_synth;
+  tt.kpad_synth = c->tc_kpad_synth;
+  tt.rows_anal = c->tc_rows_anal;
+  tt.kpad_anal = c->tc_kpad_anal;
+  const bool tc_rad = b->mixed && tc_radial_fits(H);
+  const bool tc_ang = b->mixed && c->tc_phi && angular_tc_enabled();
+  float* prev = bc.X;
+  long long ldp = bc.ld;
+  float* cur = bc.Yalt;
+  long long ldc = bc.ld_alt;
+  cudaError_t e = cudaSuccess;
+  for (int step = 1; step <= b->degree && e == cudaSuccess; ++step) {
+    // input: X at step 1, else cur; output: Yalt at step 1, else prev (over Y_{i-1})
+    const float* in = step == 1 ? bc.X : cur;
+    const long long ldi = step == 1 ? bc.ld : ldc;
+    float* out = step == 1 ? bc.Yalt : prev;
+    const long long ldo = step == 1 ? bc.ld_alt : ldp;
+    e = tc_rad ? launch_tc_radial_synth(tt, H, in, ldi, bc.G, S, c->dev_err, st)
+               : launch_radial_synth<float>(in, ldi, bc.G, bc.rad, H.L, H.N, H.n_r, S, st);
+    if (e != cudaSuccess) break;
+    e = tc_ang ? launch_angular_tc(bc.ang, c->tc_phi, bc.G, c->dev_err, st)
+               : launch_angular<float>(bc.ang, ANG_FULL, bc.G, nullptr, nullptr, st);
+    if (e != cudaSuccess) break;
+    Epilogue<float> ep;
+    ep.mode = EP_CHEB;
+    ep.out = out;
+    ep.X = in;
+    ep.ld = ldi;
+    ep.ld_out = ldo;
+    ep.Yprev = step == 1 ? nullptr : prev;
+    ep.half_lambda = bc.half_lambda;
+    ep.cA = cf[3 * (step - 1) + 0];
+    ep.cB = cf[3 * (step - 1) + 1];
+    ep.cshift = cf[3 * (step - 1) + 2];
+    e = tc_rad ? launch_tc_radial_anal(tt, H, bc.G, S, ep, c->dev_err, st)
+               : launch_radial_anal<float>(bc.G, bc.rad, H.L, H.N, H.n_r, S, ep, st);
+    if (step > 1) {
+      std::swap(prev, cur);
+      std::swap(ldp, ldc);
+    }
+  }
+  if (e == cudaSuccess && (b->degree & 1))  // the result sits in Yalt
+    e = launch_copy_block<float>(bc.Yalt, bc.ld_alt, bc.X, bc.ld, H.d, S, st);
+  return e;
+}
+
+// the concurrent variant's filter, captured on `cap`: the clusters, largest first, dealt over
+// kConcStreams branches forked from and joined back into the capture stream
+cudaError_t launch_concurrent(cs_batch* b, cudaStream_t cap) {
+  const int nc = (int)b->ctxs.size();
+  if (b->conc.empty()) {
+    for (int k = 0; k < kConcStreams; ++k) {
+      cudaStream_t s;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+        return cudaErrorMemoryAllocation;
+      b->conc.push_back(s);
+    }
+  }
+  std::vector<int> order(nc);
+  for (int i = 0; i < nc; ++i) order[i] = i;
+  auto work = [&](int i) {
+    const HostTables& H = b->ctxs[i]->host;
+    return (double)H.n_r * H.L * H.L * b->n_s[i];
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  cudaEvent_t fork, join[kConcStreams];
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int k = 0; k < kConcStreams && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(fork, cap);
+  for (int k = 0; k < kConcStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->conc[k], fork, 0);
+  // greedy: each cluster to the branch with the least work so far
+  std::vector<double> load(kConcStreams, 0.0);
+  for (int idx = 0; idx < nc && e == cudaSuccess; ++idx) {
+    const int ci = order[idx];
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += work(ci);
+    e = launch_cluster_filter(b, ci, b->conc[k]);
+  }
+  for (int k = 0; k < kConcStreams && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(join[k], b->conc[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join[k], 0);
+  }
+  cudaEventDestroy(fork);
+  for (int k = 0; k < kConcStreams; ++k) cudaEventDestroy(join[k]);
   return e;
 }
 
@@ -438,6 +546,15 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
   // descriptors (caller and workspace pointers)
   std::vector<void*> key;
   key.push_back(work);
+  if (b->variant == kConcurrent) {
+    // that variant's launches carry the coefficients as parameters: new bounds, new graph
+    for (float f : b->h_coef) {
+      uint32_t u;
+      memcpy(&u, &f, sizeof u);
+      key.push_back((void*)(uintptr_t)u);
+    }
+    key.push_back((void*)(uintptr_t)(b->mixed ? 1 : 0));
+  }
   for (int ci = 0; ci < nc; ++ci) {
     if (!X[ci] || ld[ci] < b->ctxs[ci]->host.d) return bfail(b, CS_ERR_ARG, "bad block or ld");
     b->h_cl[ci].X = X[ci];
@@ -460,7 +577,9 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     const size_t ctr_bytes = (1 + 3 * (size_t)nc) * sizeof(int);
-    for (int step = 1; step <= b->degree && e == cudaSuccess; ++step) {
+    if (b->variant == kConcurrent) e = launch_concurrent(b, cap);
+    for (int step = 1; b->variant != kConcurrent && step <= b->degree && e == cudaSuccess;
+         ++step) {
       if (b->variant == kStaged) {
         e = launch_staged_step(b, step, cap);
       } else {
@@ -468,7 +587,7 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
         if (e == cudaSuccess) e = launch_variant_step(b, b->variant, step, cap);
       }
     }
-    if (e == cudaSuccess && (b->degree & 1)) {
+    if (e == cudaSuccess && (b->degree & 1) && b->variant != kConcurrent) {
       dim3 grid(64, nc);
       k_batch_copy_back<<<grid, 256, 0, cap>>>(b->d_cl, nc);
       e = cudaGetLastError();
@@ -483,8 +602,13 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
     b->graph_variant = b->variant;
   }
   if (cudaGraphLaunch(b->graph, st) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "graph launch failed");
-  const int per_step = (b->variant == kStaged) ? (int)b->groups.size() : 1;
-  for (cs_ctx* c : b->ctxs) c->launches += (long long)b->degree * per_step + ((b->degree & 1) ? 1 : 0);
+  if (b->variant == kConcurrent) {
+    for (cs_ctx* c : b->ctxs) c->launches += 3LL * b->degree + ((b->degree & 1) ? 1 : 0);
+  } else {
+    const int per_step = (b->variant == kStaged) ? (int)b->groups.size() : 1;
+    for (cs_ctx* c : b->ctxs)
+      c->launches += (long long)b->degree * per_step + ((b->degree & 1) ? 1 : 0);
+  }
   return CS_OK;
 }
 
@@ -561,6 +685,7 @@ cs_status cs_batch_free(cs_batch* b) {
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaStream_t s : b->conc) cudaStreamDestroy(s);
   if (b->d_cl) cudaFree(b->d_cl);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_coef) cudaFree(b->d_coef);
@@ -610,6 +735,7 @@ cs_status cs_batch_tune(cs_batch* b, float* const* X, const long long* ld, const
   cudaEventCreate(&e1);
   for (int v = 0; v < kNumVariants; ++v) {
     if (variant_smem(b->ctxs, v) > 227 * 1024) continue;
+    if (b->mixed && v != kConcurrent) continue;  // the mixed precision runs concurrently only
     b->variant = v;
     cs_status s = build_items(b, v);
     if (s != CS_OK) return s;
@@ -641,8 +767,25 @@ cs_status cs_batch_tune(cs_batch* b, float* const* X, const long long* ld, const
   return CS_OK;
 }
 
+cs_status cs_batch_set_precision(cs_batch* b, cs_precision prec) {
+  if (!b || (prec != CS_FP32 && prec != CS_MIXED_BF16))
+    return bfail(b, CS_ERR_ARG, "batch precision must be CS_FP32 or CS_MIXED_BF16");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "cudaSetDevice failed");
+  b->mixed = prec == CS_MIXED_BF16;
+  if (b->mixed && b->variant != kConcurrent) {
+    b->variant = kConcurrent;
+    return build_items(b, kConcurrent);
+  }
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_variant = -1;
+  return CS_OK;
+}
+
 cs_status cs_batch_set_variant(cs_batch* b, int variant) {
   if (!b || variant < 0 || variant >= kNumVariants) return bfail(b, CS_ERR_ARG, "bad variant");
+  if (b->mixed && variant != kConcurrent)
+    return bfail(b, CS_ERR_ARG, "the mixed precision runs the concurrent variant only");
   if (variant_smem(b->ctxs, variant) > 227 * 1024)
     return bfail(b, CS_ERR_ARG, "variant does not fit in shared memory");
   if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, CS_ERR_CUDA, "cudaSetDevice failed");

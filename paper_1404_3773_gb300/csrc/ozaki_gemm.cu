@@ -309,22 +309,33 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const int* __restrict__ part,
   }
 }
 
-// E[c] = ceil(log2 max_r |X[r + c ld]|) over r < d (one CTA per column; 0 for zero columns and
-// for c >= n, the padding)
-__global__ void k_oz_colexp(const double* __restrict__ X, long long ld, long long d, int n,
-                            int* __restrict__ E) {
-  const int c = blockIdx.x;
+// max_r |X[r + c ld]| over r < d for every column c < n, as the bits of the FP64 value (for
+// non-negative doubles the order of the bit patterns is the order of the values): grid (row
+// chunks, columns); each CTA reduces its chunk and merges with an atomic maximum into mb[c],
+// which the caller zeroes first
+__global__ void k_oz_colmax(const double* __restrict__ X, long long ld, long long d, int n,
+                            long long rows_per_cta, unsigned long long* __restrict__ mb) {
+  const int c = blockIdx.y;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min(d, r0 + rows_per_cta);
   double m = 0.0;
   if (c < n)
-    for (long long r = threadIdx.x; r < d; r += blockDim.x) m = fmax(m, fabs(X[r + c * ld]));
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) m = fmax(m, fabs(X[r + c * ld]));
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    E[c] = oz_exponent(m);
+    if (m > 0.0) atomicMax(mb + c, (unsigned long long)__double_as_longlong(m));
   }
+}
+
+// E[c] = ceil(log2 max|x|) of column c (0 for zero columns and for the padding)
+__global__ void k_oz_colexp_fin(const unsigned long long* __restrict__ mb, int ncols,
+                                int* __restrict__ E) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncols) E[c] = oz_exponent(__longlong_as_double((long long)mb[c]));
 }
 
 // E[r] = ceil(log2 max_c |X[r + c ld]|) over c < n (one thread per row; 0 past d)
@@ -398,7 +409,7 @@ struct OzPlan {
   long long kpad, mpad, npad;  // K rows (multiple of 32); A-side rows (x128); B-side rows (x32)
   long long wins, groups;
   int wins_per_cta;
-  size_t offEA, offEB, offA, offB, offP, total;
+  size_t offEA, offEB, offMB, offA, offB, offP, total;
 };
 
 OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
@@ -425,6 +436,8 @@ OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
   o += al256((size_t)p.mpad * 4);
   p.offEB = o;
   o += al256((size_t)p.npad * 4);
+  p.offMB = o;  // column maxima (bits), for the larger of the two sides
+  o += al256((size_t)(p.mpad > p.npad ? p.mpad : p.npad) * 8);
   p.offA = o;
   o += al256((size_t)p.kpad * p.mpad * kS * 2);
   p.offB = o;
@@ -471,6 +484,24 @@ cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B,
   return e;
 }
 
+cudaError_t col_exponents(const double* X, long long ld, long long d, int n, int cols_pad,
+                          unsigned long long* mb, int* E, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(mb, 0, (size_t)cols_pad * 8, st);
+  if (e != cudaSuccess) return e;
+  // about 4 CTAs per SM in all, at least 2048 rows each
+  long long chunks = (4 * kSms + n - 1) / (n > 0 ? n : 1);
+  long long rows = (d + chunks - 1) / (chunks > 0 ? chunks : 1);
+  if (rows < 2048) rows = 2048;
+  chunks = (d + rows - 1) / rows;
+  if (chunks < 1) chunks = 1;
+  if (n > 0) {
+    dim3 grid((unsigned)chunks, (unsigned)n);
+    k_oz_colmax<<<grid, 256, 0, st>>>(X, ld, d, n, rows, mb);
+  }
+  k_oz_colexp_fin<<<(cols_pad + 255) / 256, 256, 0, st>>>(mb, cols_pad, E);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t oz_gram_work_bytes(long long d, int na, int nb, bool same) {
@@ -491,12 +522,14 @@ cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long
   int* EB = same ? EA : reinterpret_cast<int*>(w + p.offEB);
   unsigned char* sa = w + p.offA;
   unsigned char* sb = same ? sa : w + p.offB;
-  k_oz_colexp<<<(unsigned)p.mpad, 256, 0, st>>>(A, lda, d, na, EA);
+  unsigned long long* mb = reinterpret_cast<unsigned long long*>(w + p.offMB);
+  cudaError_t e0 = col_exponents(A, lda, d, na, (int)p.mpad, mb, EA, st);
+  if (e0 != cudaSuccess) return e0;
   long long nt = p.mpad * (p.kpad / 8);
   k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, na, EA, p.mpad,
                                                                 p.kpad, sa);
   if (!same) {
-    k_oz_colexp<<<(unsigned)p.npad, 256, 0, st>>>(B, ldb, d, nb, EB);
+    if ((e0 = col_exponents(B, ldb, d, nb, (int)p.npad, mb, EB, st)) != cudaSuccess) return e0;
     nt = p.npad * (p.kpad / 8);
     k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(B, ldb, d, nb, EB, p.npad,
                                                                   p.kpad, sb);
@@ -519,7 +552,10 @@ cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, in
   long long nt = p.mpad * (p.kpad / 8);
   k_oz_split_rows<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, k, EA, p.mpad, p.kpad,
                                                                 sa);
-  k_oz_colexp<<<(unsigned)p.npad, 256, 0, st>>>(Q, ldq, k, n, EB);
+  cudaError_t e0 =
+      col_exponents(Q, ldq, k, n, (int)p.npad, reinterpret_cast<unsigned long long*>(w + p.offMB),
+                    EB, st);
+  if (e0 != cudaSuccess) return e0;
   nt = p.npad * (p.kpad / 8);
   k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(Q, ldq, k, n, EB, p.npad, p.kpad,
                                                                 sb);

@@ -44,12 +44,16 @@ __host__ __device__ inline void oz_decompose(double x, uint64_t& M, int& q) {
 }
 
 __host__ __device__ inline int oz_bit_length(uint64_t v) {
+#ifdef __CUDA_ARCH__
+  return 64 - __clzll((long long)v);
+#else
   int n = 0;
   while (v) {
     ++n;
     v >>= 1;
   }
   return n;
+#endif
 }
 
 // ceil(log2 m) for m = max |x| of a column (m > 0); 0 for m = 0

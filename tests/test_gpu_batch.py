@@ -33,22 +33,29 @@ def _bounds(ctx, cs, torch):
     return tmin + 0.2 * (b - tmin), b, tmin
 
 
-@pytest.mark.parametrize("variant", ["persistent_rp4", "persistent_rp2", "staged"])
-def test_batched_filter_equals_single_cluster_filters(variant):
-    """One persistent launch per step (row-pair tiles of 4 or 2 states) and the staged form
-    (one launch per stage and tile shape): both bitwise equal to the single-cluster filters."""
+@pytest.mark.parametrize("variant,precision", [("persistent_rp4", "fp32"),
+                                               ("persistent_rp2", "fp32"), ("staged", "fp32"),
+                                               ("concurrent", "fp32"), ("concurrent", "mixed")])
+def test_batched_filter_equals_single_cluster_filters(variant, precision):
+    """One persistent launch per step (row-pair tiles of 4 or 2 states), the staged form (one
+    launch per stage and tile shape) and the concurrent form (the single-cluster kernels on
+    parallel graph branches, FP32 and the split-BF16 tensor-core mixed mode): all bitwise
+    equal to the single-cluster filters of the same precision."""
     torch, cs = need_gpu()
     ws = _clusters()
     ctxs = [make_ctx(w) for w in ws]
     degree = 7
+    prec = cs.CS_FP32 if precision == "fp32" else cs.CS_MIXED_BF16
     bounds = [_bounds(c, cs, torch) for c in ctxs]
     Xs = [to_dev(w.x_block(), dtype=torch.float32, ld=c.d + 2) for w, c in zip(ws, ctxs)]
     refs = []
     for X, c, (a, b, a0) in zip(Xs, ctxs, bounds):
         Y = X.clone()
-        cs.cs_cheb_filter(c, Y, degree, a, b, a0, cs.CS_FP32)
+        cs.cs_cheb_filter(c, Y, degree, a, b, a0, prec)
         refs.append(Y)
     batch = cs.cs_batch_create(ctxs, [w.n_s for w in ws], degree)
+    if precision == "mixed":
+        cs.cs_batch_set_precision(batch, cs.CS_MIXED_BF16)
     cs.cs_batch_set_variant(batch, variant)
     a, b, a0 = zip(*bounds)
     Yb = [X.clone() for X in Xs]
@@ -64,9 +71,12 @@ def test_batched_filter_equals_single_cluster_filters(variant):
     torch.cuda.synchronize()
     for X, c, aa, bb, aa0, Y in zip(Xs, ctxs, a2, b, a0, Yb2):
         R = X.clone()
-        cs.cs_cheb_filter(c, R, degree, aa, bb, aa0, cs.CS_FP32)
+        cs.cs_cheb_filter(c, R, degree, aa, bb, aa0, prec)
         torch.cuda.synchronize()
         assert torch.equal(Y, R)
+    if precision == "mixed":
+        with pytest.raises(cs.CsError, match="CS_ERR_ARG"):
+            cs.cs_batch_set_variant(batch, "staged")
 
 
 def test_batched_filter_vs_oracle_and_tuner():

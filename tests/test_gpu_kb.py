@@ -174,3 +174,29 @@ def test_projector_pair_as_slice_products_matches_oracle(case):
     print(f"kb {case} fp64 sliced: fro {fro:.3e} col {col:.3e}")
     assert fro <= 1e-11 and col <= 1e-11, (fro, col)
     assert cs.cs_device_error(ctx) == 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_double_float_apply_with_slice_product_projectors(case):
+    """CS_DF64 H.X with projectors (allowed with CS_FP64_SLICED dense products: the projector
+    term is formed as exact slice products and added in double-float) against the oracle at
+    the FP64 bar; without slice products the call is refused."""
+    torch, cs = need_gpu()
+    w, natoms = CASES[case]
+    atoms = W.place_atoms(w.x_seed + 11, natoms, 0.6 * w.R, 1.0)
+    ctx = make_ctx(w)
+    Hkb = _oracle_with_projectors(w, atoms)
+    X = w.x_block()
+    ref = Hkb.apply(X)
+    _set_library_projectors(torch, cs, ctx, atoms)
+    Xd = to_dev(X, ld=ctx.d + 8)
+    with pytest.raises(cs.CsError, match="CS_ERR_STATE"):
+        cs.cs_apply_H(ctx, Xd, torch.zeros_like(Xd), cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_DF64)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    print(f"kb {case} df64 with sliced projectors: fro {fro:.3e} col {col:.3e}")
+    assert fro <= 1e-11 and col <= 1e-11, (fro, col)
+    assert cs.cs_device_error(ctx) == 0
