@@ -15,16 +15,18 @@
 //   diagonal sums are combined in 128-bit integers and rounded once to FP64. The result is
 //   the exactly rounded value of the truncated slice sum: bit for bit what the oracle computes.
 //
-// Layout of a split operand (both sides): [K step of 16][digit][group of 8 operand rows]
-// [256 B canonical core-matrix pair]: per K step and digit, every operand row's 16 values in
-// the canonical K-major no-swizzle layout, so a tile of R consecutive operand rows is one
-// contiguous run of R / 8 x 256 bytes.
+// Layout of a split operand: [tile of TR operand rows][K step of 16][digit][group of 8 rows of
+// the tile][256 B canonical core-matrix pair] (canonical K-major, no swizzle), TR = 128 for the
+// A side and 32 for the B side, so one pipeline stage of a tile (two K steps, all digits) is
+// one contiguous run: 64 KB (A) and 16 KB (B), two bulk copies per stage.
 //
 // The product kernel: one CTA per (128 rows of the A side) x (32 rows of the B side) x (a
 // group of up to 64 windows of K). Warp 8 issues the bulk copies (two stages of 32 K rows:
-// 80 KB), warp 9 issues the MMAs (36 per K step of 16) into one of two tensor-memory buffers of
-// 8 diagonals x 32 columns, and warps 0-7 drain the other buffer (warps w and w + 4 share a
-// lane quarter and take diagonals 0-3 and 4-7). Every wait is bounded; on expiry the kernel
+// 80 KB), warp 9 issues the MMAs into one of two tensor-memory buffers of 8 diagonals x 32
+// columns, and warps 0-7 drain the other buffer (warps w and w + 4 share a lane quarter and
+// take diagonals 0-3 and 4-7). The digits of the B tile sit one after another in shared
+// memory, so digit k of A times digits 0 .. 7-k of B is one MMA of N = (8 - k) 32 whose
+// columns are the accumulators of diagonals k .. 7: 8 MMAs per K step of 16. Every wait is bounded; on expiry the kernel
 // records an error code in *err, lets its copies and MMAs land (bounded), frees its tensor
 // memory and returns.
 #include <cuda_bf16.h>
@@ -60,8 +62,7 @@ constexpr int kSms = 152;
 struct OzArgs {
   const unsigned char* A;  // split A side
   const unsigned char* B;  // split B side
-  long long a_groups;      // groups of 8 operand rows in A's layout
-  long long b_groups;
+  long long ksteps;        // K steps of 16 in both layouts (K rows / 16, padded)
   long long kchunks;       // K rows / 32 (padded)
   int wins_per_cta;
   // direct: C[i + j ldc] for i < M, j < N;  partial: part[((z 8 + t) Np + j) Mp + i]
@@ -131,22 +132,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
       }
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, kStageBytes);
-      for (int ks = 0; ks < 2; ++ks) {
-        const long long kstep = (c0 + i) * 2 + ks;
-        for (int d = 0; d < kS; ++d) {
-          const unsigned char* a =
-              g.A + ((kstep * kS + d) * g.a_groups + mt * (kTM / 8)) * 256;
-          const unsigned char* b =
-              g.B + ((kstep * kS + d) * g.b_groups + (long long)nt * (kTN / 8)) * 256;
-          bulk_g2s(sA(s) + (ks * kS + d) * kAStep, a, kAStep, fb);
-          bulk_g2s(sB(s) + (ks * kS + d) * kBStep, b, kBStep, fb);
-        }
-      }
+      const long long kstep = (c0 + i) * 2;
+      const unsigned char* a = g.A + ((mt * g.ksteps + kstep) * kS) * (size_t)kAStep;
+      const unsigned char* b = g.B + (((long long)nt * g.ksteps + kstep) * kS) * (size_t)kBStep;
+      bulk_g2s(sA(s), a, 2 * kS * kAStep, fb);
+      bulk_g2s(sB(s), b, 2 * kS * kBStep, fb);
     }
     issued_sh = i;
   } else if (warp == kDrainWarps + 1 && lane == 0) {
-    // MMA issuer: 36 MMAs per K step, pair (k, l) into the accumulator of diagonal k + l
-    constexpr uint32_t idesc = make_idesc(kTM, kTN);
+    // MMA issuer: per K step, digit k of A times digits 0 .. 7-k of B (N = (8 - k) 32) into
+    // the accumulators of diagonals k .. 7
     int i = 0;
     for (; i < nk; ++i) {
       const int s = i & 1;
@@ -166,16 +161,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
       const uint32_t dbase = tmem + (uint32_t)(buf * kS * kTN);
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t bd = make_desc(sB(s) + ks * kS * kBStep, 128, 256);
 #pragma unroll
-        for (int t = 0; t < kS; ++t) {
-#pragma unroll
-          for (int k = 0; k <= t; ++k) {
-            const int l = t - k;
-            const uint64_t ad = make_desc(sA(s) + (ks * kS + k) * kAStep, 128, 256);
-            const uint64_t bd = make_desc(sB(s) + (ks * kS + l) * kBStep, 128, 256);
-            const uint32_t accum = (!first || ks > 0 || k > 0) ? 1u : 0u;
-            mma_bf16(dbase + (uint32_t)(t * kTN), ad, bd, idesc, accum);
-          }
+        for (int k = 0; k < kS; ++k) {
+          const uint64_t ad = make_desc(sA(s) + (ks * kS + k) * kAStep, 128, 256);
+          const uint32_t idesc = make_idesc(kTM, (kS - k) * kTN);
+          // k = 0 covers every diagonal: it starts each window's accumulators
+          const uint32_t accum = (!first || ks > 0 || k > 0) ? 1u : 0u;
+          mma_bf16(dbase + (uint32_t)(k * kTN), ad, bd, idesc, accum);
         }
       }
       mma_commit(smem_u32(&empty[s]));
@@ -238,34 +231,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
     }
   }
   if (g.direct) {
-    // warps 4-7 hand diagonals 4-7 to warps 0-3 through shared memory (the stages are idle)
-    int* stash = reinterpret_cast<int*>(smem);  // [4][kTN][kTM]
-    if (drain_ok && warp >= 4 && warp < kDrainWarps) {
-      const int r = (warp & 3) * 32 + lane;
+    // every drain warp combines half of its rows' columns: warps 0-3 (diagonals 0-3) take
+    // columns 0-15 and hand diagonals 0-3 of columns 16-31 to warps 4-7, which hand back
+    // diagonals 4-7 of columns 0-15 (through shared memory; the stages are idle now)
+    constexpr int H = kTN / 2;
+    int* lo_part = reinterpret_cast<int*>(smem);   // [4][H][kTM]: diagonals 0-3, columns H..
+    int* hi_part = lo_part + 4 * H * kTM;          // [4][H][kTM]: diagonals 4-7, columns 0..
+    const int r = (warp & 3) * 32 + lane;
+    if (drain_ok && warp < kDrainWarps) {
+      if (warp < 4) {
 #pragma unroll
-      for (int tt = 0; tt < 4; ++tt)
+        for (int tt = 0; tt < 4; ++tt)
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) stash[(tt * kTN + c) * kTM + r] = acc[tt][c];
+          for (int c = 0; c < H; ++c) lo_part[(tt * H + c) * kTM + r] = acc[tt][H + c];
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt)
+#pragma unroll
+          for (int c = 0; c < H; ++c) hi_part[(tt * H + c) * kTM + r] = acc[tt][c];
+      }
     }
     __syncthreads();
-    if (drain_ok && warp < 4) {
-      const int r = warp * 32 + lane;
-      const long long i = mt * kTM + r;
-      if (i < g.M) {
-        const int ea = g.EA[i];
-        // fully unrolled, so that acc stays in registers
+    const long long i = mt * kTM + r;
+    if (drain_ok && warp < kDrainWarps && i < g.M) {
+      const int ea = g.EA[i];
+      const bool low = warp < 4;
+      // fully unrolled, so that acc stays in registers
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) {
-          const long long j = (long long)nt * kTN + c;
-          if (j < g.N) {
-            int64_t D[kS];
+      for (int c = 0; c < H; ++c) {
+        const long long j = (long long)nt * kTN + (low ? c : H + c);
+        if (j < g.N) {
+          int64_t D[kS];
 #pragma unroll
-            for (int tt = 0; tt < 4; ++tt) {
-              D[tt] = acc[tt][c];
-              D[4 + tt] = stash[(tt * kTN + c) * kTM + r];
-            }
-            g.C[i + j * g.ldc] = oz_combine(D, ea, g.EB[j], kBeta, kS);
+          for (int tt = 0; tt < 4; ++tt) {
+            D[tt] = low ? acc[tt][c] : lo_part[(tt * H + c) * kTM + r];
+            D[4 + tt] = low ? hi_part[(tt * H + c) * kTM + r] : acc[tt][H + c];
           }
+          g.C[i + j * g.ldc] = oz_combine(D, ea, g.EB[j], kBeta, kS);
         }
       }
     }
@@ -349,26 +351,30 @@ __global__ void k_oz_rowexp(const double* __restrict__ X, long long ld, long lon
   E[r] = oz_exponent(m);
 }
 
-__device__ __forceinline__ void oz_store_digits(unsigned char* out, long long kstep, int kh,
-                                                long long groups, long long row,
+// the 8 digits of one operand row's octet of K values into the layout with tiles of TR rows
+__device__ __forceinline__ void oz_store_digits(unsigned char* out, int TR, long long ksteps,
+                                                long long kstep, int kh, long long row,
                                                 const int (*dig)[kS]) {
   // dig[i][k]: digit k of the operand row's K value i of this octet
+  const long long tile = row / TR, rt = row - tile * TR;
 #pragma unroll
   for (int k = 0; k < kS; ++k) {
     __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn((float)dig[i][k]);
-    const size_t off = ((size_t)(kstep * kS + k) * groups + (row >> 3)) * 256 + kh * 128 +
-                       (row & 7) * 16;
+    const size_t off = (((size_t)(tile * ksteps + kstep) * kS + k) * (TR / 8) + (rt >> 3)) * 256 +
+                       kh * 128 + (rt & 7) * 16;
     *reinterpret_cast<uint4*>(out + off) = *reinterpret_cast<const uint4*>(h);
   }
 }
 
 // Operand rows = columns c of X (d x n, ld), K = rows r (Gram side; one exponent per column).
-// One thread per (column, octet of 8 rows); consecutive threads take consecutive columns.
+// One thread per (column, octet of 8 rows); consecutive threads take consecutive columns. The
+// digits go to `out` in tiles of TR rows and, if out2 is not null, to out2 in tiles of TR2.
 __global__ void k_oz_split_cols(const double* __restrict__ X, long long ld, long long d, int n,
                                 const int* __restrict__ E, long long cols_pad, long long kpad,
-                                unsigned char* __restrict__ out) {
+                                unsigned char* __restrict__ out, int TR,
+                                unsigned char* __restrict__ out2, int TR2, long long cols2) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cols_pad * (kpad / 8)) return;
   const long long c = t % cols_pad, oct = t / cols_pad;
@@ -380,14 +386,15 @@ __global__ void k_oz_split_cols(const double* __restrict__ X, long long ld, long
     const double x = (c < n && r < d) ? X[r + c * ld] : 0.0;
     oz_slices(x, e, kBeta, kS, dig[i]);
   }
-  oz_store_digits(out, oct >> 1, (int)(oct & 1), cols_pad / 8, c, dig);
+  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), c, dig);
+  if (out2 && c < cols2) oz_store_digits(out2, TR2, kpad / 16, oct >> 1, (int)(oct & 1), c, dig);
 }
 
 // Operand rows = rows r of X (d x n, ld), K = columns c (rotation side; one exponent per row).
 // One thread per (row, octet of 8 columns); consecutive threads take consecutive rows.
 __global__ void k_oz_split_rows(const double* __restrict__ X, long long ld, long long d, int n,
                                 const int* __restrict__ E, long long rows_pad, long long kpad,
-                                unsigned char* __restrict__ out) {
+                                unsigned char* __restrict__ out, int TR) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows_pad * (kpad / 8)) return;
   const long long r = t % rows_pad, oct = t / rows_pad;
@@ -399,7 +406,7 @@ __global__ void k_oz_split_rows(const double* __restrict__ X, long long ld, long
     const double x = (r < d && c < n) ? X[r + c * ld] : 0.0;
     oz_slices(x, e, kBeta, kS, dig[i]);
   }
-  oz_store_digits(out, oct >> 1, (int)(oct & 1), rows_pad / 8, r, dig);
+  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), r, dig);
 }
 
 long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -417,7 +424,6 @@ OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
   p.kpad = rup(K, kKC);
   p.mpad = rup(M, kTM);
   p.npad = rup(N, kTN);
-  if (same) p.npad = p.mpad;  // one split serves both sides
   p.wins = (p.kpad + kWin - 1) / kWin;
   const long long tiles = (p.mpad / kTM) * (p.npad / kTN);
   long long groups = 1;
@@ -440,8 +446,8 @@ OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
   o += al256((size_t)(p.mpad > p.npad ? p.mpad : p.npad) * 8);
   p.offA = o;
   o += al256((size_t)p.kpad * p.mpad * kS * 2);
-  p.offB = o;
-  o += same ? 0 : al256((size_t)p.kpad * p.npad * kS * 2);
+  p.offB = o;  // the B side in tiles of 32 rows (also when A and B are one block)
+  o += al256((size_t)p.kpad * p.npad * kS * 2);
   p.offP = o;
   o += p.groups > 1 ? al256((size_t)p.groups * kS * p.mpad * p.npad * 4) : 0;
   p.total = o;
@@ -457,8 +463,7 @@ cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B,
   OzArgs g{};
   g.A = A;
   g.B = B;
-  g.a_groups = p.mpad / 8;
-  g.b_groups = p.npad / 8;
+  g.ksteps = p.kpad / 16;
   g.kchunks = p.kpad / kKC;
   g.wins_per_cta = p.wins_per_cta;
   g.direct = p.groups == 1;
@@ -521,18 +526,19 @@ cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long
   int* EA = reinterpret_cast<int*>(w + p.offEA);
   int* EB = same ? EA : reinterpret_cast<int*>(w + p.offEB);
   unsigned char* sa = w + p.offA;
-  unsigned char* sb = same ? sa : w + p.offB;
+  unsigned char* sb = w + p.offB;
   unsigned long long* mb = reinterpret_cast<unsigned long long*>(w + p.offMB);
   cudaError_t e0 = col_exponents(A, lda, d, na, (int)p.mpad, mb, EA, st);
   if (e0 != cudaSuccess) return e0;
   long long nt = p.mpad * (p.kpad / 8);
-  k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, na, EA, p.mpad,
-                                                                p.kpad, sa);
+  // one split; with A and B one block it writes both layouts (tiles of 128 and of 32 rows)
+  k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+      A, lda, d, na, EA, p.mpad, p.kpad, sa, kTM, same ? sb : nullptr, kTN, p.npad);
   if (!same) {
     if ((e0 = col_exponents(B, ldb, d, nb, (int)p.npad, mb, EB, st)) != cudaSuccess) return e0;
     nt = p.npad * (p.kpad / 8);
     k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(B, ldb, d, nb, EB, p.npad,
-                                                                  p.kpad, sb);
+                                                                  p.kpad, sb, kTN, nullptr, kTN, 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -551,14 +557,14 @@ cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, in
   k_oz_rowexp<<<(unsigned)((p.mpad + 255) / 256), 256, 0, st>>>(A, lda, d, k, p.mpad, EA);
   long long nt = p.mpad * (p.kpad / 8);
   k_oz_split_rows<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A, lda, d, k, EA, p.mpad, p.kpad,
-                                                                sa);
+                                                                sa, kTM);
   cudaError_t e0 =
       col_exponents(Q, ldq, k, n, (int)p.npad, reinterpret_cast<unsigned long long*>(w + p.offMB),
                     EB, st);
   if (e0 != cudaSuccess) return e0;
   nt = p.npad * (p.kpad / 8);
   k_oz_split_cols<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(Q, ldq, k, n, EB, p.npad, p.kpad,
-                                                                sb);
+                                                                sb, kTN, nullptr, kTN, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return run(p, sa, sb, EA, EB, d, n, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st);
