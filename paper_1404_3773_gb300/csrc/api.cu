@@ -25,7 +25,7 @@ thread_local std::string g_init_error;
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, oz, kbtc, total;
+  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, oz, kbtc, wa, total;
 };
 
 constexpr int kMaxLanczos = 64;
@@ -80,6 +80,11 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
   o.X32 = take(reduced ? d * ns * 4 : 0);
   // scratch of the tensor-core projector products (mixed precision with projectors)
   o.kbtc = take(mixed && np ? kb_tc_work_bytes(kb_tc_shape(T.d, (int)np, n_s)) : 0);
+  // FP32 intermediate of the three-pass tensor-core angular block (sized whenever the block
+  // is eligible, so that the choice of angular kernel never changes the workspace size)
+  o.wa = take(mixed && angular_wide_eligible(T.L, T.n_theta, T.n_phi)
+                  ? angular_wide_work_bytes(T.L, T.n_r, T.n_theta, n_s)
+                  : 0);
   o.total = off;
   return o;
 }
@@ -291,7 +296,14 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
                D.theta_pairs};
   bool ang_done = false;
   if constexpr (std::is_same<T, float>::value) {
-    if (tc && c->tc_phi && angular_tc_enabled()) {
+    if (tc && c->wide_tab &&
+        angular_wide_enabled(H.L, H.n_theta, H.n_phi, c->tc_phi != nullptr)) {
+      const Layout lw = layout(c, n_s, CS_MIXED_BF16);
+      CS_LAUNCH_CLS(c, prof_cls<T>(1), 3,
+                    launch_angular_wide(a, c->wide_tab, G, reinterpret_cast<float*>(work + lw.wa),
+                                        c->dev_err, st));
+      ang_done = true;
+    } else if (tc && c->tc_phi && angular_tc_enabled()) {
       CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular_tc(a, c->tc_phi, G, c->dev_err, st));
       ang_done = true;
     }
@@ -666,6 +678,14 @@ cs_status cs_basis_init(double R, int lmax, int nmax, const cs_quadrature* q, in
                 cudaSuccess)
           st = CS_ERR_ALLOC;
       }
+      if (st == CS_OK && angular_wide_eligible(c->host.L, c->host.n_theta, c->host.n_phi)) {
+        std::vector<uint16_t> tab;
+        build_wide_tables(c->host, tab);
+        if (cudaMalloc(&c->wide_tab, tab.size() * 2) != cudaSuccess ||
+            cudaMemcpy(c->wide_tab, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+          st = CS_ERR_ALLOC;
+      }
       if (st == CS_OK && (cudaMalloc((void**)&c->dev_err, sizeof(int)) != cudaSuccess ||
                           cudaMemset(c->dev_err, 0, sizeof(int)) != cudaSuccess))
         st = CS_ERR_ALLOC;
@@ -729,6 +749,7 @@ cs_status cs_basis_free(cs_ctx* c) {
     if (c->tc_synth) cudaFree(c->tc_synth);
     if (c->tc_anal) cudaFree(c->tc_anal);
     if (c->tc_phi) cudaFree(c->tc_phi);
+    if (c->wide_tab) cudaFree(c->wide_tab);
     if (c->kb_tabA) cudaFree(c->kb_tabA);
     if (c->kb_tabB) cudaFree(c->kb_tabB);
     if (c->dev_err) cudaFree(c->dev_err);

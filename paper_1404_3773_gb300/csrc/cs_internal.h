@@ -75,6 +75,7 @@ struct cs_ctx {
   void* tc_synth = nullptr;  // split-BF16 radial tables (tensor-core path)
   void* tc_anal = nullptr;
   void* tc_phi = nullptr;    // split-BF16 phi operands of the tensor-core angular kernel
+  void* wide_tab = nullptr;  // split-BF16 Legendre and folded-trig operands of the wide block
   int tc_rows_synth = 0, tc_kpad_synth = 0, tc_rows_anal = 0, tc_kpad_anal = 0;
   void* kb_tabA = nullptr;   // split-BF16 projector operands (kb_tc.cu), set with the projectors
   void* kb_tabB = nullptr;

@@ -102,6 +102,18 @@ void build_tc_phi_table(int L, int n_phi, std::vector<uint16_t>& out);
 cudaError_t launch_angular_tc(const AngArgs<float>& a, const void* tphi, float* G, int* err,
                               cudaStream_t stream);
 
+// three-pass tensor-core angular block for large lmax (angular_wide.cu): Legendre sums per m,
+// folded phi transforms per grid row and Legendre quadrature per m, all split BF16 on tcgen05,
+// through the FP32 intermediate FA (angular_wide_work_bytes); needs n_phi a multiple of 4
+bool angular_wide_eligible(int L, int n_theta, int n_phi);
+// the wide block is taken when eligible and the fused block is not, or when CS_ANGULAR_KERNEL
+// starts with 'w'; any other non-empty CS_ANGULAR_KERNEL keeps it off
+bool angular_wide_enabled(int L, int n_theta, int n_phi, bool fused_eligible);
+size_t angular_wide_work_bytes(int L, int n_r, int n_theta, int S);
+void build_wide_tables(const HostTables& H, std::vector<uint16_t>& out);
+cudaError_t launch_angular_wide(const AngArgs<float>& a, const void* tab, float* G, float* FA,
+                                int* err, cudaStream_t stream);
+
 // ---------------------------------------------------------------- dense FP64 pieces
 // C (na x nb, column-major, ldc) = A^T B, A: d x na (lda), B: d x nb (ldb), split over d
 // into chunks whose partial products land in `partial` (gram_partial_elems doubles) and

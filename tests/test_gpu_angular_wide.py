@@ -1,0 +1,105 @@
+"""The three-pass tensor-core angular block of the mixed filter (per-m Legendre products,
+folded phi transforms per grid row, per-m Legendre quadrature, all split BF16 on tcgen05):
+H.X against the FP64 oracle, against the fused tensor-core block where both apply, state
+blocks of 128 with a ragged last block, odd theta counts, and the 400-atom cluster's angular
+size (lmax 60, 120 x 240).
+
+Bars: 3x the errors measured on a GB300 (both blocks are deterministic)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import make_ctx, need_gpu, oracle_H, register, rel_errors, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # lmax 60 at the 400-atom cluster's angular size, thin radial grid: the wide block is the
+    # default there (the fused block stops at lmax 31)
+    "l60_t120_p240": W.small_cluster(lmax=60, nmax=4, n_r=6, n_theta=120, n_phi=240, R=10.0,
+                                     n_s=5, natoms=4, seed=7601),
+    # odd theta count (a self-mirror row), 130 states: two blocks, the second of 2 states
+    "l9_t13_p24_s130": W.small_cluster(lmax=9, nmax=6, n_r=10, n_theta=13, n_phi=24, n_s=130,
+                                       seed=9101),
+    # lmax 40, 16 states, n_phi = 4 (Q + 1) - 4 with Q = 21: padded quarter angles
+    "l40_t41_p84": W.small_cluster(lmax=40, nmax=5, n_r=8, n_theta=41, n_phi=84, R=9.0,
+                                   n_s=16, natoms=3, seed=9111),
+    # the fused block's own territory, forced onto the wide block
+    "l6_t14_p28": W.small_cluster(lmax=6, nmax=8, n_r=20, n_theta=14, n_phi=28, n_s=13),
+    # the smallest shapes: lmax 1, one theta pair, 8 angles, one state
+    "l1_t2_p8_s1": W.small_cluster(lmax=1, nmax=5, n_r=8, n_theta=2, n_phi=8, n_s=1,
+                                   seed=9121),
+}
+# measured: l60 1.37e-6 / 9.8e-8, l9 s130 1.10e-5 / 4.2e-6, l40 1.80e-6 / 1.9e-7, l6 9.5e-6 /
+# 2.9e-6, l1 1.36e-5 / 7.1e-6
+BARS = {"l60_t120_p240": (4.1e-6, 2.9e-7), "l9_t13_p24_s130": (3.3e-5, 1.3e-5),
+        "l40_t41_p84": (5.4e-6, 5.6e-7), "l6_t14_p28": (2.8e-5, 8.6e-6),
+        "l1_t2_p8_s1": (4.1e-5, 2.1e-5)}
+for _w in CASES.values():
+    register(_w)
+
+
+def _mixed_apply(torch, cs, ctx, Xd):
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_MIXED_BF16)
+    torch.cuda.synchronize()
+    return HXd
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_wide_angular_block_matches_oracle(case, monkeypatch):
+    torch, cs = need_gpu()
+    monkeypatch.setenv("CS_ANGULAR_KERNEL", "wide")
+    w = CASES[case]
+    ctx = make_ctx(w)
+    Xd = to_dev(w.x_block(), dtype=torch.float32, ld=ctx.d + 4)
+    ref = oracle_H(w.name).apply(to_host(Xd, ctx.d))
+    n0 = cs.cs_launch_count(ctx)
+    HXd = _mixed_apply(torch, cs, ctx, Xd)
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    print(f"wide angular {case}: fro {fro:.3e} col {col:.3e}")
+    bf, bc = BARS[case]
+    assert fro <= bf and col <= bc, (fro, col)
+    assert torch.all(HXd[:, ctx.d:] == 0)
+    assert cs.cs_device_error(ctx) == 0
+    # radial synthesis, three angular passes, radial analysis
+    assert cs.cs_launch_count(ctx) - n0 == 5
+    # deterministic: a second call gives the same bits
+    assert torch.equal(_mixed_apply(torch, cs, ctx, Xd), HXd)
+
+
+@pytest.mark.parametrize("case", ["l6_t14_p28", "l9_t13_p24_s130"])
+def test_wide_and_fused_blocks_agree(case, monkeypatch):
+    """Where both tensor-core blocks apply they differ only by the split-BF16 rounding of the
+    Legendre sums (FP32 in the fused block): close, and not identical."""
+    torch, cs = need_gpu()
+    w = CASES[case]
+    ctx = make_ctx(w)
+    Xd = to_dev(w.x_block(), dtype=torch.float32)
+    out = {}
+    for kern in ("wide", "tc"):
+        monkeypatch.setenv("CS_ANGULAR_KERNEL", kern)
+        out[kern] = to_host(_mixed_apply(torch, cs, ctx, Xd), ctx.d)
+    fro, _ = rel_errors(out["wide"], out["tc"])
+    print(f"wide vs fused {case}: {fro:.3e}")
+    assert 0 < fro <= 3e-5, fro  # measured 7.2e-6 (l6) and 9.0e-6 (l9, 130 states)
+    assert cs.cs_device_error(ctx) == 0
+
+
+def test_wide_block_is_default_above_fused_limit(monkeypatch):
+    """Without CS_ANGULAR_KERNEL, lmax 60 takes the wide block (three angular launches);
+    CS_ANGULAR_KERNEL=simt takes the FP32 kernel (one launch) and agrees to the mixed level."""
+    torch, cs = need_gpu()
+    monkeypatch.delenv("CS_ANGULAR_KERNEL", raising=False)
+    w = CASES["l60_t120_p240"]
+    ctx = make_ctx(w)
+    Xd = to_dev(w.x_block(), dtype=torch.float32)
+    n0 = cs.cs_launch_count(ctx)
+    a = to_host(_mixed_apply(torch, cs, ctx, Xd), ctx.d)
+    assert cs.cs_launch_count(ctx) - n0 == 5
+    monkeypatch.setenv("CS_ANGULAR_KERNEL", "simt")
+    n0 = cs.cs_launch_count(ctx)
+    b = to_host(_mixed_apply(torch, cs, ctx, Xd), ctx.d)
+    assert cs.cs_launch_count(ctx) - n0 == 3
+    fro, _ = rel_errors(a, b)
+    assert fro <= 5e-5, fro
