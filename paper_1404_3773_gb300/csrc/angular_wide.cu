@@ -43,6 +43,7 @@ namespace {
 using namespace tcx;
 
 constexpr int kWaThreads = 256;
+constexpr int kPThreads = 512;  // the phi pass
 constexpr int kWaRows = 128;  // MMA M: the states of one block
 constexpr int kSmemPerSM = 228 * 1024;
 
@@ -97,6 +98,8 @@ __host__ __device__ inline size_t l1_smem(const WaShape& s) {
 __host__ __device__ inline size_t l2_smem(const WaShape& s) {
   return (size_t)2 * 2 * kWaRows * s.NPp * 2 + (size_t)s.leg_per_a;
 }
+// quarter angles per quadrature pass of the phi kernel
+__host__ __device__ inline int p_qh(int QP) { return (QP % 32 == 0) ? 32 : 16; }
 struct PSmem {
   size_t f, a, tab, wv, total;
 };
@@ -105,9 +108,9 @@ __host__ __device__ inline PSmem p_smem(const WaShape& s, int SW) {
   size_t o = 0;
   p.tab = o;  // trig tables first (one bulk copy at the start)
   o += s.phi_bytes;
-  p.a = o;    // F operand (4 classes) / h operand (2 classes)
+  p.a = o;    // F operand / folded grid-value operand (4 classes each)
   size_t ab = (size_t)4 * 2 * kWaRows * s.KC * 2;
-  const size_t hb = (size_t)2 * 2 * kWaRows * s.QP * 2;
+  const size_t hb = (size_t)4 * 2 * kWaRows * p_qh(s.QP) * 2;
   if (hb > ab) ab = hb;
   o += ab;
   p.f = o;    // the row's F, [M2][SW] floats
@@ -154,6 +157,9 @@ struct WaArgs {
 __device__ __forceinline__ void record(int* err, int code) { atomicCAS(err, 0, code); }
 
 // ------------------------------------------------------------------------------------ L1
+// NT: operand tasks (8 values each) per thread and mode, an upper bound on KL / 8. The next
+// mode's G values are loaded into registers while this mode's MMAs and stores run.
+template <int NT>
 __global__ void __launch_bounds__(kWaThreads)
     k_leg_synth_tc(WaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -172,6 +178,7 @@ __global__ void __launch_bounds__(kWaThreads)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t bar_tab = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
   const uint32_t tcols = pow2_cols(2 * NPp);
+  const int ntask = kWaRows * 2 * (KL / 8);
   if (tid == 0) {
     mbar_init(bar_tab, 1);
     mbar_init(bar_mma, 1);
@@ -183,6 +190,25 @@ __global__ void __launch_bounds__(kWaThreads)
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
   const uint32_t idesc = make_idesc(kWaRows, NPp);
+  // A[par][s][i] = G[k][l = am + par + 2i, m][s0 + s] (zero past lmax and past the states)
+  float gx[NT][8];
+  auto load = [&](int it) {
+    const int m = item_m(it), am = m < 0 ? -m : m;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int task = tid + u * kWaThreads;
+      const int s = task & (kWaRows - 1), rest = task >> 7;
+      const int par = rest & 1, ig = rest >> 1;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int l = am + par + 2 * (8 * ig + j);
+        gx[u][j] = (task < ntask && l <= lmax && s < ns)
+                       ? a.G[((size_t)k * L2 + l * l + l + m) * S + s0 + s]
+                       : 0.f;
+      }
+    }
+  };
+  if (it0 < it1) load(it0);
   uint32_t ph_tab = 0, ph_mma = 0;
   int cur_a = -1;
   bool ok = true;
@@ -194,20 +220,17 @@ __global__ void __launch_bounds__(kWaThreads)
       bulk_g2s(smem_u32(sB), a.tab + (size_t)am * sh.leg_per_a, (uint32_t)sh.leg_per_a, bar_tab);
     }
     cur_a = am;
-    // A[par][s][i] = G[k][l = am + par + 2i, m][s0 + s] (zero past lmax and past the states)
-    const int ntask = kWaRows * 2 * (KL / 8);
-    for (int task = tid; task < ntask; task += kWaThreads) {
-      const int s = task & (kWaRows - 1), rest = task >> 7;
-      const int par = rest & 1, ig = rest >> 1;
-      float x[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int l = am + par + 2 * (8 * ig + j);
-        x[j] = (l <= lmax && s < ns) ? a.G[((size_t)k * L2 + l * l + l + m) * S + s0 + s] : 0.f;
+    for (int u = 0; u < NT; ++u) {
+      const int task = tid + u * kWaThreads;
+      if (task < ntask) {
+        const int s = task & (kWaRows - 1), rest = task >> 7;
+        const int par = rest & 1, ig = rest >> 1;
+        unsigned char* hi = sA + (size_t)par * 2 * aplane;
+        store_split8(hi, hi + aplane, s, 8 * ig, kWaRows, gx[u]);
       }
-      unsigned char* hi = sA + (size_t)par * 2 * aplane;
-      store_split8(hi, hi + aplane, s, 8 * ig, kWaRows, x);
     }
+    if (it + 1 < it1) load(it + 1);
     fence_async_smem();
     tc_fence_before();
     bool t_ok = true;
@@ -241,8 +264,8 @@ __global__ void __launch_bounds__(kWaThreads)
     ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
     if (!ok) break;
     tc_fence_after();
-    // F(t) = E + O, F(mirror t) = E - O for this warp's lane quarter (states) and half of
-    // the pairs
+    // F(t) = E + O, F(mirror t) = E - O for this warp's lane quarter (states), every other
+    // 16 pairs
     {
       const int qd = warp & 3, hh = warp >> 2, s = 32 * qd + lane;
       float* base = a.FA + (((size_t)blk * a.n_r + k) * Nt) * (size_t)M2 * SW;
@@ -272,7 +295,11 @@ __global__ void __launch_bounds__(kWaThreads)
 }
 
 // ------------------------------------------------------------------------------------ L2
-__global__ void __launch_bounds__(kWaThreads)
+// 512 threads. NT: operand tasks (8 pairs each) per thread and mode, an upper bound on NPp / 32;
+// the next
+// mode's AP values are loaded into registers while this mode's MMAs and stores run.
+template <int NT>
+__global__ void __launch_bounds__(kPThreads, 1)
     k_leg_anal_tc(WaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
@@ -290,6 +317,7 @@ __global__ void __launch_bounds__(kWaThreads)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t bar_tab = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
   const uint32_t tcols = pow2_cols(2 * KL);
+  const int ntask = kWaRows * (NPp / 8);
   if (tid == 0) {
     mbar_init(bar_tab, 1);
     mbar_init(bar_mma, 1);
@@ -302,11 +330,30 @@ __global__ void __launch_bounds__(kWaThreads)
   const uint32_t tmem = tmem_sh;
   const uint32_t idesc = make_idesc(kWaRows, KL);
   const float* base = a.FA + (((size_t)blk * a.n_r + k) * Nt) * (size_t)M2 * SW;
+  // AP(t) and AP(mirror t) of the task's 8 pairs (the self-mirror row of an odd n_theta has
+  // no mirror: its second value stays zero and it enters the even part only)
+  float xv[NT][8], yv[NT][8];
+  auto load = [&](int it) {
+    const int kap = item_m(it) + lmax;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int task = tid + u * kPThreads;
+      const int s = task & (kWaRows - 1), tg = task >> 7;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int t = 8 * tg + j, tb = Nt - 1 - t;
+        const bool in = task < ntask && t < NP && s < SW;
+        xv[u][j] = in ? base[((size_t)t * M2 + kap) * SW + s] : 0.f;
+        yv[u][j] = (in && tb != t) ? base[((size_t)tb * M2 + kap) * SW + s] : 0.f;
+      }
+    }
+  };
+  if (it0 < it1) load(it0);
   uint32_t ph_tab = 0, ph_mma = 0;
   int cur_a = -1;
   bool ok = true;
   for (int it = it0; it < it1 && ok; ++it) {
-    const int m = item_m(it), am = m < 0 ? -m : m, kap = m + lmax;
+    const int m = item_m(it), am = m < 0 ? -m : m;
     const bool load_tab = am != cur_a;
     if (load_tab && tid == 0) {
       mbar_expect_tx(bar_tab, (uint32_t)sh.leg_per_a);
@@ -314,26 +361,24 @@ __global__ void __launch_bounds__(kWaThreads)
                (uint32_t)sh.leg_per_a, bar_tab);
     }
     cur_a = am;
-    // A[0][s][t] = AP(t) + AP(mirror t), A[1][s][t] = AP(t) - AP(mirror t) (the self-mirror
-    // row of an odd n_theta enters the even part only)
-    const int ntask = kWaRows * (NPp / 8);
-    for (int task = tid; task < ntask; task += kWaThreads) {
-      const int s = task & (kWaRows - 1), tg = task >> 7;
-      float e[8], o[8];
+    // A[0][s][t] = AP(t) + AP(mirror t), A[1][s][t] = AP(t) - AP(mirror t)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int t = 8 * tg + j, tb = Nt - 1 - t;
-        float x = 0.f, y = 0.f;
-        if (t < NP && s < SW) {
-          x = base[((size_t)t * M2 + kap) * SW + s];
-          if (tb != t) y = base[((size_t)tb * M2 + kap) * SW + s];
+    for (int u = 0; u < NT; ++u) {
+      const int task = tid + u * kPThreads;
+      if (task < ntask) {
+        const int s = task & (kWaRows - 1), tg = task >> 7;
+        float e[8], o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int t = 8 * tg + j;
+          e[j] = xv[u][j] + yv[u][j];
+          o[j] = (Nt - 1 - t != t) ? xv[u][j] - yv[u][j] : 0.f;
         }
-        e[j] = x + y;
-        o[j] = (tb != t) ? x - y : 0.f;
+        store_split8(sA, sA + aplane, s, 8 * tg, kWaRows, e);
+        store_split8(sA + 2 * aplane, sA + 3 * aplane, s, 8 * tg, kWaRows, o);
       }
-      store_split8(sA, sA + aplane, s, 8 * tg, kWaRows, e);
-      store_split8(sA + 2 * aplane, sA + 3 * aplane, s, 8 * tg, kWaRows, o);
     }
+    if (it + 1 < it1) load(it + 1);
     fence_async_smem();
     tc_fence_before();
     bool t_ok = true;
@@ -367,10 +412,11 @@ __global__ void __launch_bounds__(kWaThreads)
     ok = __syncthreads_and(w_ok ? 1 : 0) != 0;
     if (!ok) break;
     tc_fence_after();
-    // G'[l = am + par + 2i, m][s]; warp half = parity
+    // G'[l = am + par + 2i, m][s]; warps 4..7 and 12..15 the odd parity, warps 8..15 every
+    // other 16 l
     {
-      const int qd = warp & 3, par = warp >> 2, s = 32 * qd + lane;
-      for (int i0 = 0; i0 < KL; i0 += 16) {
+      const int qd = warp & 3, par = (warp >> 2) & 1, s = 32 * qd + lane;
+      for (int i0 = 16 * (warp >> 3); i0 < KL; i0 += 32) {
         float v[16];
         tmem_ld16_issue(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(par * KL + i0), v);
         tmem_ld_wait();
@@ -390,15 +436,17 @@ __global__ void __launch_bounds__(kWaThreads)
 }
 
 // ------------------------------------------------------------------------------------- P
-// One tile = (block, k, t). Columns of tensor memory: synthesis class c at c QP (4 QP in
-// all), quadrature class c at 4 QP + c KC.
-__global__ void __launch_bounds__(kWaThreads)
+// One tile = (block, k, t), 512 threads. Tensor-memory columns: synthesis class c at c QP
+// (4 QP in all), quadrature class c at 4 QP + c KC. The quadrature runs in passes over QH
+// quarter angles: each pass forms the four classes' folded grid values for its angles once,
+// and its MMAs accumulate into the quadrature columns.
+__global__ void __launch_bounds__(kPThreads, 1)
     k_phi_tc(WaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t tmem_sh;
   const WaShape sh = wa_shape(a.L, a.Nt, a.Np);
-  const int lmax = a.L - 1, M2 = sh.M2, KC = sh.KC, QP = sh.QP, Q = sh.Q;
+  const int lmax = a.L - 1, M2 = sh.M2, KC = sh.KC, QP = sh.QP, Q = sh.Q, QH = p_qh(QP);
   const int Nt = a.Nt, Np = a.Np, SW = a.SW;
   const PSmem ps = p_smem(sh, SW);
   unsigned char* sT = smem + ps.tab;                       // [c][hi|lo][QP x KC]
@@ -406,7 +454,7 @@ __global__ void __launch_bounds__(kWaThreads)
   unsigned char* sA = smem + ps.a;
   const float* Fst = reinterpret_cast<const float*>(smem + ps.f);
   const float* WVb = reinterpret_cast<const float*>(smem + ps.wv);
-  const size_t fplane = (size_t)kWaRows * KC * 2, hplane = (size_t)kWaRows * QP * 2;
+  const size_t fplane = (size_t)kWaRows * KC * 2, hplane = (size_t)kWaRows * QH * 2;
   const size_t tplane = (size_t)QP * KC * 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t bar_tab = smem_u32(&bars[0]), bar_f = smem_u32(&bars[1]),
@@ -425,7 +473,7 @@ __global__ void __launch_bounds__(kWaThreads)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
-  // tile -> (block, k, t); its FA row and W V row
+  // tile -> its FA row and W V row
   auto tile_src = [&](long long tl, const float*& f, const float*& w) {
     const int t = (int)(tl % Nt);
     const int k = (int)((tl / Nt) % a.n_r);  // tl / Nt = block n_r + k
@@ -447,7 +495,9 @@ __global__ void __launch_bounds__(kWaThreads)
   if (!ok) record(a.err, 25);
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
   const uint32_t idesc_s = make_idesc(kWaRows, QP), idesc_a = make_idesc(kWaRows, KC);
-  const int qd = warp & 3, hh = warp >> 2, s_me = 32 * qd + lane;
+  const int qd = warp & 3, cg = warp >> 2, s_me = 32 * qd + lane;
+  const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+  const int npass = QP / QH;
   uint32_t ph_f = 0, ph_mma = 0;
   int buf = 0;
   for (long long tl = blockIdx.x; ok && tl < ntiles; tl += gridDim.x, buf ^= 1) {
@@ -459,7 +509,7 @@ __global__ void __launch_bounds__(kWaThreads)
     // ---- F operand of the four classes: A_c[s][i] = F[kap(c, i)][s]
     {
       const int ntask = kWaRows * 4 * (KC / 8);
-      for (int task = tid; task < ntask; task += kWaThreads) {
+      for (int task = tid; task < ntask; task += kPThreads) {
         const int s = task & (kWaRows - 1), rest = task >> 7;
         const int c = rest & 3, ig = rest >> 2;
         float x[8];
@@ -508,41 +558,37 @@ __global__ void __launch_bounds__(kWaThreads)
     if (!ok) break;
     tc_fence_after();
     const float* wvr = WVb + (size_t)buf * Np;
-    // two passes: classes (cos even, cos odd), then (sin even, sin odd)
-    for (int pass = 0; pass < 2 && ok; ++pass) {
-      // grid values at the four mirror angles of q, times W V, folded back per class
-      {
-        for (int q0 = 16 * hh; q0 < QP; q0 += 32) {
-          float v[4][16];
-          const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)q0;
+    for (int pass = 0; pass < npass && ok; ++pass) {
+      // grid values at the four mirror angles of 8 quarter angles, times W V, folded back
+      // into the four classes: h_c[s][q - pass QH]
+      if (8 * cg < QH) {
+        const int qc = pass * QH + 8 * cg;
+        float v[4][8];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) tmem_ld16_issue(ta + (uint32_t)(c * QP), v[c]);
-          tmem_ld_wait();
-          float h0[16], h1[16];
+        for (int c = 0; c < 4; ++c) tmem_ld8_issue(tmem + lane_base + (uint32_t)(c * QP + qc), v[c]);
+        tmem_ld_wait();
+        float h[4][8];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int q = q0 + j;
-            const float ce = v[0][j], co = v[1][j], se = v[2][j], so = v[3][j];
-            float g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f;
-            if (q <= Q) {
-              const int p2 = 2 * Q - q, p3 = 2 * Q + q, p4 = 4 * Q - q;
-              g1 = wvr[q] * (ce + co + se + so);
-              if (q != Q) g2 = wvr[p2] * (ce - co - se + so);
-              if (q != 0) g3 = wvr[p3] * (ce - co + se - so);
-              if (q != 0 && q != Q) g4 = wvr[p4] * (ce + co - se - so);
-            }
-            if (pass == 0) {
-              h0[j] = (g1 + g2) + (g3 + g4);
-              h1[j] = (g1 - g2) - (g3 - g4);
-            } else {
-              h0[j] = (g1 - g2) + (g3 - g4);
-              h1[j] = (g1 + g2) - (g3 + g4);
-            }
+        for (int j = 0; j < 8; ++j) {
+          const int q = qc + j;
+          const float ce = v[0][j], co = v[1][j], se = v[2][j], so = v[3][j];
+          float g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f;
+          if (q <= Q) {
+            const int p2 = 2 * Q - q, p3 = 2 * Q + q, p4 = 4 * Q - q;
+            g1 = wvr[q] * (ce + co + se + so);
+            if (q != Q) g2 = wvr[p2] * (ce - co - se + so);
+            if (q != 0) g3 = wvr[p3] * (ce - co + se - so);
+            if (q != 0 && q != Q) g4 = wvr[p4] * (ce + co - se - so);
           }
-          store_split8(sA, sA + hplane, s_me, q0, kWaRows, h0);
-          store_split8(sA, sA + hplane, s_me, q0 + 8, kWaRows, h0 + 8);
-          store_split8(sA + 2 * hplane, sA + 3 * hplane, s_me, q0, kWaRows, h1);
-          store_split8(sA + 2 * hplane, sA + 3 * hplane, s_me, q0 + 8, kWaRows, h1 + 8);
+          h[0][j] = (g1 + g2) + (g3 + g4);
+          h[1][j] = (g1 - g2) - (g3 - g4);
+          h[2][j] = (g1 - g2) + (g3 - g4);
+          h[3][j] = (g1 + g2) - (g3 + g4);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          unsigned char* hi = sA + (size_t)c * 2 * hplane;
+          store_split8(hi, hi + hplane, s_me, 8 * cg, kWaRows, h[c]);
         }
       }
       fence_async_smem();
@@ -550,16 +596,16 @@ __global__ void __launch_bounds__(kWaThreads)
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = 2 * pass + cc;
-          const uint32_t ah = smem_u32(sA + (size_t)cc * 2 * hplane), al = ah + (uint32_t)hplane;
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t ah = smem_u32(sA + (size_t)c * 2 * hplane), al = ah + (uint32_t)hplane;
           const uint32_t uh = smem_u32(sUt + (size_t)c * 2 * tplane), ul = uh + (uint32_t)tplane;
-          for (int ks = 0; ks < QP / 16; ++ks) {
-            const uint32_t ao = ks * (kWaRows / 8) * 256, uo = ks * (KC / 8) * 256;
+          for (int ks = 0; ks < QH / 16; ++ks) {
+            const uint32_t ao = ks * (kWaRows / 8) * 256;
+            const uint32_t uo = (pass * (QH / 16) + ks) * (KC / 8) * 256;
             const uint64_t dah = make_desc(ah + ao, 128, 256), dal = make_desc(al + ao, 128, 256);
             const uint64_t duh = make_desc(uh + uo, 128, 256), dul = make_desc(ul + uo, 128, 256);
             const uint32_t d = tmem + (uint32_t)(4 * QP + c * KC);
-            mma_bf16(d, dah, duh, idesc_a, ks > 0 ? 1u : 0u);
+            mma_bf16(d, dah, duh, idesc_a, (pass > 0 || ks > 0) ? 1u : 0u);
             mma_bf16(d, dah, dul, idesc_a, 1u);
             mma_bf16(d, dal, duh, idesc_a, 1u);
           }
@@ -573,22 +619,19 @@ __global__ void __launch_bounds__(kWaThreads)
       tc_fence_after();
     }
     if (!ok) break;
-    // AP[kap][s] in place of the row's F; warp half hh writes classes 2 hh, 2 hh + 1
+    // AP[kap][s] in place of the row's F; warp column group cg writes class cg
     {
       float* dst = a.FA + (size_t)tl * M2 * SW;
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * hh + cc;
-        for (int i0 = 0; i0 < KC; i0 += 16) {
-          float v[16];
-          tmem_ld16_issue(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(4 * QP + c * KC + i0),
-                          v);
-          tmem_ld_wait();
-          if (s_me < SW) {
+      const int c = cg;
+      for (int i0 = 0; i0 < KC; i0 += 16) {
+        float v[16];
+        tmem_ld16_issue(tmem + lane_base + (uint32_t)(4 * QP + c * KC + i0), v);
+        tmem_ld_wait();
+        if (s_me < SW) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int kap = class_kap(c, i0 + j, lmax);
-              if (kap >= 0) dst[(size_t)kap * SW + s_me] = v[j];
-            }
+          for (int j = 0; j < 16; ++j) {
+            const int kap = class_kap(c, i0 + j, lmax);
+            if (kap >= 0) dst[(size_t)kap * SW + s_me] = v[j];
           }
         }
       }
@@ -620,7 +663,9 @@ void residency(size_t smem, uint32_t tcols, int& per_sm, size_t& request) {
 bool angular_wide_eligible(int L, int n_theta, int n_phi) {
   if (L < 1 || n_theta < 2 || n_phi < 8 || (n_phi & 3) != 0) return false;
   const WaShape s = wa_shape(L, n_theta, n_phi);
-  if (s.NPp > 256 || s.QP > 128 || s.KC > 128 || s.KL > 128) return false;
+  // register-prefetch bounds of the Legendre passes: KL <= 32 (lmax <= 62), NPp <= 64
+  // (n_theta <= 128)
+  if (s.NPp > 64 || s.KL > 32 || s.QP > 128 || s.KC > 128) return false;
   if (4 * s.QP + 4 * s.KC > 512 || 2 * s.NPp > 512) return false;
   if (l1_smem(s) > 200 * 1024 || l2_smem(s) > 200 * 1024) return false;
   return p_smem(s, kWaRows).total <= 220 * 1024;
@@ -722,10 +767,11 @@ cudaError_t launch_angular_wide(const AngArgs<float>& a, const void* tab, float*
   int per_sm;
   size_t req;
   residency(l1_smem(s), pow2_cols(2 * s.NPp), per_sm, req);
-  if ((e = cudaFuncSetAttribute(k_leg_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)req)) != cudaSuccess)
+  auto l1 = s.KL <= 16 ? k_leg_synth_tc<2> : k_leg_synth_tc<4>;
+  if ((e = cudaFuncSetAttribute(l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req)) !=
+      cudaSuccess)
     return e;
-  k_leg_synth_tc<<<base * nmr, kWaThreads, req, stream>>>(w);
+  l1<<<base * nmr, kWaThreads, req, stream>>>(w);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const PSmem ps = p_smem(s, w.SW);
   residency(ps.total, pow2_cols(4 * s.QP + 4 * s.KC), per_sm, req);
@@ -735,13 +781,14 @@ cudaError_t launch_angular_wide(const AngArgs<float>& a, const void* tab, float*
   const long long ntiles = (long long)w.nblk * a.n_r * a.n_theta;
   long long grid = (long long)nsm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_phi_tc<<<(int)grid, kWaThreads, req, stream>>>(w);
+  k_phi_tc<<<(int)grid, kPThreads, req, stream>>>(w);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   residency(l2_smem(s), pow2_cols(2 * s.KL), per_sm, req);
-  if ((e = cudaFuncSetAttribute(k_leg_anal_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)req)) != cudaSuccess)
+  auto l2 = s.NPp <= 32 ? k_leg_anal_tc<1> : k_leg_anal_tc<2>;
+  if ((e = cudaFuncSetAttribute(l2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req)) !=
+      cudaSuccess)
     return e;
-  k_leg_anal_tc<<<base * nmr, kWaThreads, req, stream>>>(w);
+  l2<<<base * nmr, kPThreads, req, stream>>>(w);
   return cudaGetLastError();
 }
 

@@ -127,6 +127,15 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float* v) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+// 8 columns of the warp's 32 lanes, without the wait
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }

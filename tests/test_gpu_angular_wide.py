@@ -88,7 +88,7 @@ def test_wide_and_fused_blocks_agree(case, monkeypatch):
 
 def test_wide_block_is_default_above_fused_limit(monkeypatch):
     """Without CS_ANGULAR_KERNEL, lmax 60 takes the wide block (three angular launches);
-    CS_ANGULAR_KERNEL=simt takes the FP32 kernel (one launch) and agrees to the mixed level."""
+    CS_ANGULAR_KERNEL=rp takes the FP32 row-pair kernel (one launch) and agrees to the mixed level."""
     torch, cs = need_gpu()
     monkeypatch.delenv("CS_ANGULAR_KERNEL", raising=False)
     w = CASES["l60_t120_p240"]
@@ -97,7 +97,7 @@ def test_wide_block_is_default_above_fused_limit(monkeypatch):
     n0 = cs.cs_launch_count(ctx)
     a = to_host(_mixed_apply(torch, cs, ctx, Xd), ctx.d)
     assert cs.cs_launch_count(ctx) - n0 == 5
-    monkeypatch.setenv("CS_ANGULAR_KERNEL", "simt")
+    monkeypatch.setenv("CS_ANGULAR_KERNEL", "rp")
     n0 = cs.cs_launch_count(ctx)
     b = to_host(_mixed_apply(torch, cs, ctx, Xd), ctx.d)
     assert cs.cs_launch_count(ctx) - n0 == 3
