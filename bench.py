@@ -102,12 +102,24 @@ def dense_flops(d, n):
 NCU_TRAFFIC_BYTES = {"angular_f32": 32.496384e6 + 1024.0}  # k_angular_tc (mixed default)
 
 
+# the profiling recipe's fallback denominators, used only when the generated peaks file
+# is absent: one earlier GB300 measurement (HBM copy, cuBLAS bf16 burst and sustained)
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "source": "fallback"}
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
-            return json.load(f)
+            p = json.load(f)
+        p.setdefault("source", "measured")
+        return p
     except (OSError, ValueError):
-        return {}
+        return dict(FALLBACK_PEAKS)
+
+
+def peak_word(peaks):
+    return "fallback" if peaks.get("source") == "fallback" else "measured"
 
 
 def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps, dense_prec):
@@ -116,7 +128,7 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps, dense_prec):
     class (Gram matrices and rotations of CholQR2 and Rayleigh-Ritz, factor, eigensolve) is
     rated against the pipe its Gram matrices and rotations run on: FP64, or the FP32 pipe in
     double-float."""
-    from paper_1404_3773_gb300 import CS_DF64, CS_MIXED_BF16
+    from paper_1404_3773_gb300 import CS_DF64, CS_FP64_SLICED, CS_MIXED_BF16
     names = cs.profile_class_names()
     af = algorithmic_flops(w, n_s)
     peaks = measured_peaks()
@@ -140,13 +152,18 @@ def roofline_table(cs, w, d, n_s, prec, prof_ms, prof_n, steps, dense_prec):
         else:
             flops = None
         if f32 and prec == CS_MIXED_BF16 and fam.startswith("radial") and bf16:
-            bound, peak, src = "tensor", bf16, "measured bf16 sustained (MEASURED_PEAKS.json)"
+            bound, peak, src = "tensor", bf16, f"{peak_word(peaks)} bf16 sustained"
         elif mixed_ang:
             bound, peak, src = "alu", FP32_PEAK_TFLOPS, (
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; counted: the Legendre sums and W V "
                 "on the FP32 pipe (the phi transforms run on tcgen05 and are not counted)")
         elif f32:
             bound, peak, src = "alu", FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        elif fam == "dense" and dense_prec == CS_FP64_SLICED and bf16:
+            # each FP64 product is 36 BF16 slice products (8 digits, pairs k + l <= 7)
+            bound, peak, src = "tensor", bf16 / 36.0, (
+                f"{peak_word(peaks)} bf16 sustained / 36 (FP64-equivalent rate of the slice "
+                "products; the class also holds the FP64 factor, eigensolve and residual kernels)")
         elif kind == "df64" or (fam == "dense" and dense_prec == CS_DF64):
             bound, peak, src = "alu", DF64_PEAK_TFLOPS, ("FP32 issue rate / 15 instructions "
                                                          "per double-float multiply-add")
@@ -1210,16 +1227,40 @@ def at_scale_chfsi_measure(dev, chunk=128, timed_iters=2, cpu_seconds=10.0):
         dom = max(single, key=lambda k: single[k]["ms_per_iteration"])
         n_launch = pn[names.index(dom)]
         avg_ms = pms[names.index(dom)] / n_launch
-        if dom == "angular_f32":
-            per_launch = ang_flops_state * chunk  # one launch per 128-state chunk
+        if dom == "angular_df64":
+            # the Rayleigh-Ritz H.X: one launch over all states, double-float on the FP32 pipe
+            per_launch = ang_flops_state * n_s / max(1.0, pn[names.index(dom)] / timed_iters)
             ach = per_launch / (avg_ms / 1e3) / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4),
-                    "peak": round(FP32_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
-                    "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                    "peak": round(DF64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+                    "frac": round(ach / DF64_PEAK_TFLOPS, 4), "traffic": None,
                     "flops_per_launch": per_launch, "avg_launch_ms": round(avg_ms, 4),
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                    "note": "flops per launch include the last, ragged chunk's 112 states as "
-                            "128"}
+                    "peak_source": "FP32 issue rate / 15 instructions per double-float "
+                                   "multiply-add"}
+        elif dom == "angular_f32":
+            # the mixed filter's angular block, one profiled record per H.X: at lmax 60 the
+            # three-pass tensor-core block (Legendre sums, phi passes, Legendre quadrature)
+            # unless CS_ANGULAR_KERNEL selects another
+            env = os.environ.get("CS_ANGULAR_KERNEL", "")
+            wide = env == "" or env.startswith("w")
+            flops = ang_flops_state * chunk
+            ach = flops / (avg_ms / 1e3) / 1e12
+            peaks = measured_peaks()
+            byts = 2.0 * w.n_r * L * L * chunk * 4  # G in, G' out (FP32)
+            if wide:
+                peak = peaks["bf16_tflops_sustained"] / 3.0
+                src = (f"{peak_word(peaks)} bf16 sustained / 3 (split BF16: three BF16 products "
+                       "per product)")
+            else:
+                peak, src = FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+            roof = {"bound": "tensor" if wide else "alu", "kernel": dom,
+                    "launches_per_hx": 3 if wide else 1, "achieved": round(ach, 4),
+                    "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                    "traffic": None, "flops_per_hx": flops, "ms_per_hx": round(avg_ms, 4),
+                    "peak_source": src,
+                    "hbm_view": {"algorithmic_bytes": byts,
+                                 "achieved_gbs": round(byts / (avg_ms / 1e3) / 1e9, 1)},
+                    "note": "flops per H.X include the last, ragged chunk's 112 states as 128"}
         else:
             roof = {"kernel": dom, "avg_launch_ms": round(avg_ms, 4), "frac": None}
     cpu = cpu_baseline_local(w, dev, budget_s=cpu_seconds)
@@ -1341,6 +1382,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_hx(case, n_states, reps):
+    """A small case for profiler captures (no JSON bench line): `reps` mixed H.X calls on
+    `n_states` seeded states of the 32-atom cluster (erf32) or of the 400-atom cluster without
+    its projectors (erf400), after one untimed call; prints the mean CUDA-event time."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t
+    w = W.erf_cluster_32() if case == "erf32" else W.erf_cluster_400_kb()
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, 0)
+    xyz = torch.tensor(cs.grid_points(ctx), device="cuda")
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, w.atoms()).contiguous())
+    del xyz
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.x_seed)
+    X = torch.randn((n_states, ctx.d), generator=gen, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    work = ctx.workspace(n_states, cs.CS_MIXED_BF16)
+    cs.cs_apply_H(ctx, X, Y, cs.CS_MIXED_BF16, work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        cs.cs_apply_H(ctx, X, Y, cs.CS_MIXED_BF16, work)
+    e1.record()
+    e1.synchronize()
+    if cs.cs_device_error(ctx) != 0:
+        raise RuntimeError("device error word set")
+    print(json.dumps({"profile_hx": case, "states": n_states, "reps": reps,
+                      "ms_per_apply": round(e0.elapsed_time(e1) / max(1, reps), 4),
+                      "angular_kernel": os.environ.get("CS_ANGULAR_KERNEL", "default")}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1365,7 +1440,14 @@ def main():
     ap.add_argument("--no-at-scale-chfsi", action="store_true",
                     help="skip the ChFSI iterations of the 400-atom cluster (880 states)")
     ap.add_argument("--no-scf", action="store_true")
+    ap.add_argument("--profile-hx", default=None, choices=["erf32", "erf400"],
+                    help="only run a small mixed H.X case for profiler captures")
+    ap.add_argument("--profile-states", type=int, default=32)
+    ap.add_argument("--profile-reps", type=int, default=2)
     args = ap.parse_args()
+    if args.profile_hx:
+        profile_hx(args.profile_hx, args.profile_states, args.profile_reps)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -41,6 +41,7 @@ struct BCluster {
   float* X;                // caller block (ld)
   float* Yalt;             // workspace block (ld_alt)
   float* G;                // workspace radial-node intermediate
+  float* FA;               // workspace intermediate of the three-pass angular block (or null)
   long long ld, ld_alt;
   const float* coef;       // [step][3]: cA, cB, cshift
   int n_items[3];
@@ -249,7 +250,7 @@ struct cs_batch {
   int* d_ctr = nullptr;           // head + 3 counters per cluster
   std::vector<BCluster> h_cl;
   std::vector<float> h_coef;
-  std::vector<size_t> off_alt, off_G, off_bk;  // workspace offsets per cluster
+  std::vector<size_t> off_alt, off_G, off_bk, off_wa;  // workspace offsets per cluster
   size_t ws_bytes = 0;
   cudaGraphExec_t graph = nullptr;
   std::vector<void*> graph_key;  // pointers the graph was captured with
@@ -362,6 +363,9 @@ cudaError_t launch_cluster_filter(cs_batch* b, int ci, cudaStream_t st) {
   tt.rows_anal = c->tc_rows_anal;
   tt.kpad_anal = c->tc_kpad_anal;
   const bool tc_rad = b->mixed && tc_radial_fits(H);
+  // the angular block that cs_apply_H takes for this cluster in the mixed precision
+  const bool wide = b->mixed && c->wide_tab && bc.FA &&
+                    angular_wide_enabled(H.L, H.n_theta, H.n_phi, c->tc_phi != nullptr);
   const bool tc_ang = b->mixed && c->tc_phi && angular_tc_enabled();
   float* prev = bc.X;
   long long ldp = bc.ld;
@@ -377,8 +381,9 @@ cudaError_t launch_cluster_filter(cs_batch* b, int ci, cudaStream_t st) {
     e = tc_rad ? launch_tc_radial_synth(tt, H, in, ldi, bc.G, S, c->dev_err, st)
                : launch_radial_synth<float>(in, ldi, bc.G, bc.rad, H.L, H.N, H.n_r, S, st);
     if (e != cudaSuccess) break;
-    e = tc_ang ? launch_angular_tc(bc.ang, c->tc_phi, bc.G, c->dev_err, st)
-               : launch_angular<float>(bc.ang, ANG_FULL, bc.G, nullptr, nullptr, st);
+    e = wide     ? launch_angular_wide(bc.ang, c->wide_tab, bc.G, bc.FA, c->dev_err, st)
+        : tc_ang ? launch_angular_tc(bc.ang, c->tc_phi, bc.G, c->dev_err, st)
+                 : launch_angular<float>(bc.ang, ANG_FULL, bc.G, nullptr, nullptr, st);
     if (e != cudaSuccess) break;
     Epilogue<float> ep;
     ep.mode = EP_CHEB;
@@ -561,6 +566,8 @@ cs_status run_filter(cs_batch* b, float* const* X, const long long* ld, const do
     b->h_cl[ci].ld = ld[ci];
     b->h_cl[ci].Yalt = reinterpret_cast<float*>((char*)work + b->off_alt[ci]);
     b->h_cl[ci].G = reinterpret_cast<float*>((char*)work + b->off_G[ci]);
+    b->h_cl[ci].FA =
+        b->off_wa[ci] ? reinterpret_cast<float*>((char*)work + b->off_wa[ci]) : nullptr;
     key.push_back(X[ci]);
     key.push_back((void*)(intptr_t)ld[ci]);
   }
@@ -653,6 +660,12 @@ cs_status cs_batch_create(int n, cs_ctx* const* ctxs, const int* n_s, int degree
     b->h_cl.push_back(bc);
     b->off_alt.push_back(take((size_t)H.d * n_s[i] * sizeof(float)));
     b->off_G.push_back(take((size_t)H.n_r * H.L * H.L * n_s[i] * sizeof(float)));
+    // the three-pass angular block's intermediate, wherever that block is eligible (the
+    // precision may change after creation); offset 0 marks none
+    const size_t wa = angular_wide_eligible(H.L, H.n_theta, H.n_phi)
+                          ? angular_wide_work_bytes(H.L, H.n_r, H.n_theta, n_s[i])
+                          : 0;
+    b->off_wa.push_back(wa ? take(wa) : 0);
   }
   for (int i = 0; i < n; ++i)  // tuner's copy of the blocks
     b->off_bk.push_back(take((size_t)ctxs[i]->host.d * n_s[i] * sizeof(float)));
