@@ -73,6 +73,18 @@ cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream
   }
 }
 
+template <typename T>
+bool angular_rp_fits(int L, int Q4) {
+  const int Q = Q4 + 1, rowlen = L * (L + 1) / 2;
+  const int st_rc[][2] = {{8, 8}, {8, 4}, {4, 8}, {4, 4}, {2, 8}, {2, 4}};
+  for (const auto& v : st_rc)
+    if (rp_smem_elems(L, Q, rowlen, v[0], v[1]) * sizeof(T) <= 227 * 1024) return true;
+  return false;
+}
+template bool angular_rp_fits<float>(int, int);
+template bool angular_rp_fits<double>(int, int);
+template bool angular_rp_fits<df64>(int, int);
+
 template cudaError_t launch_angular_rp<float>(const AngArgs<float>&, float*, int, cudaStream_t);
 template cudaError_t launch_angular_rp<double>(const AngArgs<double>&, double*, int, cudaStream_t);
 template cudaError_t launch_angular_rp<df64>(const AngArgs<df64>&, df64*, int, cudaStream_t);

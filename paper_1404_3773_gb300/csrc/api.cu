@@ -25,7 +25,8 @@ thread_local std::string g_init_error;
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, oz, kbtc, wa, total;
+  size_t G, Yalt, X32, Wkb, kbZ, HX, tmp, part, small, lanV, status, HXr, chw, oz, wd, kbtc, wa,
+      total;
 };
 
 constexpr int kMaxLanczos = 64;
@@ -73,6 +74,11 @@ Layout layout(const cs_ctx* c, int n_s, cs_precision prec) {
                                    oz_rotate_work_bytes(T.d, (int)np, n_s)));
   }
   o.oz = take(ozb);
+  // double-float intermediate of the three-pass angular block (one block of 32 states), sized
+  // whenever that block is eligible, whatever the precision of the call
+  o.wd = take(angular_wide_df_eligible(T.L, T.n_theta, T.n_phi)
+                  ? angular_wide_df_work_bytes(T.L, T.n_r, T.n_theta)
+                  : 0);
   // last, so that every other offset is the same for both precisions
   auto is_f32 = [](cs_precision p) { return p == CS_FP32 || p == CS_MIXED_BF16; };
   const bool reduced = is_f32(prec) || is_f32(c->rr_prec);
@@ -305,6 +311,14 @@ cs_status hx_core(cs_ctx* c, int n_s, const T* X, long long ldx, T* out, long lo
       ang_done = true;
     } else if (tc && c->tc_phi && angular_tc_enabled()) {
       CS_LAUNCH_CLS(c, prof_cls<T>(1), 1, launch_angular_tc(a, c->tc_phi, G, c->dev_err, st));
+      ang_done = true;
+    }
+  }
+  if constexpr (std::is_same<T, df64>::value) {
+    if (angular_wide_df_enabled(H.L, H.n_theta, H.n_phi, c->Q4)) {
+      const int nblk = (n_s + 31) / 32;
+      CS_LAUNCH_CLS(c, prof_cls<T>(1), 3 * nblk,
+                    launch_angular_wide_df(a, G, reinterpret_cast<df64*>(work + lay.wd), st));
       ang_done = true;
     }
   }

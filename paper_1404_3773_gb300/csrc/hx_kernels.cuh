@@ -59,6 +59,19 @@ cudaError_t launch_angular(const AngArgs<T>& a, int mode, T* G, T* gout, const T
 // variant -1 = first (states per CTA, row pairs per chunk) tile that fits shared memory
 template <typename T>
 cudaError_t launch_angular_rp(const AngArgs<T>& a, T* G, int variant, cudaStream_t stream);
+// whether some row-pair tile fits in shared memory
+template <typename T>
+bool angular_rp_fits(int L, int Q4);
+
+// three-pass double-float angular block for large lmax (angular_wide_df.cu): Legendre sums per
+// m, folded phi transforms per grid row, Legendre quadrature per m, in blocks of 32 states
+// through the double-float intermediate FA (angular_wide_df_work_bytes, one block); needs n_phi
+// a multiple of 4. Taken where no row-pair tile fits, or with CS_ANGULAR_KERNEL=wide.
+bool angular_wide_df_eligible(int L, int n_theta, int n_phi);
+bool angular_wide_df_enabled(int L, int n_theta, int n_phi, int Q4);
+size_t angular_wide_df_work_bytes(int L, int n_r, int n_theta);
+cudaError_t launch_angular_wide_df(const AngArgs<df64>& a, df64* G, df64* FA,
+                                   cudaStream_t stream);
 
 // register-blocked FP32 angular kernel (angular_gm.cu); cudaErrorInvalidConfiguration when
 // its tile does not fit in shared memory or the transposed Legendre table is missing

@@ -103,3 +103,49 @@ def test_wide_block_is_default_above_fused_limit(monkeypatch):
     assert cs.cs_launch_count(ctx) - n0 == 3
     fro, _ = rel_errors(a, b)
     assert fro <= 5e-5, fro
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_double_float_wide_block_matches_oracle(case, monkeypatch):
+    """The double-float three-pass block (Legendre products per m, folded phi passes per grid
+    row, 32-state blocks) holds the FP64 bar, 1e-11 relative, against the FP64 oracle; the
+    130-state case runs five blocks, the last of 2 states."""
+    torch, cs = need_gpu()
+    monkeypatch.setenv("CS_ANGULAR_KERNEL", "wide")
+    w = CASES[case]
+    ctx = make_ctx(w)
+    X = w.x_block()
+    ref = oracle_H(w.name).apply(X)
+    Xd = to_dev(X, ld=ctx.d + 3)
+    HXd = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXd, cs.CS_DF64)
+    torch.cuda.synchronize()
+    fro, col = rel_errors(to_host(HXd, ctx.d), ref)
+    print(f"double-float wide {case}: fro {fro:.3e} col {col:.3e}")
+    assert fro <= 1e-11 and col <= 1e-11, (fro, col)
+    assert torch.all(HXd[:, ctx.d:] == 0)
+    assert cs.cs_device_error(ctx) == 0
+
+
+def test_double_float_wide_block_is_default_where_row_pairs_do_not_fit(monkeypatch):
+    """At lmax 60 no double-float row-pair tile fits: the wide block runs by default (three
+    launches per 32-state block), and the row-stream kernel (CS_ANGULAR_KERNEL=stream) agrees
+    with it to the double-float level."""
+    torch, cs = need_gpu()
+    monkeypatch.delenv("CS_ANGULAR_KERNEL", raising=False)
+    w = CASES["l60_t120_p240"]
+    ctx = make_ctx(w)
+    Xd = to_dev(w.x_block())
+    HXa = torch.zeros_like(Xd)
+    n0 = cs.cs_launch_count(ctx)
+    cs.cs_apply_H(ctx, Xd, HXa, cs.CS_DF64)
+    torch.cuda.synchronize()
+    # conversion in, radial synthesis, 3 angular launches, radial analysis, conversion out
+    assert cs.cs_launch_count(ctx) - n0 >= 5
+    monkeypatch.setenv("CS_ANGULAR_KERNEL", "stream")
+    HXb = torch.zeros_like(Xd)
+    cs.cs_apply_H(ctx, Xd, HXb, cs.CS_DF64)
+    torch.cuda.synchronize()
+    fro, _ = rel_errors(to_host(HXa, ctx.d), to_host(HXb, ctx.d))
+    print(f"double-float wide vs row-stream at lmax 60: {fro:.3e}")
+    assert 0 < fro <= 1e-12, fro
