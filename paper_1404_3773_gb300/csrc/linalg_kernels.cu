@@ -389,6 +389,102 @@ __global__ void __launch_bounds__(32) k_tri_inv_col(const double* __restrict__ w
   for (int i = lane; i < n; i += 32) U[c + (size_t)i * n] = (i >= c) ? dc * y[i - c] : 0.0;
 }
 
+// The same factor for blocks whose L does not fit one CTA's shared memory, blocked over
+// panels of kCholNB columns so that the O(n^3) trailing update runs on the whole GPU: per panel
+// one CTA factors its columns (the one-CTA method above, restricted to the panel) and a grid of
+// 32 x 32 lower tiles subtracts the panel's outer product from the trailing block. L lives in
+// `work` (L2-resident); status is cleared before the first launch.
+constexpr int kCholNB = 32;
+
+__global__ void k_chol_init(const double* __restrict__ M, int n, double* __restrict__ work,
+                            int* __restrict__ status) {
+  double* Lc = work;
+  double* Dv = work + (size_t)n * n;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const double mi = M[i + (size_t)i * n], mj = M[j + (size_t)j * n];
+  const bool oki = mi > 0.0 && isfinite(mi), okj = mj > 0.0 && isfinite(mj);
+  if (i == j) {
+    Dv[i] = oki ? rsqrt(mi) : 0.0;
+    if (!oki) atomicCAS(status, 0, i + 1);
+  }
+  Lc[e] = (i >= j && oki && okj) ? M[e] * rsqrt(mi) * rsqrt(mj) : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_chol_panel(int n, int p, double* __restrict__ work,
+                                                    int* __restrict__ status) {
+  double* Lc = work;
+  double* rinv = work + (size_t)n * n + n;
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nt >> 5, pe = min(p + kCholNB, n);
+  if (status[0] != 0) return;
+  for (int j = p; j < pe; ++j) {
+    if (tid == 0) {
+      fail = 0;
+      const double piv = Lc[j + (size_t)j * n];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        fail = 1;
+        status[0] = j + 1;
+      } else {
+        const double r = rsqrt(piv);
+        rinv[j] = r;
+        Lc[j + (size_t)j * n] = piv * r;
+      }
+    }
+    __syncthreads();
+    if (fail) return;
+    const double r = rinv[j];
+    for (int i = j + 1 + tid; i < n; i += nt) Lc[i + (size_t)j * n] *= r;
+    __syncthreads();
+    for (int k = j + 1 + warp; k < pe; k += nw) {
+      const double lkj = Lc[k + (size_t)j * n];
+      for (int i = k + lane; i < n; i += 32) Lc[i + (size_t)k * n] -= Lc[i + (size_t)j * n] * lkj;
+    }
+    __syncthreads();
+  }
+}
+
+// trailing update after panel p: L[i][k] -= sum_{j in panel} L[i][j] L[k][j], i >= k >= p + NB;
+// one CTA per 32 x 32 tile on or below the diagonal (tile index t -> (ti >= tk))
+__global__ void __launch_bounds__(256) k_chol_trail(int n, int p, double* __restrict__ work,
+                                                    const int* __restrict__ status) {
+  __shared__ double Ai[32][kCholNB + 1], Ak[32][kCholNB + 1];
+  if (status[0] != 0) return;
+  double* Lc = work;
+  const int q = p + kCholNB;  // first trailing column
+  int t = blockIdx.x, ti = 0;
+  while (t > ti) {  // row tile ti holds tiles tk = 0 .. ti
+    t -= ti + 1;
+    ++ti;
+  }
+  const int tk = t;
+  const int i0 = q + 32 * ti, k0 = q + 32 * tk;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * kCholNB; e += blockDim.x) {
+    const int r = e % 32, c = e / 32;
+    const int ii = i0 + r, kk = k0 + r;
+    Ai[r][c] = ii < n ? Lc[ii + (size_t)(p + c) * n] : 0.0;
+    Ak[r][c] = kk < n ? Lc[kk + (size_t)(p + c) * n] : 0.0;
+  }
+  __syncthreads();
+  // thread: row r = tid % 32, columns c = tid / 32 + 8 u (u < 4)
+  const int r = tid & 31, cb = tid >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = 0; j < kCholNB; ++j) {
+    const double a = Ai[r][j];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(a, Ak[cb + 8 * u][j], acc[u]);
+  }
+  const int i = i0 + r;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int k = k0 + cb + 8 * u;
+    if (i < n && k < n && i >= k) Lc[i + (size_t)k * n] -= acc[u];
+  }
+}
+
 cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work, int* status,
                                  cudaStream_t stream) {
   size_t smem = ((size_t)n * n + 2 * n) * sizeof(double);
@@ -399,7 +495,17 @@ cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work
     if (e != cudaSuccess) return e;
     k_cholesky<true><<<1, 1024, smem, stream>>>(M, n, work, status);
   } else {
-    k_cholesky<false><<<1, 1024, 0, stream>>>(M, n, work, status);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), stream)) != cudaSuccess) return e;
+    const long long n2 = (long long)n * n;
+    k_chol_init<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(M, n, work, status);
+    for (int p = 0; p < n; p += kCholNB) {
+      k_chol_panel<<<1, 256, 0, stream>>>(n, p, work, status);
+      const int rest = n - (p + kCholNB);
+      if (rest > 0) {
+        const int t = (rest + 31) / 32;
+        k_chol_trail<<<(unsigned)(t * (t + 1) / 2), 256, 0, stream>>>(n, p, work, status);
+      }
+    }
   }
   const size_t sm2 = ((size_t)n * n + n) * sizeof(double);
   if (sm2 <= 200 * 1024) {
@@ -1148,19 +1254,29 @@ __global__ void __launch_bounds__(1024) k_le_tridiag(const T* __restrict__ A, in
 
 // eigenvalue i by bisection on Sturm counts, its eigenvector of T by inverse iteration
 // (column i of Y; L factors in column i of L), one thread per eigenvalue
+// Eigenvalues of the tridiagonal (d, e) by multisection on Sturm counts, one warp per
+// eigenvalue: each round the 32 lanes evaluate the count at 32 interior points of the bracket
+// (33 equal parts) and a warp vote keeps the part that holds eigenvalue i, 33x per round where
+// bisection gives 2x, so about 11 serial Sturm sweeps reach the FP64 resolution instead of
+// about 55, and the warps of all eigenvalues spread over the GPU. Lane 0 then finds the
+// eigenvector by inverse iteration with the LDL^T factors of T - lambda I (three passes from a
+// start vector that differs per eigenvalue).
 template <typename T>
-__global__ void k_le_bisect(int n, const T* __restrict__ d, const T* __restrict__ e,
-                            const T* __restrict__ e2, const T* __restrict__ bnd,
-                            T* __restrict__ lam, T* __restrict__ Y, T* __restrict__ Ls) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(256) k_le_multisect(int n, const T* __restrict__ d,
+                                                      const T* __restrict__ e,
+                                                      const T* __restrict__ e2,
+                                                      const T* __restrict__ bnd,
+                                                      T* __restrict__ lam, T* __restrict__ Y,
+                                                      T* __restrict__ Ls) {
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps leave together
   const T glo = bnd[0], ghi = bnd[1];
   const T tnorm = fmax(fabs(glo), fabs(ghi)) + T(1e-30);
   const T piv = EigEps<T>::v() * tnorm;
-  T a = glo - piv, b = ghi + piv;
-  for (int it = 0; it < 128; ++it) {
-    const T x = T(0.5) * (a + b);
-    if (!(x > a && x < b)) break;
+  T a = glo - piv, b = ghi + piv;  // count(a) <= i < count(b)
+  for (int round = 0; round < 40; ++round) {
+    const T x = a + (b - a) * (T)(lane + 1) * T(1.0 / 33.0);
     int cnt = 0;
     T q = d[0] - x;
     if (fabs(q) < piv) q = -piv;
@@ -1170,9 +1286,19 @@ __global__ void k_le_bisect(int n, const T* __restrict__ d, const T* __restrict_
       if (fabs(q) < piv) q = -piv;
       cnt += (q < T(0));
     }
-    if (cnt > i) b = x;
-    else a = x;
+    // the first interior point above eigenvalue i bounds it from above, the point before it
+    // from below
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
+    const int k = above ? __ffs(above) - 1 : 32;
+    const T xk = __shfl_sync(0xffffffffu, x, k < 32 ? k : 31);
+    const T xl = __shfl_sync(0xffffffffu, x, k > 0 ? k - 1 : 0);
+    const T na = (k == 0) ? a : xl;
+    const T nb = (k == 32) ? b : xk;
+    if (!(na > a || nb < b)) break;  // no interior point moved the bracket: resolution reached
+    a = na;
+    b = nb;
   }
+  if (lane != 0) return;
   const T x = T(0.5) * (a + b);
   lam[i] = x;
   T* y = Y + (size_t)i * n;
@@ -1283,7 +1409,8 @@ cudaError_t le_stage(const double* Ain, int n, double* big, double* vec, double*
     k_le_update<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
   }
   k_le_tridiag<T><<<1, 1024, 0, st>>>(a.A, n, a.d, a.e, a.e2, a.bnd);
-  k_le_bisect<T><<<(n + 31) / 32, 32, 0, st>>>(n, a.d, a.e, a.e2, a.bnd, a.lam, a.Y, a.L);
+  k_le_multisect<T><<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(
+      n, a.d, a.e, a.e2, a.bnd, a.lam, a.Y, a.L);
   k_le_clusters<T><<<1, 1024, 0, st>>>(n, a.lam, a.bnd, T(1e-10), a.Y, a.cst);
   for (int k = n - 3; k >= 0; --k) k_le_apply<T><<<(n + 7) / 8, 256, 0, st>>>(a.A, n, k, a.Y);
   k_le_out<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(a.Y, n2, V0, status);

@@ -76,6 +76,34 @@ def test_cholqr_matches_oracle():
     assert np.max(np.abs(got - ref)) < 1e-10
 
 
+@pytest.mark.parametrize("n_s", [200, 333])
+def test_cholqr_large_block_matches_oracle(n_s):
+    """Blocks whose Cholesky factor does not fit one CTA's shared memory take the blocked
+    factor (panels of 32 columns, trailing updates over the GPU); 333 states leave a ragged
+    last panel. Column norms spread over 4 decades."""
+    torch, cs = need_gpu()
+    ctx = make_ctx(HO)
+    rng = np.random.default_rng(81)
+    X = rng.standard_normal((ctx.d, n_s)) @ np.diag(np.logspace(0, 4, n_s))
+    ref = eigen.cholqr(X)
+    Xd = to_dev(X)
+    cs.cs_cholqr(ctx, Xd)
+    torch.cuda.synchronize()
+    got = to_host(Xd, ctx.d)
+    assert np.max(np.abs(got.T @ got - np.eye(n_s))) < 1e-13
+    assert np.max(np.abs(got - ref)) < 1e-10
+
+
+def test_cholqr_large_block_rank_deficient_reports_breakdown():
+    torch, cs = need_gpu()
+    ctx = make_ctx(HO)
+    rng = np.random.default_rng(82)
+    X = rng.standard_normal((ctx.d, 200))
+    X[:, 150] = 0.0  # a zero column: its Gram diagonal is zero, the blocked factor stops
+    with pytest.raises(cs.CsError, match="CS_ERR_CHOLESKY"):
+        cs.cs_cholqr(ctx, to_dev(X))
+
+
 def test_cholqr_rank_deficient_reports_breakdown():
     torch, cs = need_gpu()
     ctx = make_ctx(SMALL)
