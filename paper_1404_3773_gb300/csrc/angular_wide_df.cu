@@ -122,11 +122,7 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_synth_df(DfArgs a) {
     __syncthreads();
     for (int ti = threadIdx.x; ti < ntile; ti += blockDim.x) {
       const int t0 = 2 * (ti / (kDfSB / 4)), s0 = 4 * (ti % (kDfSB / 4));
-      df64 e[2][4], o[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) e[u][v] = o[u][v] = df64(0.f, 0.f);
+      df64acc e[2][4], o[2][4];
       const int t1 = min(t0 + 1, NP - 1);
       const df64* te0 = th + (size_t)t0 * KL;
       const df64* te1 = th + (size_t)t1 * KL;
@@ -145,8 +141,8 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_synth_df(DfArgs a) {
         for (int u = 0; u < 2; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            e[u][v] = fma(ae[u], be[v], e[u][v]);
-            o[u][v] = fma(ao[u], bo[v], o[u][v]);
+            e[u][v].add_prod(ae[u], be[v]);
+            o[u][v].add_prod(ao[u], bo[v]);
           }
       }
 #pragma unroll
@@ -158,8 +154,9 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_synth_df(DfArgs a) {
         df64* fb = base + ((size_t)tb * M2 + kap) * kDfSB + s0;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          ft[v] = e[u][v] + o[u][v];
-          if (tb != t) fb[v] = e[u][v] - o[u][v];
+          const df64 ev = e[u][v].value(), ov = o[u][v].value();
+          ft[v] = ev + ov;
+          if (tb != t) fb[v] = ev - ov;
         }
       }
     }
@@ -203,11 +200,7 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
     // class sums at 2 quarter angles x 2 states, folded with W V into the four classes
     for (int ti = threadIdx.x; ti < nsyn; ti += blockDim.x) {
       const int q0 = 2 * (ti / (kDfSB / 2)), s0 = 2 * (ti % (kDfSB / 2));
-      df64 acc[4][2][2];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int u = 0; u < 2; ++u) acc[c][u][0] = acc[c][u][1] = df64(0.f, 0.f);
+      df64acc acc[4][2][2];
       const int q1 = min(q0 + 1, Qn - 1);
       for (int i = 0; i < KC; ++i) {
 #pragma unroll
@@ -219,8 +212,8 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
           const df64 tv[2] = {tt[((size_t)c * Qn + q0) * KC + i], tt[((size_t)c * Qn + q1) * KC + i]};
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            acc[c][u][0] = fma(tv[u], fv[0], acc[c][u][0]);
-            acc[c][u][1] = fma(tv[u], fv[1], acc[c][u][1]);
+            acc[c][u][0].add_prod(tv[u], fv[0]);
+            acc[c][u][1].add_prod(tv[u], fv[1]);
           }
         }
       }
@@ -232,7 +225,8 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
                    w4 = ws[(4 * Q - q) % Np];
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
-          const df64 ce = acc[0][u][v], co = acc[1][u][v], se = acc[2][u][v], so = acc[3][u][v];
+          const df64 ce = acc[0][u][v].value(), co = acc[1][u][v].value();
+          const df64 se = acc[2][u][v].value(), so = acc[3][u][v].value();
           const df64 cp = ce + co, cm = ce - co, sp = se + so, sm = se - so;
           const df64 zero(0.f, 0.f);
           const df64 g1 = w1 * (cp + sp);
@@ -254,11 +248,7 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
       const int c = ti / per_c, rem = ti - c * per_c;
       const int i0 = 2 * (rem / (kDfSB / 4)), s0 = 4 * (rem % (kDfSB / 4));
       const int i1 = min(i0 + 1, KC - 1);
-      df64 acc[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = df64(0.f, 0.f);
+      df64acc acc[2][4];
       const df64* tc = tt + (size_t)c * Qn * KC;
       const df64* hc = hs + (size_t)c * Qn * kDfSB + s0;
       for (int q = 0; q < Qn; ++q) {
@@ -270,7 +260,7 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fma(tv[u], hv[v], acc[u][v]);
+          for (int v = 0; v < 4; ++v) acc[u][v].add_prod(tv[u], hv[v]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -280,7 +270,7 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
         if (kap < 0) continue;
         df64* dst = frow + (size_t)kap * kDfSB + s0;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) dst[v] = acc[u][v];
+        for (int v = 0; v < 4; ++v) dst[v] = acc[u][v].value();
       }
     }
   }
@@ -319,11 +309,7 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_anal_df(DfArgs a) {
       const int i1 = min(i0 + 1, KL - 1);
       const df64* tp = th + (size_t)par * NP * KL;
       const df64* apb = ap + (size_t)par * NP * kDfSB + s0;
-      df64 acc[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = df64(0.f, 0.f);
+      df64acc acc[2][4];
       for (int t = 0; t < NP; ++t) {
         const df64 tv[2] = {tp[(size_t)t * KL + i0], tp[(size_t)t * KL + i1]};
         const float4* p = reinterpret_cast<const float4*>(apb + (size_t)t * kDfSB);
@@ -333,7 +319,7 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_anal_df(DfArgs a) {
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fma(tv[u], hv[v], acc[u][v]);
+          for (int v = 0; v < 4; ++v) acc[u][v].add_prod(tv[u], hv[v]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -341,7 +327,8 @@ __global__ void __launch_bounds__(kDfThreads) k_leg_anal_df(DfArgs a) {
         if (i0 + u >= KL || l > lmax) continue;
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-          if (s0 + v < ns) a.G[((size_t)k * L2 + l * l + l + m) * S + a.s0 + s0 + v] = acc[u][v];
+          if (s0 + v < ns)
+            a.G[((size_t)k * L2 + l * l + l + m) * S + a.s0 + s0 + v] = acc[u][v].value();
       }
     }
   }

@@ -118,6 +118,32 @@ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
   return df64(h, l);
 }
 __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+
+// Accumulator of a sum of df64 products without the per-step renormalisation of fma above:
+// each step adds the exact rounded product p = a.hi b.hi to hi by two_sum (exact), and the
+// product's error terms and two_sum's error to lo; hi + lo is renormalised once, when read.
+// 12 FP32 instructions per multiply-add instead of 15. lo stays small against hi for the short
+// sums it is used for (at most a few hundred terms of table-times-value products), so the
+// result keeps the df64 accuracy.
+struct df64acc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(df64 a, df64 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ df64 value() const {
+    float s, e;
+    two_sum(hi, lo, s, e);
+    return df64(s, e);
+  }
+};
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 
 }  // namespace cs
