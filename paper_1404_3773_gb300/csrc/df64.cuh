@@ -146,4 +146,19 @@ struct df64acc {
 };
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 
+// Multiply-add accumulator over an arithmetic type: a fused multiply-add for float and double,
+// df64acc for df64 (one renormalisation when read).
+template <typename C>
+struct MacAcc {
+  C v = C(0);
+  __device__ __forceinline__ void add_prod(C a, C b) { v = fma(a, b, v); }
+  __device__ __forceinline__ C value() const { return v; }
+};
+template <>
+struct MacAcc<df64> {
+  df64acc a;
+  __device__ __forceinline__ void add_prod(df64 x, df64 y) { a.add_prod(x, y); }
+  __device__ __forceinline__ df64 value() const { return a.value(); }
+};
+
 }  // namespace cs

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
 #include "hx_kernels.cuh"
 
 namespace cs {
@@ -32,11 +33,7 @@ __device__ __forceinline__ void radial_synth_tile(const T* __restrict__ X, long 
   const int L2 = L * L;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  MacAcc<T> acc[4][4];
   const T* radl = rad + (size_t)l * n_r * N;
   for (int n0 = 0; n0 < N; n0 += RBK) {
     for (int idx = tid; idx < RBM * RBK; idx += 256) {
@@ -65,7 +62,7 @@ __device__ __forceinline__ void radial_synth_tile(const T* __restrict__ X, long 
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j].add_prod(a[i], b[j]);
     }
     __syncthreads();
   }
@@ -76,7 +73,7 @@ __device__ __forceinline__ void radial_synth_tile(const T* __restrict__ X, long 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int c = c0 + tx + 16 * j;
-      if (c < ncol) G[((size_t)k * L2 + l * l) * S + c] = acc[i][j];
+      if (c < ncol) G[((size_t)k * L2 + l * l) * S + c] = acc[i][j].value();
     }
   }
 }
@@ -92,11 +89,7 @@ __device__ __forceinline__ void radial_anal_tile(const T* __restrict__ G,
   const int L2 = L * L;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;  // tx -> n, ty -> c
-  T acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  MacAcc<T> acc[4][4];
   const T* radl = rad + (size_t)l * n_r * N;
   for (int k0 = 0; k0 < n_r; k0 += RBK) {
     for (int idx = tid; idx < RBM * RBK; idx += 256) {
@@ -120,7 +113,7 @@ __device__ __forceinline__ void radial_anal_tile(const T* __restrict__ G,
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j].add_prod(a[i], b[j]);
     }
     __syncthreads();
   }
@@ -135,7 +128,7 @@ __device__ __forceinline__ void radial_anal_tile(const T* __restrict__ G,
       if (n >= N) continue;
       size_t a = (size_t)(l * l + mi) * N + n;
       size_t o = a + (size_t)s * ep.ld_out;
-      T z = acc[i][j];
+      T z = acc[i][j].value();
       if (ep.mode == EP_PLAIN) {
         ep.out[o] = z;
         continue;

@@ -66,11 +66,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, l
   __shared__ C As[GK][T + 1];
   __shared__ C Bs[GK][T + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  C acc[U][U];
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-#pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = C(0);
+  MacAcc<C> acc[U][U];
   for (long long rb = r0; rb < r1; rb += GK) {
     for (int idx = tid; idx < GK * T; idx += 256) {
       int rr = idx % GK, cc = idx / GK;
@@ -90,7 +86,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, l
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < U; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v].add_prod(a[u], b[v]);
     }
     __syncthreads();
   }
@@ -100,7 +96,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(const F* __restrict__ A, l
 #pragma unroll
     for (int v = 0; v < U; ++v) {
       int i = i0 + tx + 16 * u, j = j0 + ty + 16 * v;
-      if (i < na && j < nb) P[i + (size_t)j * na] = out_val(acc[u][v]);
+      if (i < na && j < nb) P[i + (size_t)j * na] = out_val(acc[u][v].value());
     }
 }
 
@@ -170,11 +166,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long l
   __shared__ Cm As[GK][BM + 1];  // As[k][r]
   __shared__ Cm Qs[GK][BN + 1];  // Qs[k][j]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  Cm acc[4][U];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < U; ++v) acc[u][v] = Cm(0);
+  MacAcc<Cm> acc[4][U];
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int idx = tid; idx < GK * BM; idx += 256) {
       int rr = idx % BM, kk = idx / BM;
@@ -198,7 +190,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long l
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < U; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v].add_prod(a[u], b[v]);
     }
     __syncthreads();
   }
@@ -211,8 +203,9 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const F* __restrict__ A, long l
       long long r = r0 + tx + 16 * u;
       if (r >= d) continue;
       F* c = C + r + (long long)j * ldc;
-      *c = (beta == F(0)) ? out_val(Cm(alpha) * acc[u][v])
-                          : out_val(fma(Cm(alpha), acc[u][v], Cm(beta) * Cm(*c)));
+      const Cm av = acc[u][v].value();
+      *c = (beta == F(0)) ? out_val(Cm(alpha) * av)
+                          : out_val(fma(Cm(alpha), av, Cm(beta) * Cm(*c)));
     }
   }
 }
