@@ -151,12 +151,17 @@ __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b;
 template <typename C>
 struct MacAcc {
   C v = C(0);
+  __device__ __forceinline__ void set(C x) { v = x; }
   __device__ __forceinline__ void add_prod(C a, C b) { v = fma(a, b, v); }
   __device__ __forceinline__ C value() const { return v; }
 };
 template <>
 struct MacAcc<df64> {
   df64acc a;
+  __device__ __forceinline__ void set(df64 x) {
+    a.hi = x.hi;
+    a.lo = x.lo;
+  }
   __device__ __forceinline__ void add_prod(df64 x, df64 y) { a.add_prod(x, y); }
   __device__ __forceinline__ df64 value() const { return a.value(); }
 };
