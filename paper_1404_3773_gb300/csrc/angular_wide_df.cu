@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
     tt[idx] = v;
   }
   const long long ntiles = (long long)a.n_r * Nt;
-  const int nsyn = ((Qn + 1) / 2) * (kDfSB / 2);   // synthesis tiles: 2 q x 2 states
-  const int nana = 4 * ((KC + 1) / 2) * (kDfSB / 4);  // quadrature tiles: 2 modes x 4 states
+  const int nsyn = ((Qn + 3) / 4) * (kDfSB / 2);   // synthesis tiles: 4 q x 2 states
+  const int nana = 4 * ((KC + 3) / 4) * (kDfSB / 4);  // quadrature tiles: 4 modes x 4 states
   for (long long tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int k = (int)(tl / Nt), t = (int)(tl % Nt);
     df64* frow = a.FA + (size_t)tl * M2 * kDfSB;
@@ -197,11 +197,13 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
       for (int idx = threadIdx.x; idx < Np; idx += blockDim.x) ws[idx] = wvr[idx];
     }
     __syncthreads();
-    // class sums at 2 quarter angles x 2 states, folded with W V into the four classes
+    // class sums at 4 quarter angles x 2 states, folded with W V into the four classes
     for (int ti = threadIdx.x; ti < nsyn; ti += blockDim.x) {
-      const int q0 = 2 * (ti / (kDfSB / 2)), s0 = 2 * (ti % (kDfSB / 2));
-      df64acc acc[4][2][2];
-      const int q1 = min(q0 + 1, Qn - 1);
+      const int q0 = 4 * (ti / (kDfSB / 2)), s0 = 2 * (ti % (kDfSB / 2));
+      df64acc acc[4][4][2];
+      int qq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qq[u] = min(q0 + u, Qn - 1);
       for (int i = 0; i < KC; ++i) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -209,16 +211,17 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
           if (kap < 0) continue;
           const float4 f = *reinterpret_cast<const float4*>(fs + (size_t)kap * kDfSB + s0);
           const df64 fv[2] = {df64(f.x, f.y), df64(f.z, f.w)};
-          const df64 tv[2] = {tt[((size_t)c * Qn + q0) * KC + i], tt[((size_t)c * Qn + q1) * KC + i]};
+          const df64* tc = tt + (size_t)c * Qn * KC + i;
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            acc[c][u][0].add_prod(tv[u], fv[0]);
-            acc[c][u][1].add_prod(tv[u], fv[1]);
+          for (int u = 0; u < 4; ++u) {
+            const df64 tv = tc[(size_t)qq[u] * KC];
+            acc[c][u][0].add_prod(tv, fv[0]);
+            acc[c][u][1].add_prod(tv, fv[1]);
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < 4; ++u) {
         const int q = q0 + u;
         if (q >= Qn) continue;
         const df64 w1 = ws[q], w2 = ws[2 * Q - q], w3 = ws[(2 * Q + q) % Np],
@@ -244,26 +247,29 @@ __global__ void __launch_bounds__(kDfThreads) k_phi_df(DfArgs a) {
     __syncthreads();
     // quadrature per class: AP[kap(c, i)][s] = sum_q T_c[q][i] h_c[q][s]
     for (int ti = threadIdx.x; ti < nana; ti += blockDim.x) {
-      const int per_c = ((KC + 1) / 2) * (kDfSB / 4);
+      const int per_c = ((KC + 3) / 4) * (kDfSB / 4);
       const int c = ti / per_c, rem = ti - c * per_c;
-      const int i0 = 2 * (rem / (kDfSB / 4)), s0 = 4 * (rem % (kDfSB / 4));
-      const int i1 = min(i0 + 1, KC - 1);
-      df64acc acc[2][4];
+      const int i0 = 4 * (rem / (kDfSB / 4)), s0 = 4 * (rem % (kDfSB / 4));
+      int ii[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ii[u] = min(i0 + u, KC - 1);
+      df64acc acc[4][4];
       const df64* tc = tt + (size_t)c * Qn * KC;
       const df64* hc = hs + (size_t)c * Qn * kDfSB + s0;
       for (int q = 0; q < Qn; ++q) {
-        const df64 tv[2] = {tc[(size_t)q * KC + i0], tc[(size_t)q * KC + i1]};
+        const df64* tq = tc + (size_t)q * KC;
+        const df64 tv[4] = {tq[ii[0]], tq[ii[1]], tq[ii[2]], tq[ii[3]]};
         const float4* hp = reinterpret_cast<const float4*>(hc + (size_t)q * kDfSB);
         const float4 h0 = hp[0], h1 = hp[1];
         const df64 hv[4] = {df64(h0.x, h0.y), df64(h0.z, h0.w), df64(h1.x, h1.y),
                             df64(h1.z, h1.w)};
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v].add_prod(tv[u], hv[v]);
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < 4; ++u) {
         const int i = i0 + u;
         if (i >= KC) continue;
         const int kap = df_class_kap(c, i, lmax);
