@@ -1018,11 +1018,29 @@ def batched_measure(dev, reps=2):
         cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_MIXED_BF16, work_m)
     torch.cuda.synchronize()
     same_m = all(torch.equal(p, q) for p, q in zip(Y5, Y6))
+    # where the sequential time goes: each cluster's mixed filter alone (CUDA events), sorted.
+    # Overlapping clusters can hide only the time of those that leave the GPU idle; the largest
+    # ones fill it alone, so their share bounds what batching can gain.
+    per = []
+    for c, y, w, aa, bb, aa0 in zip(ctxs, Ys, ws, a, b, a0):
+        e0.record(stream)
+        cs.cs_cheb_filter(c, y, degree, aa, bb, aa0, cs.CS_MIXED_BF16, work_m)
+        e1.record(stream)
+        e1.synchronize()
+        per.append((e0.elapsed_time(e1), w.n_s, w.lmax))
+    per.sort(reverse=True)
+    tot = sum(p[0] for p in per)
+    shares = {f"largest_{k}": round(sum(p[0] for p in per[:k]) / tot, 3) for k in (8, 16, 32)}
+    mixed_clusters = {"sequential_ms_sum": round(tot, 3), "time_share": shares,
+                      "largest_ms": [round(p[0], 3) for p in per[:8]],
+                      "largest_n_s_lmax": [[p[1], p[2]] for p in per[:8]],
+                      "median_ms": round(per[len(per) // 2][0], 3)}
     mixed = {"applies_per_s": round(cols / (t_bm / 1e3), 1),
              "sequential_applies_per_s": round(cols / (t_sm / 1e3), 1),
              "speedup_vs_sequential": round(t_sm / t_bm, 3),
              "filter_ms": round(t_bm, 3), "sequential_filter_ms": round(t_sm, 3),
-             "variant": "concurrent", "bitwise_equal_to_sequential": bool(same_m)}
+             "variant": "concurrent", "bitwise_equal_to_sequential": bool(same_m),
+             "clusters": mixed_clusters}
     return {"workload": "96 erf clusters (4-48 atoms, R 8-16, lmax 12-32, N 24-56, "
                         f"{sum(w.n_s for w in ws)} states in total), FP32 degree-{degree} filter",
             "applies_per_s": round(cols / (t_batch / 1e3), 1),
