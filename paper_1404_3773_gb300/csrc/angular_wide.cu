@@ -761,6 +761,11 @@ cudaError_t launch_angular_wide(const AngArgs<float>& a, const void* tab, float*
   // Legendre passes: one CTA per (block, k, range of modes), about 6 CTAs per SM in all
   const int base = w.nblk * a.n_r;
   int nmr = (6 * nsm + base - 1) / base;
+  // CS_WIDE_CTAS_PER_SM overrides the 6 CTAs per SM of the Legendre passes (for tuning)
+  if (const char* e6 = getenv("CS_WIDE_CTAS_PER_SM")) {
+    const int v = atoi(e6);
+    if (v > 0 && v <= 64) nmr = (v * nsm + base - 1) / base;
+  }
   if (nmr < 1) nmr = 1;
   if (nmr > s.M2) nmr = s.M2;
   w.nmr = nmr;
