@@ -841,6 +841,13 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
         cs.cs_mlp_train_step(net, Xd, Td, 1e-3, want_loss=False)
     loss = cs.cs_mlp_loss_grad(net, Xd, Td)[0]
     train_s = time.perf_counter() - t0
+    # the same loss on the validation clusters' centres (not trained on)
+    Dv, Cv = D_all[n_fit_centres:], C_all[n_fit_centres:]
+    val_loss = None
+    if Dv.shape[0] > 0:
+        Xv = torch.tensor(((Dv - d_mean) / d_std).T.copy(), dtype=torch.float32, device=dev)
+        Tv = torch.tensor((Cv / c_scale).T.copy(), dtype=torch.float32, device=dev)
+        val_loss = cs.cs_mlp_loss_grad(net, Xv, Tv)[0]
     def learned_start(atoms, start, alpha):
         """(density, accepted): start + alpha * prediction, clipped at 0, renormalised"""
         ne = 4.0 * len(atoms)
@@ -901,7 +908,7 @@ def learned_init_measure(dev, n_train=160, n_test=40, tol=1e-6, hidden=128, step
                         f"|dE| <= {tol:g} Ha; correction on atoms and on bond midpoints "
                         f"(pairs closer than {rcut:g} bohr)",
             "train_centres": int(D.shape[0]), "train_bond_centres": int(n_bonds),
-            "train_loss_first": loss0, "train_loss_final": loss,
+            "train_loss_first": loss0, "train_loss_final": loss, "validation_loss": val_loss,
             "train_seconds": round(train_s, 3),
             "held_out_mean_iterations_gaussian_start": float(np.mean(it_g)),
             "held_out_mean_iterations_learned_start": float(np.mean(it_l)),
