@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <utility>
 
 #include "df64.cuh"
@@ -1424,7 +1425,14 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
   double* lam = Ep + n2;          // n
   double* scal = lam + n;         // 4
   double* scratch = scal + 4;     // 2 n^2 + 2 n (final step)
-  const int threads = 256;
+  // threads of the one-CTA FP32 stage: 512 measured fastest at n = 80 (1.55 ms per Rayleigh-Ritz
+  // dense part against 1.65 at 256, 1.90 at 128, 1.56 at 1024; the same Ritz values);
+  // CS_EIG_THREADS (a multiple of 32, up to 1024) overrides
+  int threads = 512;
+  if (const char* et = getenv("CS_EIG_THREADS")) {
+    const int v = atoi(et);
+    if (v >= 32 && v <= 1024 && v % 32 == 0) threads = v;
+  }
   // 1. FP32 eigendecomposition of sym(A) -> V0 (FP64 copy of the FP32 vectors)
   cudaError_t e;
   const size_t smem_b = (4 * n2 + 7 * (size_t)n) * sizeof(float);
