@@ -457,9 +457,9 @@ cudaError_t dense_gram(const cs_ctx* c, const double* A, long long lda, const do
 }
 cudaError_t dense_rotate(const cs_ctx* c, const double* A, long long lda, const double* Q, int ldq,
                          long long d, int k, int n, double* C, long long ldc, cudaStream_t st,
-                         void* oz) {
+                         void* oz, bool upper = false) {
   if (c->dense_prec == CS_FP64_SLICED)
-    return launch_oz_rotate(A, lda, Q, ldq, d, k, n, C, ldc, oz, c->dev_err, st);
+    return launch_oz_rotate(A, lda, Q, ldq, d, k, n, C, ldc, oz, c->dev_err, st, upper);
   return c->dense_prec == CS_DF64
              ? launch_gemm_nn_df(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st)
              : launch_gemm_nn<double>(A, lda, Q, ldq, d, k, n, 1.0, 0.0, C, ldc, st);
@@ -478,7 +478,8 @@ cs_status cholqr_core(cs_ctx* c, int n_s, double* X, long long ld, char* work, c
   for (int pass = 0; pass < 2; ++pass) {
     CS_LAUNCH(c, 2, dense_gram(c, X, ld, X, ld, H.d, n_s, n_s, M, n_s, part, st, oz));
     CS_LAUNCH(c, 1, launch_cholqr_factor(M, n_s, U, w, status_dev + pass, st));
-    CS_LAUNCH(c, 1, dense_rotate(c, X, ld, U, n_s, H.d, n_s, n_s, tmp, H.d, st, oz));
+    // U = R^-1 is upper triangular with its lower part stored as zeros
+    CS_LAUNCH(c, 1, dense_rotate(c, X, ld, U, n_s, H.d, n_s, n_s, tmp, H.d, st, oz, true));
     CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   }
   return CS_OK;
@@ -525,7 +526,14 @@ cs_status rr_core(cs_ctx* c, int n_s, double* X, long long ld, double* theta, do
   if (r != CS_OK) return r;
   void* oz = work + lay.oz;
   CS_LAUNCH(c, 2, dense_gram(c, X, ld, HX, H.d, H.d, n_s, n_s, Hs, n_s, part, st, oz));
-  CS_LAUNCH(c, 1, launch_sym_eig(Hs, n_s, theta, Q, jw, status_dev, st));
+  // with slice-product dense steps the eigensolver's refinement products may use them too
+  // (the workspace slot holds at least the d x n_s products' split operands)
+  const bool sl = c->dense_prec == CS_FP64_SLICED;
+  const size_t ozb = sl ? std::max(oz_gram_work_bytes(H.d, n_s, n_s, false),
+                                   oz_rotate_work_bytes(H.d, n_s, n_s))
+                        : 0;
+  CS_LAUNCH(c, 1, launch_sym_eig(Hs, n_s, theta, Q, jw, status_dev, st, sl ? oz : nullptr, ozb,
+                                 c->dev_err));
   CS_LAUNCH(c, 1, dense_rotate(c, X, ld, Q, n_s, H.d, n_s, n_s, tmp, H.d, st, oz));
   CS_LAUNCH(c, 1, launch_copy_block<double>(tmp, H.d, X, ld, H.d, n_s, st));
   // H X Q straight into HX_out when the caller keeps it, else into tmp

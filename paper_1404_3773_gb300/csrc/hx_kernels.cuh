@@ -160,8 +160,11 @@ cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work
 // bisection tiles do not fit in shared memory), Newton-Schulz re-orthonormalisation and
 // Ogita-Aishima refinement in FP64, exact FP64 Jacobi inside clusters of near-equal values.
 // work: 8n^2 + 3n + 4 doubles. status[0] = 1, or negative if a step did not converge.
+// oz (oz_bytes), oz_err: optional slice-product workspace and its error word; with them the
+// FP64 refinement products of large blocks run as slice products (launch_oz_gram/rotate).
 cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, double* work,
-                              int* status, cudaStream_t stream);
+                              int* status, cudaStream_t stream, void* oz = nullptr,
+                              size_t oz_bytes = 0, int* oz_err = nullptr);
 // resid[i] = || HX[:, i] - theta[i] X[:, i] ||_2
 cudaError_t launch_residuals(const double* X, long long ldx, const double* HX, long long ldh,
                              long long d, int n, const double* theta, double* resid,
@@ -210,11 +213,12 @@ size_t oz_gram_work_bytes(long long d, int na, int nb, bool same);
 cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long long ldb,
                            long long d, int na, int nb, double* C, int ldc, void* work, int* err,
                            cudaStream_t stream);
-// Rotation C (d x n, ldc) = A (d x k, lda) Q (k x n, ldq). A must not overlap C.
+// Rotation C (d x n, ldc) = A (d x k, lda) Q (k x n, ldq). A must not overlap C. `upper`: Q is
+// upper triangular (zeros stored below the diagonal), so each tile skips the zero rows.
 size_t oz_rotate_work_bytes(long long d, int k, int n);
 cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, int ldq,
                              long long d, int k, int n, double* C, long long ldc, void* work,
-                             int* err, cudaStream_t stream);
+                             int* err, cudaStream_t stream, bool upper = false);
 // Lanczos tridiagonal T (k x k) from alpha[k] and the squared off-diagonals beta2[k-1]
 cudaError_t launch_build_tridiag(const double* alpha, const double* beta2, int k, double* T,
                                  cudaStream_t stream);

@@ -866,23 +866,25 @@ __global__ void __launch_bounds__(1024) k_sym_eig(const double* __restrict__ Ain
 // All FP64 work here is wide (n x n GEMM tiles over many CTAs), which matters on a GPU
 // whose FP64 pipe is narrow: the FP32 factorisation carries the long serial chains.
 
-// C (n x n) = op(A) B, op(A) = A^T if TA; 16 x 16 output tiles, one element per thread
-template <bool TA>
-__global__ void __launch_bounds__(256) k_small_gemm(const double* __restrict__ A,
-                                                     const double* __restrict__ B, int n,
-                                                     double* __restrict__ C) {
-  __shared__ double As[16][17], Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+// C (n x n) = op(A) B, op(A) = A^T if TA; T x T output tiles, one element per thread. The FP64
+// pipe of one SM is narrow, so n <= 256 takes 8 x 8 tiles: at n = 80 that spreads the work over
+// 100 CTAs instead of 25 (16 x 16 tiles).
+template <bool TA, int T>
+__global__ void __launch_bounds__(T * T) k_small_gemm(const double* __restrict__ A,
+                                                       const double* __restrict__ B, int n,
+                                                       double* __restrict__ C) {
+  __shared__ double As[T][T + 1], Bs[T][T + 1];
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int i = blockIdx.x * T + tx, j = blockIdx.y * T + ty;
   double acc = 0.0;
-  for (int k0 = 0; k0 < n; k0 += 16) {
+  for (int k0 = 0; k0 < n; k0 += T) {
     const int ka = k0 + ty, kb = k0 + tx;
     // As[kk][ii] = op(A)[i][k], Bs[kk][jj] = B[k][j]
     As[ty][tx] = (i < n && ka < n) ? (TA ? A[ka + (size_t)i * n] : A[i + (size_t)ka * n]) : 0.0;
     Bs[tx][ty] = (j < n && kb < n) ? B[kb + (size_t)j * n] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+    for (int kk = 0; kk < T; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
     __syncthreads();
   }
   if (i < n && j < n) C[i + (size_t)j * n] = acc;
@@ -890,9 +892,15 @@ __global__ void __launch_bounds__(256) k_small_gemm(const double* __restrict__ A
 
 static cudaError_t small_gemm(bool ta, const double* A, const double* B, int n, double* C,
                               cudaStream_t st) {
-  dim3 grid((n + 15) / 16, (n + 15) / 16);
-  if (ta) k_small_gemm<true><<<grid, 256, 0, st>>>(A, B, n, C);
-  else k_small_gemm<false><<<grid, 256, 0, st>>>(A, B, n, C);
+  if (n <= 256) {
+    dim3 grid((n + 7) / 8, (n + 7) / 8);
+    if (ta) k_small_gemm<true, 8><<<grid, 64, 0, st>>>(A, B, n, C);
+    else k_small_gemm<false, 8><<<grid, 64, 0, st>>>(A, B, n, C);
+  } else {
+    dim3 grid((n + 15) / 16, (n + 15) / 16);
+    if (ta) k_small_gemm<true, 16><<<grid, 256, 0, st>>>(A, B, n, C);
+    else k_small_gemm<false, 16><<<grid, 256, 0, st>>>(A, B, n, C);
+  }
   return cudaGetLastError();
 }
 
@@ -1414,7 +1422,8 @@ cudaError_t le_stage(const double* Ain, int n, double* big, double* vec, double*
 }  // namespace
 
 cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, double* work,
-                              int* status, cudaStream_t stream) {
+                              int* status, cudaStream_t stream, void* oz, size_t oz_bytes,
+                              int* oz_err) {
   const size_t n2 = (size_t)n * n;
   double* V0 = work;
   double* V1 = V0 + n2;
@@ -1448,27 +1457,39 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
     // refinement); status as the one-CTA solver's
     if ((e = le_stage(A, n, P, Ep, V0, status, stream)) != cudaSuccess) return e;
   }
-  // 2. orthonormalise to FP64 precision (Newton-Schulz), then refine in FP64
+  // 2. orthonormalise to FP64 precision (Newton-Schulz), then refine in FP64. The 25 n x n
+  // products take the FP64 pipe (small_gemm) or, for large n when the caller hands over a
+  // slice-product workspace, the exact slice products on the tensor cores: at n = 880 one
+  // FP64-pipe product is about 1.1 ms at the pipe's peak
+  const bool sliced = oz != nullptr && oz_err != nullptr && n > 256 &&
+                      oz_gram_work_bytes(n, n, n, false) <= oz_bytes &&
+                      oz_rotate_work_bytes(n, n, n) <= oz_bytes;
+  // C = X^T Y (ta) or X Y, all n x n with leading dimension n
+  auto prod = [&](bool ta, const double* X, const double* Y, double* C) -> cudaError_t {
+    if (!sliced) return small_gemm(ta, X, Y, n, C, stream);
+    return ta ? launch_oz_gram(X, n, Y, n, n, n, n, C, n, oz, oz_err, stream)
+              : launch_oz_rotate(X, n, Y, n, n, n, n, C, n, oz, oz_err, stream);
+  };
   double* Vc = V0;
   double* Vn = V1;
   for (int it = 0; it < 3; ++it) {
-    if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;   // G = V^T V
+    if ((e = prod(true, Vc, Vc, G)) != cudaSuccess) return e;   // G = V^T V
     k_ns_factor<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(G, n, Ep);
-    if ((e = small_gemm(false, Vc, Ep, n, Vn, stream)) != cudaSuccess) return e;
+    if ((e = prod(false, Vc, Ep, Vn)) != cudaSuccess) return e;
     std::swap(Vc, Vn);
   }
   for (int it = 0; it < 4; ++it) {
-    if ((e = small_gemm(false, A, Vc, n, P, stream)) != cudaSuccess) return e;   // P = A V
-    if ((e = small_gemm(true, Vc, P, n, S, stream)) != cudaSuccess) return e;    // S = V^T A V
-    if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;   // G = V^T V
+    if ((e = prod(false, A, Vc, P)) != cudaSuccess) return e;   // P = A V
+    if ((e = prod(true, Vc, P, S)) != cudaSuccess) return e;    // S = V^T A V
+    if ((e = prod(true, Vc, Vc, G)) != cudaSuccess) return e;   // G = V^T V
     k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
     k_oa_update<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(S, G, n, lam, scal, Ep);
-    if ((e = small_gemm(false, Vc, Ep, n, Vn, stream)) != cudaSuccess) return e;  // V (I + E)
+    if ((e = prod(false, Vc, Ep, Vn)) != cudaSuccess) return e;  // V (I + E)
     std::swap(Vc, Vn);
   }
-  if ((e = small_gemm(false, A, Vc, n, P, stream)) != cudaSuccess) return e;
-  if ((e = small_gemm(true, Vc, P, n, S, stream)) != cudaSuccess) return e;
-  if ((e = small_gemm(true, Vc, Vc, n, G, stream)) != cudaSuccess) return e;
+  if ((e = prod(false, A, Vc, P)) != cudaSuccess) return e;
+  if ((e = prod(true, Vc, P, S)) != cudaSuccess) return e;
+  if ((e = prod(true, Vc, Vc, G)) != cudaSuccess) return e;
   k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
   // 3. sort, clusters, output
   k_oa_final<<<1, 1024, 0, stream>>>(S, G, Vc, n, scal, theta, V, scratch, status);

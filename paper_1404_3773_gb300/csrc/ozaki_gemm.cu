@@ -75,6 +75,9 @@ struct OzArgs {
   int* part;
   long long Mp, Np;
   int* err;
+  int sym;     // A and B are one block: only tiles that reach the upper triangle, mirrored
+  int upper;   // B is upper triangular: a tile's K range ends at its last column
+  int n_fast;  // grid x runs over the B-side tiles (the CTAs of one A tile run together)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -87,10 +90,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
   __shared__ uint32_t tmem_base_sh;
   __shared__ int flag_sh, issued_sh, consumed_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long mt = blockIdx.x;
-  const int nt = blockIdx.y, z = blockIdx.z;
+  const long long mt = g.n_fast ? blockIdx.y : blockIdx.x;
+  const int nt = g.n_fast ? blockIdx.x : blockIdx.y, z = blockIdx.z;
+  // C = A^T A: a tile wholly below the diagonal is the mirror of one above it (the exact sum
+  // of C[i][j] and of C[j][i] is one number), written by that tile
+  if (g.sym && mt * kTM > (long long)nt * kTN + kTN - 1) return;
+  // upper-triangular B: rows past the tile's last column are zero, their digits add nothing
+  const long long kc =
+      g.upper ? min(g.kchunks, ((long long)nt * kTN + kTN + kKC - 1) / kKC) : g.kchunks;
   const long long c0 = (long long)z * g.wins_per_cta * kChunksPerWin;
-  const long long c1 = min(g.kchunks, c0 + (long long)g.wins_per_cta * kChunksPerWin);
+  const long long c1 = min(kc, c0 + (long long)g.wins_per_cta * kChunksPerWin);
   const int nk = (int)max(0ll, c1 - c0);
   const int nw = (nk + kChunksPerWin - 1) / kChunksPerWin;
   if (tid == 0) {
@@ -260,14 +269,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
 #pragma unroll
       for (int c = 0; c < H; ++c) {
         const long long j = (long long)nt * kTN + (low ? c : H + c);
-        if (j < g.N) {
+        if (j < g.N && (!g.sym || i <= j)) {
           int64_t D[kS];
 #pragma unroll
           for (int tt = 0; tt < 4; ++tt) {
             D[tt] = low ? acc[tt][c] : lo_part[(tt * H + c) * kTM + r];
             D[4 + tt] = low ? hi_part[(tt * H + c) * kTM + r] : acc[tt][H + c];
           }
-          g.C[i + j * g.ldc] = oz_combine(D, ea, g.EB[j], kBeta, kS);
+          const double v = oz_combine(D, ea, g.EB[j], kBeta, kS);
+          g.C[i + j * g.ldc] = v;
+          if (g.sym && i < j) g.C[j + i * g.ldc] = v;
         }
       }
     }
@@ -280,16 +291,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_mma(OzArgs g) {
 // D[t] summed over the K groups in 64-bit integers, then combined: C[i + j ldc]. One CTA of 8
 // warps per 32 consecutive outputs i of one column j: warp w sums the groups w, w + 8, ...
 // (lanes on consecutive i: coalesced rows of the partials), the 8 warps' sums are added in
-// shared memory, and warp 0 combines.
+// shared memory, and warp 0 combines. With sym (C = A^T A, product tiles below the diagonal
+// skipped) only i <= j is combined and C[j + i ldc] receives the same value; the partials read
+// then all come from computed tiles (i0 <= j puts rows i0 .. i0 + 31 in a tile that reaches
+// column j).
 __global__ void __launch_bounds__(256) k_oz_reduce(const int* __restrict__ part, int groups,
                                                    long long Mp, long long Np, long long M, int N,
                                                    const int* __restrict__ EA,
                                                    const int* __restrict__ EB,
-                                                   double* __restrict__ C, long long ldc) {
+                                                   double* __restrict__ C, long long ldc,
+                                                   int sym) {
   __shared__ long long acc_sh[8][kS][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long tiles_i = (M + 31) / 32;
   const long long i0 = (blockIdx.x % tiles_i) * 32, j = blockIdx.x / tiles_i;
+  if (sym && i0 > j) return;
   const long long i = i0 + lane;  // < Mp: the padded rows of the partials exist
   int64_t D[kS];
 #pragma unroll
@@ -307,7 +323,11 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const int* __restrict__ part,
       for (int w = 0; w < 8; ++w) t += acc_sh[w][d][lane];
       D[d] = t;
     }
-    if (i < M) C[i + j * ldc] = oz_combine(D, EA[i], EB[j], kBeta, kS);
+    if (i < M && (!sym || i <= j)) {
+      const double v = oz_combine(D, EA[i], EB[j], kBeta, kS);
+      C[i + j * ldc] = v;
+      if (sym && i < j) C[j + i * ldc] = v;
+    }
   }
 }
 
@@ -456,7 +476,7 @@ OzPlan plan(long long K, long long M, long long N, bool gram, bool same) {
 
 cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B, const int* EA,
                 const int* EB, long long M, int N, double* C, long long ldc, int* part,
-                int* err, cudaStream_t st) {
+                int* err, cudaStream_t st, bool sym, bool upper, bool n_fast) {
   cudaError_t e = cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmem);
   if (e != cudaSuccess) return e;
@@ -477,13 +497,18 @@ cudaError_t run(const OzPlan& p, const unsigned char* A, const unsigned char* B,
   g.Mp = p.mpad;
   g.Np = p.npad;
   g.err = err;
-  dim3 grid((unsigned)(p.mpad / kTM), (unsigned)(rup(N, kTN) / kTN), (unsigned)p.groups);
+  g.sym = sym;
+  g.upper = upper;
+  const long long mtiles = p.mpad / kTM, ntiles = rup(N, kTN) / kTN;
+  g.n_fast = n_fast && mtiles <= 65535;
+  const dim3 grid = g.n_fast ? dim3((unsigned)ntiles, (unsigned)mtiles, (unsigned)p.groups)
+                             : dim3((unsigned)mtiles, (unsigned)ntiles, (unsigned)p.groups);
   k_oz_mma<<<grid, kThreads, kSmem, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p.groups > 1) {
     const long long blocks = ((M + 31) / 32) * (long long)N;
     k_oz_reduce<<<(unsigned)blocks, 256, 0, st>>>(part, (int)p.groups, p.mpad, p.npad, M, N, EA,
-                                                  EB, C, ldc);
+                                                  EB, C, ldc, sym ? 1 : 0);
     e = cudaGetLastError();
   }
   return e;
@@ -542,12 +567,13 @@ cudaError_t launch_oz_gram(const double* A, long long lda, const double* B, long
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run(p, sa, sb, EA, EB, na, nb, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st);
+  return run(p, sa, sb, EA, EB, na, nb, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st,
+             same, false, false);
 }
 
 cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, int ldq,
                              long long d, int k, int n, double* C, long long ldc, void* work,
-                             int* err, cudaStream_t st) {
+                             int* err, cudaStream_t st, bool upper) {
   const OzPlan p = plan(k, d, n, false, false);
   unsigned char* w = static_cast<unsigned char*>(work);
   int* EA = reinterpret_cast<int*>(w + p.offEA);
@@ -567,7 +593,10 @@ cudaError_t launch_oz_rotate(const double* A, long long lda, const double* Q, in
                                                                 sb, kTN, nullptr, kTN, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run(p, sa, sb, EA, EB, d, n, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st);
+  // the B-side tiles of one A tile run next to each other: the split A (d x k x 8 digits, far
+  // above L2 at large d) then comes from HBM once instead of once per B-side tile
+  return run(p, sa, sb, EA, EB, d, n, C, ldc, reinterpret_cast<int*>(w + p.offP), err, st,
+             false, upper, true);
 }
 
 }  // namespace cs

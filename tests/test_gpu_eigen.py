@@ -76,13 +76,18 @@ def test_cholqr_matches_oracle():
     assert np.max(np.abs(got - ref)) < 1e-10
 
 
+@pytest.mark.parametrize("dense", ["fp64", "sliced"])
 @pytest.mark.parametrize("n_s", [200, 333])
-def test_cholqr_large_block_matches_oracle(n_s):
+def test_cholqr_large_block_matches_oracle(n_s, dense):
     """Blocks whose Cholesky factor does not fit one CTA's shared memory take the blocked
     factor (panels of 32 columns, trailing updates over the GPU); 333 states leave a ragged
-    last panel. Column norms spread over 4 decades."""
+    last panel. Column norms spread over 4 decades. With slice-product dense steps the Gram
+    matrix X^T X is computed on the tiles that reach its upper triangle and mirrored, and the
+    rotation by the upper-triangular R^-1 stops each tile's contraction at its last column."""
     torch, cs = need_gpu()
     ctx = make_ctx(HO)
+    if dense == "sliced":
+        cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
     rng = np.random.default_rng(81)
     X = rng.standard_normal((ctx.d, n_s)) @ np.diag(np.logspace(0, 4, n_s))
     ref = eigen.cholqr(X)
@@ -92,6 +97,7 @@ def test_cholqr_large_block_matches_oracle(n_s):
     got = to_host(Xd, ctx.d)
     assert np.max(np.abs(got.T @ got - np.eye(n_s))) < 1e-13
     assert np.max(np.abs(got - ref)) < 1e-10
+    assert cs.cs_device_error(ctx) == 0
 
 
 def test_cholqr_large_block_rank_deficient_reports_breakdown():
@@ -359,13 +365,18 @@ def test_chfsi_mixed_filter_meets_eigenvalue_gate():
     assert dev < 1e-6, dev
 
 
-def test_rayleigh_ritz_large_block_matches_oracle():
+@pytest.mark.parametrize("dense", ["fp64", "sliced"])
+def test_rayleigh_ritz_large_block_matches_oracle(dense):
     """A 300-state block (the projected matrix's tridiagonal solve no longer fits one CTA's
     shared memory, so the device-wide FP32 stage runs before the FP64 refinement): Ritz values
-    and residual norms against the oracle's Rayleigh-Ritz, on the oscillator basis (d = 1936)."""
+    and residual norms against the oracle's Rayleigh-Ritz, on the oscillator basis (d = 1936).
+    With slice-product dense steps the Gram matrix, the rotations and the refinement's 300 x 300
+    products (above 256 states) are slice products on the tensor cores."""
     torch, cs = need_gpu()
     w = HO
     ctx = make_ctx(w)
+    if dense == "sliced":
+        cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
     Hh = oracle_H(w.name)
     X = eigen.cholqr(W.gaussian_block(4300, ctx.d, 300))
     th_ref, X_ref, _, res_ref = eigen.rayleigh_ritz(Hh.apply, X)
@@ -381,3 +392,4 @@ def test_rayleigh_ritz_large_block_matches_oracle():
     assert np.max(np.abs(resid.cpu().numpy() - res_ref)) < 1e-10 * np.abs(res_ref).max()
     got = to_host(Xd, ctx.d)
     assert np.max(np.abs(got.T @ got - np.eye(300))) < 1e-12
+    assert cs.cs_device_error(ctx) == 0

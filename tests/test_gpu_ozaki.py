@@ -52,11 +52,14 @@ def _gram(torch, cs, ctx, A, B):
 
 @pytest.mark.parametrize("shape", [(46128, 80, 80, True), (46128, 80, 80, False),
                                    (392, 13, 13, True), (1936, 37, 5, False),
-                                   (1936, 130, 70, False)])
+                                   (1936, 130, 70, False), (392, 200, 200, True),
+                                   (1936, 300, 300, True)])
 def test_slice_gram_matches_oracle_bit_for_bit(shape):
     """X^T X and X^T Y of the 32-atom cluster's size (91 windows of 512 rows, K split over
     CTAs, partial sums added in 64-bit integers), one window (the single-pass path), and
-    ragged shapes with several tiles on both sides."""
+    ragged shapes with several tiles on both sides. X^T X computes only the tiles that reach
+    its upper triangle and mirrors them: 200 and 300 columns skip tiles, in the single-pass
+    path (one window) and in the K-split path (four windows)."""
     torch, cs = need_gpu()
     d, na, nb, same = shape
     ctx = _ctx_for(d)
