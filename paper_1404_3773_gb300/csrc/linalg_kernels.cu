@@ -947,6 +947,64 @@ __global__ void __launch_bounds__(1024) k_oa_norms(const double* __restrict__ A,
   }
 }
 
+// The same norms over the whole GPU for large n (one CTA reads the three n x n matrices at a
+// few tens of GB/s: 1 ms at n = 880): per-CTA partial sums part[q * gridDim + b], in a fixed
+// order, then one CTA adds them in CTA order (deterministic for a given grid)
+__global__ void __launch_bounds__(256) k_oa_norms_part(const double* __restrict__ A,
+                                                       const double* __restrict__ S,
+                                                       const double* __restrict__ G, int n,
+                                                       double* __restrict__ lam,
+                                                       double* __restrict__ part) {
+  __shared__ double red[3][8];
+  const int tid = threadIdx.x;
+  const long long n2 = (long long)n * n;
+  double a2 = 0.0, s2 = 0.0, r2 = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < n2;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const double a = A[e];
+    double sv = S[e], rv = -G[e];
+    if (i == j) {
+      const double l = S[e] / G[e];
+      lam[i] = l;
+      sv -= l;
+      rv += 1.0;
+    }
+    a2 += a * a;
+    s2 += sv * sv;
+    r2 += rv * rv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = a2;
+    red[1][tid >> 5] = s2;
+    red[2][tid >> 5] = r2;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[tid][w];
+    part[(size_t)tid * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_oa_norms_fin(const double* __restrict__ part, int nb,
+                                                     double* __restrict__ scal) {
+  if (threadIdx.x != 0) return;
+  double t[3];
+  for (int q = 0; q < 3; ++q) {
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += part[(size_t)q * nb + b];
+    t[q] = v;
+  }
+  scal[1] = sqrt(t[0]);
+  scal[0] = 2.0 * (sqrt(t[1]) + sqrt(t[0]) * sqrt(t[2]));
+}
+
 // M = 1.5 I - 0.5 G (Newton-Schulz factor), grid over elements
 __global__ void k_ns_factor(const double* __restrict__ G, int n, double* __restrict__ M) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1008,11 +1066,15 @@ __global__ void __launch_bounds__(1024) k_oa_final(const double* __restrict__ S,
     for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, red[w]);
     dc_sh = fmax(scal[0], 1e3 * m);
   }
+  // the unsorted Rayleigh quotients go through theta (overwritten with the sorted values at the
+  // end): n divisions instead of one per pair, which cost milliseconds on one SM at n = 880
+  for (int i = tid; i < n; i += nt) theta[i] = S[i + (size_t)i * n] / G[i + (size_t)i * n];
+  __syncthreads();
   for (int i = tid; i < n; i += nt) {
-    const double vi = S[i + (size_t)i * n] / G[i + (size_t)i * n];
+    const double vi = theta[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double vj = S[j + (size_t)j * n] / G[j + (size_t)j * n];
+      const double vj = theta[j];
       rank += (vj < vi) || (vj == vi && j < i);
     }
     lam[rank] = vi;
@@ -1110,14 +1172,14 @@ __global__ void __launch_bounds__(1024) k_oa_final(const double* __restrict__ S,
 }
 
 // ------------------------------------------------------------------ large-n first stage
-// For blocks whose tridiagonal solve does not fit one CTA's shared memory (n above ~220; the
+// For blocks whose tridiagonal solve does not fit one CTA's shared memory (n above 112; the
 // 880-state block of the 400-atom cluster) the first stage runs in FP64 as a sequence of
-// device-wide kernels on global (L2-resident) arrays instead of one CTA: per Householder step a
-// reflector kernel (one CTA), p = A v with one warp per row (the trailing block is symmetric,
-// so each warp reads a contiguous column), w = p - (v.p) v (one CTA) and the rank-2 update;
-// then bisection and inverse iteration with one thread per eigenvalue (as in the one-CTA
-// solver), Gram-Schmidt inside clusters (one CTA), and the reflectors applied to the
-// eigenvector block one per kernel, one warp per column. FP64 here (not FP32 as in the small
+// device-wide kernels on global (L2-resident) arrays instead of one CTA: two launches per
+// Householder step (the reflector, recomputed per CTA, with p = A v, one warp per row: the
+// trailing block is symmetric, so each warp reads a contiguous column; then w = p - (v.p) v,
+// recomputed per CTA, with the rank-2 update); then multisection and inverse iteration with
+// one warp per eigenvalue, Gram-Schmidt inside clusters (one CTA), and all reflectors applied
+// to the eigenvector block in one launch, one warp per column. FP64 here (not FP32 as in the small
 // solver): in a dense band of eigenvalues (gaps near 1e-4 of the spectral range) FP32 vectors
 // leave couplings that the refinement cannot resolve pair by pair, and the cluster step would
 // then diagonalise most of the band on one thread.
@@ -1168,65 +1230,74 @@ __global__ void k_le_init(const double* __restrict__ Ain, int n, T* __restrict__
   A[idx] = (T)(0.5 * (Ain[i + (size_t)j * n] + Ain[j + (size_t)i * n]));
 }
 
-// reflector of step k: v (unit) into vv and into column k below the diagonal; alpha into e[k]
+// One step k of the Householder reduction in two launches (a grid-wide result that is cheap
+// to recompute is recomputed per CTA instead of taking a launch of its own):
+//  part 1: every CTA forms the reflector v of column k in shared memory (the norm by a block
+//  reduction that takes the same order in every CTA, so all CTAs hold the same v); CTA 0
+//  publishes v (vv) and e[k]; warp i of the grid forms pw[i] = sum_j A[k+1+j, k+1+i] v[j].
+//  Column k keeps x until part 2, because other CTAs still read it.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_le_reflector(T* __restrict__ A, int n, int k,
-                                                       T* __restrict__ vv, T* __restrict__ e) {
+__global__ void __launch_bounds__(256) k_le_house_matvec(const T* __restrict__ A, int n, int k,
+                                                         T* __restrict__ vv, T* __restrict__ pw,
+                                                         T* __restrict__ e) {
+  extern __shared__ __align__(16) unsigned char le_sm[];
+  T* vs = reinterpret_cast<T*>(le_sm);  // m values
   __shared__ T red[32];
   const int m = n - k - 1;
-  T* col = A + (k + 1) + (size_t)k * n;
+  const T* col = A + (k + 1) + (size_t)k * n;
   T xs = T(0);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) xs += col[i] * col[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T c = col[i];
+    vs[i] = c;
+    xs += c * c;
+  }
   const T xnorm = sqrt(le_block_sum(xs, red));
   const T x0 = col[0];
   const T alpha = (x0 >= T(0)) ? -xnorm : xnorm;
   const T vnorm2 = T(2) * (xnorm * xnorm - alpha * x0);
   const bool skip = !(vnorm2 > T(0));
   const T inv = skip ? T(0) : T(1) / sqrt(vnorm2);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const T v = skip ? T(0) : (i == 0 ? col[i] - alpha : col[i]) * inv;
-    vv[i] = v;
-    col[i] = v;
+  // each thread rewrites the entries it loaded
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    vs[i] = skip ? T(0) : (i == 0 ? vs[i] - alpha : vs[i]) * inv;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) vv[i] = vs[i];
+    if (threadIdx.x == 0) e[k] = skip ? x0 : alpha;
   }
-  if (threadIdx.x == 0) e[k] = skip ? x0 : alpha;
-}
-
-// pw[i] = sum_j A[k+1+j, k+1+i] v[j] (one warp per i; column k+1+i is contiguous)
-template <typename T>
-__global__ void k_le_matvec(const T* __restrict__ A, int n, int k, const T* __restrict__ vv,
-                            T* __restrict__ pw) {
-  const int m = n - k - 1;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= m) return;
   const T* c = A + (k + 1) + (size_t)(k + 1 + i) * n;
-  T s = T(0);
-  for (int j = lane; j < m; j += 32) s += c[j] * vv[j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) pw[i] = s;
+  T sum = T(0);
+  for (int j = lane; j < m; j += 32) sum += c[j] * vs[j];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) pw[i] = sum;
 }
 
-// pw <- pw - (v . pw) v
+//  part 2: every CTA forms K = v . pw (same order in every CTA), then w = pw - K v on the fly
+//  and the trailing block A -= 2 (v w^T + w v^T), four elements per thread; CTA 0 stores v in
+//  column k below the diagonal (read by the back-transformation).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_le_w(int n, int k, const T* __restrict__ vv,
-                                               T* __restrict__ pw) {
+__global__ void __launch_bounds__(256) k_le_w_update(T* __restrict__ A, int n, int k,
+                                                     const T* __restrict__ vv,
+                                                     const T* __restrict__ pw) {
   __shared__ T red[32];
   const int m = n - k - 1;
   T kp = T(0);
   for (int i = threadIdx.x; i < m; i += blockDim.x) kp += vv[i] * pw[i];
   const T K = le_block_sum(kp, red);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) pw[i] -= K * vv[i];
-}
-
-// trailing block -= 2 (v w^T + w v^T)
-template <typename T>
-__global__ void k_le_update(T* __restrict__ A, int n, int k, const T* __restrict__ vv,
-                            const T* __restrict__ pw) {
-  const int m = n - k - 1;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)m * m) return;
-  const int i = (int)(idx % m), j = (int)(idx / m);
-  A[(k + 1 + i) + (size_t)(k + 1 + j) * n] -= T(2) * (vv[i] * pw[j] + pw[i] * vv[j]);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(k + 1 + i) + (size_t)k * n] = vv[i];
+  const long long mm = (long long)m * m;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const long long idx = ((long long)blockIdx.x * 4 + r) * blockDim.x + threadIdx.x;
+    if (idx >= mm) break;
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    const T wi = pw[i] - K * vv[i], wj = pw[j] - K * vv[j];
+    A[(k + 1 + i) + (size_t)(k + 1 + j) * n] -= T(2) * (vv[i] * wj + wi * vv[j]);
+  }
 }
 
 // d, e of the tridiagonal; e2 = e^2; Gershgorin bounds into bnd[0..1]
@@ -1370,20 +1441,25 @@ __global__ void __launch_bounds__(1024) k_le_clusters(int n, const T* __restrict
     }
 }
 
-// Y[k+1:, j] -= 2 (v_k . Y[k+1:, j]) v_k for every column j (one warp per column)
+// The whole back-transformation Y <- H_0 H_1 ... H_{n-3} Y in one launch: columns are
+// independent, so warp j applies every reflector to column j in turn: t = 2 v_k . y_j, then
+// y_j -= t v_k, for k = n-3 down to 0
 template <typename T>
-__global__ void k_le_apply(const T* __restrict__ A, int n, int k, T* __restrict__ Y) {
-  const int m = n - k - 1;
+__global__ void k_le_apply_all(const T* __restrict__ A, int n, T* __restrict__ Y) {
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (j >= n) return;
-  const T* v = A + (k + 1) + (size_t)k * n;
-  T* y = Y + (k + 1) + (size_t)j * n;
-  T t = T(0);
-  for (int i = lane; i < m; i += 32) t += v[i] * y[i];
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  t *= T(2);
-  for (int i = lane; i < m; i += 32) y[i] -= t * v[i];
+  for (int k = n - 3; k >= 0; --k) {
+    const int m = n - k - 1;
+    const T* v = A + (k + 1) + (size_t)k * n;
+    T* y = Y + (k + 1) + (size_t)j * n;
+    T t = T(0);
+    for (int i = lane; i < m; i += 32) t += v[i] * y[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    t *= T(2);
+    for (int i = lane; i < m; i += 32) y[i] -= t * v[i];
+    __syncwarp();  // the next reflector's rows are other lanes' rows of this one
+  }
 }
 
 template <typename T>
@@ -1402,19 +1478,24 @@ cudaError_t le_stage(const double* Ain, int n, double* big, double* vec, double*
   const LeArrays<T> a = le_arrays<T>(big, vec, n);
   const long long n2 = (long long)n * n;
   k_le_init<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(Ain, n, a.A);
+  const size_t vs_bytes = (size_t)n * sizeof(T);
+  if (vs_bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_le_house_matvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs_bytes);
+    if (e != cudaSuccess) return e;
+  }
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
-    k_le_reflector<T><<<1, 1024, 0, st>>>(a.A, n, k, a.vv, a.e);
-    k_le_matvec<T><<<(m + 7) / 8, 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
-    k_le_w<T><<<1, 1024, 0, st>>>(n, k, a.vv, a.pw);
     const long long mm = (long long)m * m;
-    k_le_update<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
+    k_le_house_matvec<T><<<(m + 7) / 8, 256, (size_t)m * sizeof(T), st>>>(a.A, n, k, a.vv, a.pw,
+                                                                          a.e);
+    k_le_w_update<T><<<(unsigned)((mm + 1023) / 1024), 256, 0, st>>>(a.A, n, k, a.vv, a.pw);
   }
   k_le_tridiag<T><<<1, 1024, 0, st>>>(a.A, n, a.d, a.e, a.e2, a.bnd);
   k_le_multisect<T><<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(
       n, a.d, a.e, a.e2, a.bnd, a.lam, a.Y, a.L);
   k_le_clusters<T><<<1, 1024, 0, st>>>(n, a.lam, a.bnd, T(1e-10), a.Y, a.cst);
-  for (int k = n - 3; k >= 0; --k) k_le_apply<T><<<(n + 7) / 8, 256, 0, st>>>(a.A, n, k, a.Y);
+  k_le_apply_all<T><<<(n + 7) / 8, 256, 0, st>>>(a.A, n, a.Y);
   k_le_out<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(a.Y, n2, V0, status);
   return cudaGetLastError();
 }
@@ -1470,6 +1551,18 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
     return ta ? launch_oz_gram(X, n, Y, n, n, n, n, C, n, oz, oz_err, stream)
               : launch_oz_rotate(X, n, Y, n, n, n, n, C, n, oz, oz_err, stream);
   };
+  // ||A||, the Ogita-Aishima bound and the Rayleigh quotients; grid-wide for large n (the
+  // partial sums go to scratch, free until the final step)
+  constexpr int kNormCtas = 304;
+  auto oa_norms = [&](const double* Am, const double* Sm, const double* Gm, double* lm,
+                      double* sc) {
+    if (n > 256) {
+      k_oa_norms_part<<<kNormCtas, 256, 0, stream>>>(Am, Sm, Gm, n, lm, scratch);
+      k_oa_norms_fin<<<1, 32, 0, stream>>>(scratch, kNormCtas, sc);
+    } else {
+      k_oa_norms<<<1, 1024, 0, stream>>>(Am, Sm, Gm, n, lm, sc);
+    }
+  };
   double* Vc = V0;
   double* Vn = V1;
   for (int it = 0; it < 3; ++it) {
@@ -1482,7 +1575,7 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
     if ((e = prod(false, A, Vc, P)) != cudaSuccess) return e;   // P = A V
     if ((e = prod(true, Vc, P, S)) != cudaSuccess) return e;    // S = V^T A V
     if ((e = prod(true, Vc, Vc, G)) != cudaSuccess) return e;   // G = V^T V
-    k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
+    oa_norms(A, S, G, lam, scal);
     k_oa_update<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(S, G, n, lam, scal, Ep);
     if ((e = prod(false, Vc, Ep, Vn)) != cudaSuccess) return e;  // V (I + E)
     std::swap(Vc, Vn);
@@ -1490,7 +1583,7 @@ cudaError_t launch_sym_eig(const double* A, int n, double* theta, double* V, dou
   if ((e = prod(false, A, Vc, P)) != cudaSuccess) return e;
   if ((e = prod(true, Vc, P, S)) != cudaSuccess) return e;
   if ((e = prod(true, Vc, Vc, G)) != cudaSuccess) return e;
-  k_oa_norms<<<1, 1024, 0, stream>>>(A, S, G, n, lam, scal);
+  oa_norms(A, S, G, lam, scal);
   // 3. sort, clusters, output
   k_oa_final<<<1, 1024, 0, stream>>>(S, G, Vc, n, scal, theta, V, scratch, status);
   return cudaGetLastError();
