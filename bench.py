@@ -1441,6 +1441,53 @@ def profile_hx(case, n_states, reps):
     ctx.close()
 
 
+def profile_dense(n_states):
+    """A case for profiler launch lists of the dense steps (no JSON bench line): one Cholesky-QR
+    (two passes) and one Rayleigh-Ritz of `n_states` seeded FP64 states of the 400-atom
+    cluster's basis (no projectors), with the dense precision of the at-scale iteration
+    (slice products) and its double-float H.X; prints the CUDA-event times."""
+    import torch
+
+    import paper_1404_3773_gb300 as cs
+    from workloads.device import erf_cluster_potential_t
+    w = W.erf_cluster_400_kb()
+    ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, 0)
+    xyz = torch.tensor(cs.grid_points(ctx), device="cuda")
+    cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, w.atoms()).contiguous())
+    del xyz
+    cs.cs_set_rr_precision(ctx, cs.CS_DF64)
+    cs.cs_set_dense_precision(ctx, cs.CS_FP64_SLICED)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.x_seed)
+    X = torch.randn((n_states, ctx.d), generator=gen, dtype=torch.float64, device="cuda")
+    HX = torch.empty_like(X)
+    th = torch.empty(n_states, dtype=torch.float64, device="cuda")
+    rs = torch.empty_like(th)
+    work = ctx.workspace(n_states, cs.CS_MIXED_BF16)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f()
+        e1.record()
+        e1.synchronize()
+        return round(e0.elapsed_time(e1), 2)
+
+    out = {"profile_dense": "erf400", "states": n_states,
+           "cholqr_ms": timed(lambda: cs.cs_cholqr(ctx, X, work))}
+    cs.cs_profile_begin(ctx)
+    out["rayleigh_ritz_ms"] = timed(lambda: cs.cs_rayleigh_ritz(ctx, X, th, rs, HX, work))
+    pms, pn = cs.cs_profile_end(ctx)
+    names = cs.profile_class_names()
+    out["rayleigh_ritz_classes_ms"] = {nm: round(pms[i], 2) for i, nm in enumerate(names)
+                                       if pn[i]}
+    if cs.cs_device_error(ctx) != 0:
+        raise RuntimeError("device error word set")
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1469,9 +1516,15 @@ def main():
                     help="only run a small mixed H.X case for profiler captures")
     ap.add_argument("--profile-states", type=int, default=32)
     ap.add_argument("--profile-reps", type=int, default=2)
+    ap.add_argument("--profile-dense", type=int, default=0, metavar="N",
+                    help="only run one Cholesky-QR and one Rayleigh-Ritz of N states of the "
+                         "400-atom cluster's basis for profiler captures")
     args = ap.parse_args()
     if args.profile_hx:
         profile_hx(args.profile_hx, args.profile_states, args.profile_reps)
+        return
+    if args.profile_dense:
+        profile_dense(args.profile_dense)
         return
     if args.impl == "reference":
         run_reference(args)
