@@ -29,6 +29,12 @@
 // columns are the accumulators of diagonals k .. 7: 8 MMAs per K step of 16. Every wait is bounded; on expiry the kernel
 // records an error code in *err, lets its copies and MMAs land (bounded), frees its tensor
 // memory and returns.
+//
+// Structure taken where the operands have it (results bit for bit unchanged): a Gram matrix of
+// one block with itself runs only the tiles that reach its upper triangle and writes each value
+// to both places; a rotation by an upper-triangular factor stops each tile's K range at the
+// tile's last column; rotations walk the grid B-side tile first, so the CTAs that read one
+// A-side tile run together and share it through L2.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
