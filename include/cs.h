@@ -164,7 +164,8 @@ cs_status cs_set_rr_precision(cs_ctx* ctx, cs_precision prec);
  * X Q, H X Q) of Cholesky-QR and Rayleigh-Ritz (Sec. 3.1.1, 3.2.1): CS_FP64 (default),
  * CS_DF64 (double-float on the FP32 pipe, FP64 storage, relative errors near 1e-14) or
  * CS_FP64_SLICED (exact integer-slice products on the tensor cores, rounded once; with it the
- * projector pair of every FP64 H.X is also taken as slice products). The small
+ * projector pair of every FP64 H.X is also taken as slice products, and so are the n x n
+ * products of the eigensolve's FP64 refinement for blocks above 256 states). The small
  * factorisation, eigensolve and residual norms stay FP64. Workspaces must be sized
  * (cs_workspace_bytes) after this call. CS_ERR_ARG otherwise. */
 cs_status cs_set_dense_precision(cs_ctx* ctx, cs_precision prec);
