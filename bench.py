@@ -1441,16 +1441,18 @@ def profile_hx(case, n_states, reps):
     ctx.close()
 
 
-def profile_dense(n_states):
-    """A case for profiler launch lists of the dense steps (no JSON bench line): one Cholesky-QR
+def profile_dense(n_states, case="erf400"):
+    """A case for profiler captures of the dense steps (no JSON bench line): one Cholesky-QR
     (two passes) and one Rayleigh-Ritz of `n_states` seeded FP64 states of the 400-atom
-    cluster's basis (no projectors), with the dense precision of the at-scale iteration
-    (slice products) and its double-float H.X; prints the CUDA-event times."""
+    cluster's basis (erf400, d = 357216; no projectors) or of the 32-atom cluster's (erf32,
+    d = 46128: a few GB on the device, for full-section captures), with the dense precision of
+    the at-scale iteration (slice products) and its double-float H.X; prints the CUDA-event
+    times."""
     import torch
 
     import paper_1404_3773_gb300 as cs
     from workloads.device import erf_cluster_potential_t
-    w = W.erf_cluster_400_kb()
+    w = W.erf_cluster_32() if case == "erf32" else W.erf_cluster_400_kb()
     ctx = cs.cs_basis_init(w.R, w.lmax, w.nmax, w.n_r, w.n_theta, w.n_phi, 0, 0)
     xyz = torch.tensor(cs.grid_points(ctx), device="cuda")
     cs.cs_set_potential(ctx, erf_cluster_potential_t(xyz, w.atoms()).contiguous())
@@ -1474,7 +1476,7 @@ def profile_dense(n_states):
         e1.synchronize()
         return round(e0.elapsed_time(e1), 2)
 
-    out = {"profile_dense": "erf400", "states": n_states,
+    out = {"profile_dense": case, "states": n_states,
            "cholqr_ms": timed(lambda: cs.cs_cholqr(ctx, X, work))}
     cs.cs_profile_begin(ctx)
     out["rayleigh_ritz_ms"] = timed(lambda: cs.cs_rayleigh_ritz(ctx, X, th, rs, HX, work))
@@ -1519,12 +1521,14 @@ def main():
     ap.add_argument("--profile-dense", type=int, default=0, metavar="N",
                     help="only run one Cholesky-QR and one Rayleigh-Ritz of N states of the "
                          "400-atom cluster's basis for profiler captures")
+    ap.add_argument("--profile-basis", default="erf400", choices=["erf32", "erf400"],
+                    help="basis of --profile-dense")
     args = ap.parse_args()
     if args.profile_hx:
         profile_hx(args.profile_hx, args.profile_states, args.profile_reps)
         return
     if args.profile_dense:
-        profile_dense(args.profile_dense)
+        profile_dense(args.profile_dense, args.profile_basis)
         return
     if args.impl == "reference":
         run_reference(args)
