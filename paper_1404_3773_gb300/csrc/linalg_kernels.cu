@@ -385,8 +385,9 @@ __global__ void __launch_bounds__(32) k_tri_inv_col(const double* __restrict__ w
 
 // The same factor for blocks whose L does not fit one CTA's shared memory, blocked over
 // panels of kCholNB columns so that the O(n^3) trailing update runs on the whole GPU: per panel
-// one CTA factors its columns (the one-CTA method above, restricted to the panel) and a grid of
-// 32 x 32 lower tiles subtracts the panel's outer product from the trailing block. L lives in
+// one CTA factors its diagonal block, one warp per row below it solves for the row's panel
+// entries, and a grid of 32 x 32 lower tiles subtracts the panel's outer product from the
+// trailing block. L lives in
 // `work` (L2-resident); status is cleared before the first launch.
 constexpr int kCholNB = 32;
 
@@ -406,38 +407,79 @@ __global__ void k_chol_init(const double* __restrict__ M, int n, double* __restr
   Lc[e] = (i >= j && oki && okj) ? M[e] * rsqrt(mi) * rsqrt(mj) : 0.0;
 }
 
-__global__ void __launch_bounds__(256) k_chol_panel(int n, int p, double* __restrict__ work,
-                                                    int* __restrict__ status) {
+// Panel p in two launches. The panel's 32 columns span up to n rows; one CTA updating them
+// column by column was bound by one SM's FP64 pipe (161 us per panel at n = 880). Now:
+//  (1) k_chol_diag: one CTA factors the 32 x 32 diagonal block in shared memory (pivot, rsqrt,
+//      column scale, rank-1 update of the block's trailing lower part);
+//  (2) k_chol_rows: one warp per row i below the block solves L[i][p:pe] L_D^T = A[i][p:pe] by
+//      forward substitution, lane k holding column p + k of the row.
+__global__ void __launch_bounds__(256) k_chol_diag(int n, int p, double* __restrict__ work,
+                                                   int* __restrict__ status) {
+  __shared__ double D[kCholNB][kCholNB + 1];
+  __shared__ double rs[kCholNB];
+  __shared__ int fail;
   double* Lc = work;
   double* rinv = work + (size_t)n * n + n;
-  __shared__ int fail;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = nt >> 5, pe = min(p + kCholNB, n);
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (status[0] != 0) return;
-  for (int j = p; j < pe; ++j) {
+  const int pe = min(p + kCholNB, n), nb = pe - p;
+  for (int e = tid; e < nb * nb; e += nt) {
+    const int i = e % nb, k = e / nb;
+    D[i][k] = (i >= k) ? Lc[(p + i) + (size_t)(p + k) * n] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
     if (tid == 0) {
       fail = 0;
-      const double piv = Lc[j + (size_t)j * n];
+      const double piv = D[j][j];
       if (!(piv > 0.0) || !isfinite(piv)) {
         fail = 1;
-        status[0] = j + 1;
+        status[0] = p + j + 1;
       } else {
         const double r = rsqrt(piv);
-        rinv[j] = r;
-        Lc[j + (size_t)j * n] = piv * r;
+        rs[j] = r;
+        D[j][j] = piv * r;
       }
     }
     __syncthreads();
     if (fail) return;
-    const double r = rinv[j];
-    for (int i = j + 1 + tid; i < n; i += nt) Lc[i + (size_t)j * n] *= r;
+    const double r = rs[j];
+    for (int i = j + 1 + tid; i < nb; i += nt) D[i][j] *= r;
     __syncthreads();
-    for (int k = j + 1 + warp; k < pe; k += nw) {
-      const double lkj = Lc[k + (size_t)j * n];
-      for (int i = k + lane; i < n; i += 32) Lc[i + (size_t)k * n] -= Lc[i + (size_t)j * n] * lkj;
+    const int m = nb - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (i >= k) D[i][k] -= D[i][j] * D[k][j];
     }
     __syncthreads();
   }
+  for (int e = tid; e < nb * nb; e += nt) {
+    const int i = e % nb, k = e / nb;
+    if (i >= k) Lc[(p + i) + (size_t)(p + k) * n] = D[i][k];
+  }
+  for (int j = tid; j < nb; j += nt) rinv[p + j] = rs[j];
+}
+
+__global__ void __launch_bounds__(256) k_chol_rows(int n, int p, double* __restrict__ work,
+                                                   const int* __restrict__ status) {
+  if (status[0] != 0) return;
+  double* Lc = work;
+  const double* rinv = work + (size_t)n * n + n;
+  const int pe = min(p + kCholNB, n), nb = pe - p;
+  const int lane = threadIdx.x & 31;
+  const long long i = pe + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (i >= n) return;  // whole warps leave together
+  double x = lane < nb ? Lc[i + (size_t)(p + lane) * n] : 0.0;
+  for (int j = 0; j < nb; ++j) {
+    // L[i][p + j] = (A[i][p + j] - sum_{k < j} L[i][p + k] L[p + j][p + k]) / L[p + j][p + j];
+    // lanes k < j already hold L[i][p + k]
+    const double ljk = lane < j ? Lc[(p + j) + (size_t)(p + lane) * n] : 0.0;
+    double t = lane < j ? x * ljk : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const double xj = __shfl_sync(0xffffffffu, x, j);
+    if (lane == j) x = (xj - t) * rinv[p + j];
+  }
+  if (lane < nb) Lc[i + (size_t)(p + lane) * n] = x;
 }
 
 // trailing update after panel p: L[i][k] -= sum_{j in panel} L[i][j] L[k][j], i >= k >= p + NB;
@@ -493,7 +535,11 @@ cudaError_t launch_cholqr_factor(const double* M, int n, double* U, double* work
     const long long n2 = (long long)n * n;
     k_chol_init<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(M, n, work, status);
     for (int p = 0; p < n; p += kCholNB) {
-      k_chol_panel<<<1, 256, 0, stream>>>(n, p, work, status);
+      k_chol_diag<<<1, 256, 0, stream>>>(n, p, work, status);
+      const int below = n - min(p + kCholNB, n);
+      if (below > 0)
+        k_chol_rows<<<(unsigned)(((long long)below * 32 + 255) / 256), 256, 0, stream>>>(n, p, work,
+                                                                                        status);
       const int rest = n - (p + kCholNB);
       if (rest > 0) {
         const int t = (rest + 31) / 32;

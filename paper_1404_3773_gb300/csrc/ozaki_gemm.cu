@@ -377,20 +377,30 @@ __global__ void k_oz_rowexp(const double* __restrict__ X, long long ld, long lon
   E[r] = oz_exponent(m);
 }
 
+// The digits of one K value i of an octet, packed as they are stored: p[k][i / 2] holds digit k
+// (BF16, exact: |a| <= 64) in its low half for even i and its high half for odd i. Packing as
+// each value is split keeps 32 registers of digits per thread instead of 64 integers.
+__device__ __forceinline__ void oz_pack_value(uint32_t (&p)[kS][4], int i, const int* a) {
+#pragma unroll
+  for (int k = 0; k < kS; ++k) {
+    const uint32_t h = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)a[k]));
+    if (i & 1)
+      p[k][i >> 1] |= h << 16;
+    else
+      p[k][i >> 1] = h;
+  }
+}
+
 // the 8 digits of one operand row's octet of K values into the layout with tiles of TR rows
 __device__ __forceinline__ void oz_store_digits(unsigned char* out, int TR, long long ksteps,
                                                 long long kstep, int kh, long long row,
-                                                const int (*dig)[kS]) {
-  // dig[i][k]: digit k of the operand row's K value i of this octet
+                                                const uint32_t (&p)[kS][4]) {
   const long long tile = row / TR, rt = row - tile * TR;
 #pragma unroll
   for (int k = 0; k < kS; ++k) {
-    __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn((float)dig[i][k]);
     const size_t off = (((size_t)(tile * ksteps + kstep) * kS + k) * (TR / 8) + (rt >> 3)) * 256 +
                        kh * 128 + (rt & 7) * 16;
-    *reinterpret_cast<uint4*>(out + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(out + off) = make_uint4(p[k][0], p[k][1], p[k][2], p[k][3]);
   }
 }
 
@@ -405,15 +415,17 @@ __global__ void k_oz_split_cols(const double* __restrict__ X, long long ld, long
   if (t >= cols_pad * (kpad / 8)) return;
   const long long c = t % cols_pad, oct = t / cols_pad;
   const int e = E[c];
-  int dig[8][kS];
+  uint32_t p[kS][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const long long r = oct * 8 + i;
     const double x = (c < n && r < d) ? X[r + c * ld] : 0.0;
-    oz_slices(x, e, kBeta, kS, dig[i]);
+    int a[kS];
+    oz_slices(x, e, kBeta, kS, a);
+    oz_pack_value(p, i, a);
   }
-  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), c, dig);
-  if (out2 && c < cols2) oz_store_digits(out2, TR2, kpad / 16, oct >> 1, (int)(oct & 1), c, dig);
+  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), c, p);
+  if (out2 && c < cols2) oz_store_digits(out2, TR2, kpad / 16, oct >> 1, (int)(oct & 1), c, p);
 }
 
 // Operand rows = rows r of X (d x n, ld), K = columns c (rotation side; one exponent per row).
@@ -425,14 +437,16 @@ __global__ void k_oz_split_rows(const double* __restrict__ X, long long ld, long
   if (t >= rows_pad * (kpad / 8)) return;
   const long long r = t % rows_pad, oct = t / rows_pad;
   const int e = E[r];
-  int dig[8][kS];
+  uint32_t p[kS][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const long long c = oct * 8 + i;
     const double x = (r < d && c < n) ? X[r + c * ld] : 0.0;
-    oz_slices(x, e, kBeta, kS, dig[i]);
+    int a[kS];
+    oz_slices(x, e, kBeta, kS, a);
+    oz_pack_value(p, i, a);
   }
-  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), r, dig);
+  oz_store_digits(out, TR, kpad / 16, oct >> 1, (int)(oct & 1), r, p);
 }
 
 long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
