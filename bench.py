@@ -1407,10 +1407,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_hx(case, n_states, reps):
-    """A small case for profiler captures (no JSON bench line): `reps` mixed H.X calls on
-    `n_states` seeded states of the 32-atom cluster (erf32) or of the 400-atom cluster without
-    its projectors (erf400), after one untimed call; prints the mean CUDA-event time."""
+def profile_hx(case, n_states, reps, precision="mixed"):
+    """A small case for profiler captures (no JSON bench line): `reps` H.X calls (mixed, or
+    double-float on FP64 states) on `n_states` seeded states of the 32-atom cluster (erf32) or
+    of the 400-atom cluster without its projectors (erf400), after one untimed call; prints the
+    mean CUDA-event time."""
     import torch
 
     import paper_1404_3773_gb300 as cs
@@ -1422,20 +1423,22 @@ def profile_hx(case, n_states, reps):
     del xyz
     gen = torch.Generator(device="cuda")
     gen.manual_seed(w.x_seed)
-    X = torch.randn((n_states, ctx.d), generator=gen, dtype=torch.float32, device="cuda")
+    prec = cs.CS_DF64 if precision == "df64" else cs.CS_MIXED_BF16
+    dtype = torch.float64 if precision == "df64" else torch.float32
+    X = torch.randn((n_states, ctx.d), generator=gen, dtype=dtype, device="cuda")
     Y = torch.empty_like(X)
-    work = ctx.workspace(n_states, cs.CS_MIXED_BF16)
-    cs.cs_apply_H(ctx, X, Y, cs.CS_MIXED_BF16, work)
+    work = ctx.workspace(n_states, prec)
+    cs.cs_apply_H(ctx, X, Y, prec, work)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        cs.cs_apply_H(ctx, X, Y, cs.CS_MIXED_BF16, work)
+        cs.cs_apply_H(ctx, X, Y, prec, work)
     e1.record()
     e1.synchronize()
     if cs.cs_device_error(ctx) != 0:
         raise RuntimeError("device error word set")
-    print(json.dumps({"profile_hx": case, "states": n_states, "reps": reps,
+    print(json.dumps({"profile_hx": case, "precision": precision, "states": n_states, "reps": reps,
                       "ms_per_apply": round(e0.elapsed_time(e1) / max(1, reps), 4),
                       "angular_kernel": os.environ.get("CS_ANGULAR_KERNEL", "default")}))
     ctx.close()
@@ -1518,6 +1521,8 @@ def main():
                     help="only run a small mixed H.X case for profiler captures")
     ap.add_argument("--profile-states", type=int, default=32)
     ap.add_argument("--profile-reps", type=int, default=2)
+    ap.add_argument("--profile-precision", default="mixed", choices=["mixed", "df64"],
+                    help="arithmetic of the --profile-hx calls")
     ap.add_argument("--profile-dense", type=int, default=0, metavar="N",
                     help="only run one Cholesky-QR and one Rayleigh-Ritz of N states of the "
                          "400-atom cluster's basis for profiler captures")
@@ -1525,7 +1530,8 @@ def main():
                     help="basis of --profile-dense")
     args = ap.parse_args()
     if args.profile_hx:
-        profile_hx(args.profile_hx, args.profile_states, args.profile_reps)
+        profile_hx(args.profile_hx, args.profile_states, args.profile_reps,
+                   args.profile_precision)
         return
     if args.profile_dense:
         profile_dense(args.profile_dense, args.profile_basis)
